@@ -1,0 +1,15 @@
+"""Seeded synthetic workloads shared by the CUDA path and the CPU oracle.
+
+This package holds configuration (sizes, grid extents, prior boxes, fiducial
+values) and seeded random draws (emulator weights, noise realisations,
+covariance ingredients).  It deliberately contains none of the method's
+arithmetic: no distances, windows, projections, likelihoods or sampler steps.
+Both sides consume its outputs and compute everything else themselves.
+"""
+
+from .configs import (  # noqa: F401
+    ShearConfig, GaussConfig, CMBConfig, SamplerConfig,
+    shear5, shear39, shear37_lcdm, shear33, shear_tiny, gauss_test, cmb6,
+    SHEAR_BASE_NAMES, shear_param_names,
+)
+from .synth import make_shear_inputs, make_gauss_inputs, make_cmb_inputs  # noqa: F401
