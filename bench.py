@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the batched nested-slice-sampling step (arXiv:2509.13307) on
+the 39-parameter w0-wa cosmic-shear workload, one JSON line on rank 0.
+
+A step is one nested-sampling iteration: delete the k = 500 lowest of
+n = 1000 live points (FP64 evidence update), live covariance + Cholesky,
+500 chains x 5d = 195 hit-and-run slice moves, every proposal scored by the
+fused likelihood (BF16 tcgen05 emulator 7 -> 4x1024 -> 10000, chi(z), windows,
+P(k, z) lookup, Limber, whitened chi^2).  The metric is likelihood
+evaluations per second over the timed steps (device time, CUDA events on the
+run's stream, L2 flushed between steps).  Also reported: the plain FP32 form
+on the same workload, iterations/s, wall time to a converged log Z, the
+end-to-end rate through the public API with host buffers, the roofline of the
+dominant kernel, and the CPU oracle as a baseline.
+
+Multi-GPU (torchrun): each rank runs an independent nested-sampling run with
+its own seed (runs are independent problems: weak scaling, no collective on the
+data path); the value is the sum of evaluations over the max of rank times.
+
+--impl reference times the CPU oracle on the same workload (bounded sample of
+likelihood evaluations per step) and prints the same JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "logL evals/s and seconds to converged logZ (39-d shear), BF16+adjoint vs plain FP32"
+UNIT = "evals/s"
+WORKLOAD = ("shear39: 39-parameter w0-wa cosmic shear (7 cosmology + 2 baryon + 2 IA + 5 D_z + 5 m + "
+            "18 template amplitudes), 5 tomographic bins x 20 ell (D = 300), emulator 7->4x1024->(200 k x 50 z), "
+            "1025 chi nodes uniform in a on [1/6.02, 1], dense Knox + rank-5 covariance; n_live = 1000, "
+            "k = 500 chains, 5d = 195 slice moves per chain")
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def cpu_oracle_rate(seconds: float = 12.0, threads: int = 1) -> dict:
+    """Oracle log-likelihood evaluations/s on the host (bounded sample), in a
+    subprocess with BLAS/OpenMP pinned to `threads`."""
+    code = r"""
+import os, sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+import workloads as w
+from oracle.shear import ShearOracle
+from oracle.priors import cube_to_theta
+inp = w.make_shear_inputs(w.shear39())
+o = ShearOracle(inp)
+rng = np.random.default_rng(0)
+n = 0; t0 = time.time()
+while time.time() - t0 < %f:
+    o.loglike_cube(rng.uniform(0.02, 0.98, 39)); n += 1
+dt = time.time() - t0
+print(json.dumps({"n": n, "s": dt}))
+""" % (ROOT, seconds)
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = str(threads)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": threads, "kind": "oracle", "error": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["n"] / d["s"], "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{d['n']} oracle log-likelihood evaluations of the 39-d shear problem at random "
+                      f"prior points ({d['s']:.1f} s, FP64 NumPy, {threads} thread)"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def projection_flops_per_eval(cfg) -> float:
+    """Algorithmic FLOPs of the shear projection kernel per evaluation (the
+    count stated in the design notes): per (ell, chi-node) a 16-tap bicubic
+    lookup (32) + bracket/weights (10) + nb window products + 2 n_pairs Limber
+    FMAs; per node interval the 4-point distance quadrature (4 x 12); per node
+    and bin the n(z) / window work (25); per data element bias + templates."""
+    N = cfg.n_chi
+    nb = cfg.n_bins
+    npairs = nb * (nb + 1) // 2
+    return (cfg.n_ell * (N - 1) * (32 + 10 + nb + 2 * npairs) + (N - 1) * 48 + N * nb * 25
+            + cfg.n_data * (3 + 2 * cfg.n_tmpl))
+
+
+def fp32_alu_peak_tflops(sm_mhz: float) -> float:
+    """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16")
+    ap.add_argument("--no-full-run", action="store_true", help="skip the time-to-converged-logZ run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+def reference_arm(args):
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    if world > 1 and rank != 0:
+        return 0
+    import numpy as np
+    import workloads as w
+    from oracle.shear import ShearOracle
+    inp = w.make_shear_inputs(w.shear39())
+    o = ShearOracle(inp)
+    rng = np.random.default_rng(0)
+    per_step = 24
+    for _ in range(args.warmup):
+        for _ in range(per_step):
+            o.loglike_cube(rng.uniform(0.02, 0.98, 39))
+    t0 = time.time()
+    for _ in range(args.steps):
+        for _ in range(per_step):
+            o.loglike_cube(rng.uniform(0.02, 0.98, 39))
+    dt = time.time() - t0
+    val = args.steps * per_step / dt
+    threads = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{per_step} evaluations per step"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": int(threads), "kind": "oracle",
+                             "sample": f"{per_step} oracle log-likelihood evaluations per step at random prior points"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2509_13307_gb300.build import build
+    build()
+    import workloads as w
+    from paper_2509_13307_gb300 import Problem, NestedRun
+
+    cfg = w.shear39()
+    inp = w.make_shear_inputs(cfg)
+    sc = cfg.sampler
+    seed = sc.seed + rank
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed_steps(prob, n_warm, n_steps, profile=None):
+        run = NestedRun(prob, sc.n_live, sc.n_delete, sc.repeats, sc.tol, seed, sc.width, sc.step_cap, sc.ridge)
+        for _ in range(n_warm):
+            run.step(1)
+        if profile:
+            run.profile_stage(profile)
+        st0 = run.step(0)
+        ms = 0.0
+        for _ in range(n_steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run.step(1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        barrier()
+        st1 = run.step(0)
+        prof = run.profile_read() if profile else None
+        out = dict(ms=ms, evals=st1.evaluations - st0.evaluations, rounds=st1.rounds - st0.rounds,
+                   iters=st1.iterations - st0.iterations, prof=prof, status=st1.status_bits)
+        run.close()
+        return out
+
+    # ---------------- main arm: BF16 likelihood, timed NS steps
+    prob = Problem(inp, args.precision, max_batch=sc.n_live)
+    clocks = ClockSampler(torch.cuda.current_device() if world == 1 else local)
+    clocks.start()
+    res = timed_steps(prob, args.warmup, args.steps, profile="projection")
+    clk = clocks.stop()
+
+    t_local = res["ms"] / 1e3
+    ev_local = res["evals"]
+    if world > 1:
+        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        e = torch.tensor([float(ev_local)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        t_job, ev_job = t.item(), e.item()
+    else:
+        t_job, ev_job = t_local, float(ev_local)
+    value = ev_job / t_job
+
+    # kernels launched per round: slice state machine, prior transform, emulator input
+    # layer, one GEMM per further layer, projection, chi^2; per iteration 5 more.
+    n_layers = len(inp["emu_W"])
+    per_round = 3 + (n_layers - 1) + 2
+    gpu_launches = res["rounds"] * per_round + 5 * res["iters"]
+
+    # ---------------- roofline of the dominant kernel (projection), timed live
+    prof = res["prof"]
+    flops = projection_flops_per_eval(cfg)
+    peak = fp32_alu_peak_tflops(2070.0)
+    roofline = None
+    if prof and prof["launches"] > 0 and prof["ms"] > 0:
+        achieved = prof["rows"] * flops / (prof["ms"] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "k_shear_eval<float,5> (A8-A12: distances, windows, P lookup, Limber, data vector)",
+                    "flop_per_eval": flops, "avg_launch_ms": prof["ms"] / prof["launches"],
+                    "avg_rows_per_launch": prof["rows"] / prof["launches"],
+                    "peak_basis": "FP32 ALU 152 SM x 128 lanes x 2 x 2070 MHz (no measured FP32 peak in MEASURED_PEAKS.json)"}
+
+    extra = {}
+    # ---------------- plain FP32 form on the same workload
+    if args.precision != "fp32":
+        p32 = Problem(inp, "fp32", max_batch=sc.n_live)
+        r32 = timed_steps(p32, 1, 2)
+        p32.close()
+        extra["fp32_evals_per_s"] = r32["evals"] / (r32["ms"] / 1e3)
+        extra["speedup_vs_fp32"] = value / extra["fp32_evals_per_s"] if world == 1 else \
+            (ev_local / t_local) / extra["fp32_evals_per_s"]
+    extra["iters_per_s"] = res["iters"] / t_local
+    extra["rounds_per_step"] = res["rounds"] / max(res["iters"], 1)
+
+    # ---------------- wall time to a converged log Z (BF16), from ns_init
+    if not args.no_full_run:
+        torch.cuda.synchronize()
+        t0 = time.time()
+        run = NestedRun(prob, sc.n_live, sc.n_delete, sc.repeats, sc.tol, seed, sc.width, sc.step_cap, sc.ridge)
+        st = run.run(max_iters=2000)
+        ev = run.evidence()
+        t1 = time.time()
+        extra.update(time_to_logZ_s=t1 - t0, logZ=ev["logZ"], logZ_err=ev["logZ_err"], logZ_iters=st.iterations,
+                     logZ_evals=st.evaluations, logZ_converged=st.converged)
+        run.close()
+
+    # ---------------- end to end through the public API with host buffers
+    B = sc.n_delete
+    rng = np.random.default_rng(rank)
+    free = [i for i, p in enumerate(inp["priors"]) if p[0] != "F"]
+    host_theta = torch.empty((B, len(free)), dtype=torch.float64).pin_memory()
+    host_out = torch.empty(B, dtype=torch.float64).pin_memory()
+    cube = torch.tensor(rng.uniform(0.05, 0.95, (B, len(free))), device=dev)
+    host_theta.copy_(prob.prior_transform(cube).cpu())
+    for _ in range(3):
+        prob.loglike(host_theta.to(dev, non_blocking=True))
+    reps = 40
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for _ in range(reps):
+        th = host_theta.to(dev, non_blocking=True)
+        host_out.copy_(prob.loglike(th), non_blocking=True)
+    torch.cuda.synchronize()
+    e2e = {"value": reps * B / (time.time() - t0), "unit": UNIT,
+           "h2d_bytes_per_step": B * len(free) * 8, "d2h_bytes_per_step": B * 8,
+           "how": "loglike_batch on B = 500 parameter vectors from pinned host memory, H2D + call + D2H per step"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_oracle_rate()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": args.precision,
+                           "l2": "flushed between timed steps (256 MB write)",
+                           "evals_per_step": res["evals"] / max(res["iters"], 1),
+                           "status_bits": res["status"]},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": gpu_launches}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

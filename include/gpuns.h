@@ -1,0 +1,253 @@
+/*
+ * gpuns.h -- C ABI of the GB300 (sm_103a) batched nested-slice-sampling library
+ * with fused emulator -> chi(z) -> Limber -> chi^2 cosmic-shear likelihoods.
+ *
+ * Method: arXiv:2509.13307 (Lovick, Yallup, Piras, Spurio Mancini, Handley),
+ *   Sec. 2.1  nested sampling: evidence Z = int L pi dtheta (Eq. 1), live points
+ *             replaced under a hard likelihood constraint, slice sampling inside;
+ *   Sec. 2.2  the k lowest live points deleted at once and k chains evolved in
+ *             parallel;
+ *   Eq. 2     Bayes factor B01 = Z0 / Z1 (formed by the caller from two runs);
+ *   App. A    the cosmic-shear likelihood: Eq. 3 (C^eps = gg + gI + Ig + II),
+ *             Eq. 4 (extended Limber with k = (ell + 1/2) / chi), Eq. 5 (shear
+ *             window), Eq. 6 (NLA intrinsic-alignment window), multiplicative
+ *             bias (1 + m_i)(1 + m_j), photo-z shifts n_i(z - D_z,i), a
+ *             multivariate Gaussian likelihood, integrals on a chi grid uniform
+ *             in scale factor from a = 1 to a_min;
+ *   Table 1   uniform and Gaussian priors.
+ *
+ * Conventions for every entry point:
+ *   - Return value: NS_OK (0) or a negative NS_E* code; ns_strerror() names it.
+ *     Nothing throws or aborts across this boundary.
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller; every
+ *     other pointer is host memory owned by the caller and only read during
+ *     the call (the library copies what it keeps).
+ *   - Matrices are row-major.  Floating-point arguments at the boundary are
+ *     always FP64; the arithmetic precision inside is the problem's
+ *     `precision`.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream unless stated.
+ *   - One problem or run must not be used from two streams at once: each owns
+ *     scratch buffers that consecutive calls reuse.
+ */
+#ifndef GPUNS_H
+#define GPUNS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define NS_OK           0
+#define NS_EINVAL      (-1)   /* invalid argument or descriptor */
+#define NS_ECUDA       (-2)   /* a CUDA runtime / driver call failed */
+#define NS_ENOMEM      (-3)   /* device or host allocation failed */
+#define NS_ETIMEOUT    (-4)   /* a bounded device wait gave up (kernel watchdog) */
+#define NS_ESLICE      (-5)   /* a slice step cap was reached (also a status bit) */
+#define NS_ENONFINITE  (-6)   /* a likelihood evaluated to NaN/inf (also a status bit) */
+#define NS_ENOTSUP     (-7)   /* combination not supported by this build */
+
+/* ---- status bits accumulated by a run (ns_status.status_bits) ---------- */
+#define NS_BIT_SLICE_CAP  1   /* stepping-out or shrinkage hit its cap */
+#define NS_BIT_NONFINITE  2   /* some log L was NaN/inf (treated as outside) */
+#define NS_BIT_TIMEOUT    4   /* a device wait hit its bound */
+
+/* ---- enums -------------------------------------------------------------- */
+enum ns_kind { NS_KIND_GAUSS = 0, NS_KIND_SHEAR = 1 };
+/* Arithmetic of the likelihood.  FP64: every stage in double.  FP32: every
+ * stage in float (emulator on CUDA cores), the constant and the final log L in
+ * double.  BF16: emulator hidden/output GEMMs as tcgen05 BF16 x BF16 -> FP32
+ * tensor-core MMAs, all other stages FP32.  BF16_F64CHI2: as BF16 but the
+ * whitening solve and chi^2 in FP64. */
+enum ns_precision { NS_PREC_FP64 = 0, NS_PREC_FP32 = 1, NS_PREC_BF16 = 2, NS_PREC_BF16_F64CHI2 = 3 };
+enum ns_prior_kind { NS_PRIOR_UNIFORM = 0, NS_PRIOR_GAUSS = 1, NS_PRIOR_FIXED = 2 };
+enum ns_activation { NS_ACT_TANH = 0 };
+
+/* One prior per full parameter (Table 1).  UNIFORM: theta = a + (b - a) c;
+ * GAUSS: theta = a + b Phi^-1(c) (mean a, sd b); FIXED: theta = a and the
+ * parameter takes no cube coordinate.  c is the unit-cube coordinate. */
+typedef struct { int kind; double a; double b; } ns_prior;
+
+/* Emulator: an MLP of n_layers weight matrices, hidden layers act(W h + b),
+ * output y = W h + b de-standardised as out_mu[o] + out_sigma * y[o].  The
+ * input is x_j = (theta[inputs[j]] - in_center[j]) / in_scale[j].
+ * For the shear kind the output is log10 P on the (z, k) table, z-major:
+ * o = jz * n_k + ik. */
+typedef struct {
+    int n_layers;                 /* >= 2 */
+    const int* dims;              /* n_layers + 1 sizes; dims[0] = number of inputs */
+    const double* const* W;       /* W[l]: dims[l+1] x dims[l], row-major */
+    const double* const* b;       /* b[l]: dims[l+1] */
+    int activation;               /* ns_activation */
+    const int* inputs;            /* dims[0] indices into the full parameter vector */
+    const double* in_center;      /* dims[0] */
+    const double* in_scale;       /* dims[0] */
+    const double* out_mu;         /* dims[n_layers] */
+    double out_sigma;
+} ns_emulator_desc;
+
+/* Cosmic-shear model (App. A).  Full parameter layout:
+ *   0 omega_b, 1 omega_cdm, 2 h, 3 n_s, 4 ln10^10 A_s, 5 w0, 6 wa, 7 c_min,
+ *   8 eta0, 9 A_IA, 10 eta_IA, 11.. D_z[n_bins], then m[n_bins], then
+ *   template amplitudes b[n_tmpl]; n_params = 11 + 2 n_bins + n_tmpl.
+ * Data vector element a = p * n_ell + e for bin pair p (i <= j, row-major
+ * over i then j) and multipole e. */
+typedef struct {
+    int n_bins;
+    const double* nz_mean;        /* Gaussian n_i(z) mean per bin */
+    const double* nz_sigma;       /* and width */
+    int n_ell;
+    const double* ell;            /* multipoles */
+    int n_k;                      /* table k grid: uniform in ln k on [lnk_min, lnk_max] */
+    double lnk_min, lnk_max;
+    int n_z;                      /* table z grid: uniform on [0, z_max] */
+    double z_max;
+    int n_z_emu;                  /* emulator z nodes: n_z, or fewer (uniform on [0, z_max])
+                                     interpolated to n_z by Catmull-Rom in z */
+    int n_chi;                    /* chi grid: uniform in a on [a_min, 1], node 0 at a = 1 */
+    double a_min;
+    double ia_pivot;              /* A(z) = A_IA ((1 + z) / ia_pivot)^eta_IA */
+    double c1rho;                 /* C_1 rho_cr (Eq. 6) */
+    int n_tmpl;
+    const double* tmpl;           /* n_data x n_tmpl noise templates (may be NULL if n_tmpl = 0) */
+} ns_shear_desc;
+
+/* Isotropic Gaussian test likelihood on the cube: log L = -1/2 |(x - mu)/sigma|^2 - d ln(sigma sqrt(2 pi)). */
+typedef struct { double mu; double sigma; } ns_gauss_desc;
+
+typedef struct {
+    int kind;                     /* ns_kind */
+    int precision;                /* ns_precision */
+    int n_params;                 /* length of the full parameter vector */
+    const ns_prior* priors;       /* n_params */
+    int n_data;                   /* D (shear); ignored for GAUSS */
+    const double* data;           /* D */
+    const double* cov;            /* D x D symmetric positive definite; factorised in FP64 */
+    ns_emulator_desc emu;
+    ns_shear_desc shear;
+    ns_gauss_desc gauss;
+    int max_batch;                /* largest batch B any call will pass (>= 1) */
+} ns_problem_desc;
+
+typedef struct ns_problem ns_problem;
+typedef struct ns_run ns_run;
+
+/* Nested-sampling settings (Sec. 2.1-2.2 and the recorded readings of the
+ * slice-sampler internals). */
+typedef struct {
+    int n_live;                   /* n */
+    int n_delete;                 /* k: deleted per iteration, chains evolved in parallel */
+    int repeats;                  /* slice moves per chain; <= 0 means 5 d */
+    double tol;                   /* stop when ln(Z_dead + Z_live) - ln Z_dead < tol */
+    unsigned long long seed;      /* Philox4x32-10 key */
+    double width;                 /* initial slice width along a unit-Mahalanobis direction */
+    int step_cap;                 /* cap on stepping-out steps and on shrinkage steps */
+    double ridge;                 /* added to the live-covariance diagonal */
+    int rounds_per_sync;          /* likelihood rounds launched between host checks (<= 0: auto) */
+} ns_config;
+
+typedef struct {
+    long long iterations;         /* NS iterations completed by this run */
+    long long evaluations;        /* likelihood evaluations (init included) */
+    long long rounds;             /* batched likelihood rounds launched */
+    int converged;                /* termination criterion met */
+    int status_bits;              /* NS_BIT_* */
+    double logZ;                  /* dead-point evidence so far */
+    double logX;                  /* log enclosed prior mass */
+    double lstar;                 /* last deletion threshold */
+} ns_status;
+
+/* ---- entry points ------------------------------------------------------- */
+
+/* Static description of a status code (never NULL). */
+const char* ns_strerror(int code);
+
+/* Build a problem on the current CUDA device: copies every host array, converts
+ * weights to the problem precision, factorises cov = L L^T in FP64 (host),
+ * forms L^-1 and the constant c0 = -sum ln L_aa - D/2 ln 2 pi.
+ * Errors: NS_EINVAL (bad sizes, non-SPD covariance, unknown enums),
+ * NS_ENOMEM, NS_ECUDA, NS_ENOTSUP (e.g. BF16 with shapes the tensor-core
+ * path cannot tile). */
+int ns_problem_create(const ns_problem_desc* desc, ns_problem** out);
+int ns_problem_free(ns_problem* p);
+
+/* Number of free (non-FIXED) parameters d. */
+int ns_problem_dim(const ns_problem* p, int* d);
+
+/* Prior transform (Table 1): cube_dev (B x d) in (0,1) -> theta_dev (B x d)
+ * physical free parameters.  B <= max_batch. */
+int ns_prior_transform(const ns_problem* p, const double* cube_dev, int B,
+                       double* theta_dev, void* stream);
+
+/* Batched log-likelihood at physical free parameters theta_dev (B x d):
+ * logL_dev[b] = log L(theta_b).  B <= max_batch; B = 0 is a no-op.
+ * Non-finite results are returned as they are. */
+int loglike_batch(const ns_problem* p, const double* theta_dev, int B,
+                  double* logL_dev, void* stream);
+
+/* Shear model data vector m(theta) (B x D, FP64 out), before the residual.
+ * Used to build mock data.  NS_EINVAL for the GAUSS kind. */
+int ns_model_batch(const ns_problem* p, const double* theta_dev, int B,
+                   double* model_dev, void* stream);
+
+/* Emulator output (B x dims[n_layers], FP64 out) at physical free parameters:
+ * for the shear kind log10 P on the emulator's (z, k) grid, z-major, computed
+ * in the problem precision (BF16: tcgen05 GEMMs with FP32 accumulation).
+ * NS_EINVAL for the GAUSS kind. */
+int ns_emulator_batch(const ns_problem* p, const double* theta_dev, int B,
+                      double* out_dev, void* stream);
+
+/* Log-likelihood and its gradient d log L / d theta (B x d) by a hand-written
+ * adjoint of the likelihood stages.  NS_ENOTSUP where not built. */
+int loglike_grad_batch(const ns_problem* p, const double* theta_dev, int B,
+                       double* logL_dev, double* grad_dev, void* stream);
+
+/* Start a run: draws n live points uniformly in the cube (Philox counter
+ * (INIT | chunk << 8, 0, point, 0)), evaluates them, zeroes the evidence
+ * accumulators.  The run keeps the problem pointer: free the run first.
+ * Errors: NS_EINVAL (n_delete not in [1, n_live - 1], n_delete > max_batch,
+ * n_live > 4096, d > 64). */
+int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, ns_run** out);
+
+/* Run up to n_iters NS iterations (fewer if the termination criterion is met)
+ * and fill *st (may be NULL).  Synchronises the run's stream. */
+int ns_step(ns_run* r, int n_iters, ns_status* st);
+
+/* Final evidence with the live points added (ascending log L with n, n-1, ...
+ * 1 live points) without changing the run: log Z, its error (standard
+ * deviation over n_replays simulated shrinkage sequences, Philox counters
+ * (ERR, replay, dead index, 0); n_replays <= 0 means 200), log X, the
+ * information H and the number of dead points including the live ones.
+ * Any output pointer may be NULL.  Synchronises the run's stream. */
+int ns_evidence(const ns_run* r, int n_replays, double* logZ, double* logZ_err,
+                double* logX, double* H, long long* n_dead);
+
+/* Copy out the live set (x: n x d cube coordinates, logL: n); either may be NULL. */
+int ns_live_points(const ns_run* r, double* x, double* logL);
+
+/* Copy out up to max_out dead points in deletion order (x: cube coordinates,
+ * logL, and the live-point count booked for each).  *n_out = number copied. */
+int ns_dead_points(const ns_run* r, long long max_out, double* x, double* logL,
+                   int* n_live_at_death, long long* n_out);
+
+/* Record of the last completed iteration: L*, deleted live slots (k, ascending
+ * (log L, slot)), start slots (k), evaluations per chain (k).  Any may be NULL. */
+int ns_last_iteration(const ns_run* r, double* lstar, int* deleted, int* starts, int* evals);
+
+/* Stage timing for roofline reporting: with stage != 0, every graph launch of
+ * likelihood rounds records CUDA events on its stream around that stage in its
+ * first round (1 = shear projection kernel: background, windows, P lookup,
+ * Limber, data vector; 2 = emulator output GEMM; 3 = whitening / chi^2;
+ * 4 = first hidden emulator GEMM) and the stage's batch size.  0 turns it off.
+ * Resets the accumulators. */
+int ns_profile_stage(ns_run* r, int stage);
+
+/* Accumulated stage time [ms], number of timed launches and rows they processed. */
+int ns_profile_read(const ns_run* r, double* total_ms, long long* launches, long long* rows);
+
+int ns_free(ns_run* r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPUNS_H */

@@ -1,0 +1,321 @@
+"""Thin Python layer over the C ABI: builds problem descriptors from the seeded
+workload inputs, passes torch CUDA tensors by pointer on torch's current stream,
+and wraps runs.  Every numerical step runs inside libgpuns.so."""
+
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from .mock import diagonal_covariance, knox_covariance
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _require_cuda(t: torch.Tensor, name: str, dtype=torch.float64):
+    if not t.is_cuda or t.dtype != dtype or t.dim() != 2:
+        raise ValueError(f"{name} must be a 2-D CUDA {dtype} tensor")
+    return t.contiguous()
+
+
+class Problem:
+    """A likelihood problem resident on the current CUDA device."""
+
+    def __init__(self, inp: dict, precision: str = "fp64", max_batch: int = 1024, data=None, cov=None):
+        self.lib = L.load()
+        self.inp = inp
+        self.kind = inp["kind"]
+        self.precision = precision
+        self.max_batch = int(max_batch)
+        self._h = C.c_void_p()
+        if self.kind == "shear" and (data is None or cov is None):
+            data, cov = self._make_mock()
+        self.data = None if data is None else np.ascontiguousarray(data, dtype=np.float64)
+        self.cov = None if cov is None else np.ascontiguousarray(cov, dtype=np.float64)
+        self._create(precision, self.max_batch, self.data, self.cov, self._templates(self.cov))
+        d = C.c_int()
+        L.check(self.lib.ns_problem_dim(self._h, C.byref(d)), "ns_problem_dim")
+        self.d = d.value
+
+    # ------------------------------------------------------------ set-up
+    def _templates(self, cov):
+        inp = self.inp
+        if self.kind != "shear" or inp["n_tmpl"] == 0:
+            return None
+        if cov is None:
+            return np.zeros((len(inp["noise_eps"]), inp["n_tmpl"]))
+        sig = np.sqrt(np.diag(cov))
+        return np.ascontiguousarray(0.1 * sig[:, None] * inp["tmpl_g"])
+
+    def _make_mock(self):
+        """data = model(fiducial) + L eps with the library's FP64 model vector."""
+        inp = self.inp
+        D = len(inp["noise_eps"])
+        self._create("fp64", 1, np.zeros(D), np.eye(D),
+                     np.zeros((D, inp["n_tmpl"])) if inp["n_tmpl"] else None)
+        fid = np.asarray(inp["fiducial"], float)
+        free = [i for i, p in enumerate(inp["priors"]) if p[0] != "F"]
+        th = torch.tensor(fid[free][None, :], dtype=torch.float64, device="cuda")
+        mfid = self.model(th)[0].cpu().numpy()
+        self._free()
+        if inp["cov_kind"] == "diag10":
+            cov = diagonal_covariance(mfid)
+        else:
+            cov = knox_covariance(mfid, inp["n_bins"], inp["ell"], inp["delta_ell"], inp["f_sky"],
+                                  inp["sigma_e"] ** 2 / inp["n_gal_sr"], inp["cov_V"], inp["cov_rank_amp"])
+        data = mfid + np.linalg.cholesky(cov) @ inp["noise_eps"]
+        return data, cov
+
+    def _create(self, precision, max_batch, data, cov, tmpl):
+        inp = self.inp
+        keep = []   # arrays that must stay alive during ns_problem_create
+        desc = L.ProblemDesc()
+        desc.kind = L.NS_KIND_SHEAR if self.kind == "shear" else L.NS_KIND_GAUSS
+        desc.precision = L.NS_PREC[precision]
+        pri = inp["priors"]
+        desc.n_params = len(pri)
+        parr = (L.Prior * len(pri))(*[L.Prior(L.NS_PRIOR[k], a, b) for (k, a, b) in pri])
+        keep.append(parr)
+        desc.priors = parr
+        desc.max_batch = max_batch
+        if self.kind == "gauss":
+            desc.gauss = L.GaussDesc(inp["mu"], inp["sigma"])
+        else:
+            D = len(inp["noise_eps"])
+            desc.n_data = D
+            for arr, field in ((data, "data"), (cov, "cov")):
+                a = np.ascontiguousarray(arr, dtype=np.float64)
+                keep.append(a)
+                setattr(desc, field, _dptr(a))
+            Ws = [np.ascontiguousarray(w, dtype=np.float64) for w in inp["emu_W"]]
+            bs = [np.ascontiguousarray(b, dtype=np.float64) for b in inp["emu_b"]]
+            keep += Ws + bs
+            nl = len(Ws)
+            dims = np.array([Ws[0].shape[1]] + [w.shape[0] for w in Ws], dtype=np.int32)
+            Wp = (C.POINTER(C.c_double) * nl)(*[_dptr(w) for w in Ws])
+            bp = (C.POINTER(C.c_double) * nl)(*[_dptr(b) for b in bs])
+            ins = np.ascontiguousarray(inp["emu_inputs"], dtype=np.int32)
+            cen = np.ascontiguousarray(inp["emu_in_center"], dtype=np.float64)
+            scl = np.ascontiguousarray(inp["emu_in_scale"], dtype=np.float64)
+            mu = np.ascontiguousarray(inp["emu_out_mu"], dtype=np.float64)
+            keep += [dims, Wp, bp, ins, cen, scl, mu]
+            e = desc.emu
+            e.n_layers = nl
+            e.dims = _iptr(dims)
+            e.W = C.cast(Wp, C.POINTER(C.POINTER(C.c_double)))
+            e.b = C.cast(bp, C.POINTER(C.POINTER(C.c_double)))
+            e.activation = 0
+            e.inputs = _iptr(ins)
+            e.in_center = _dptr(cen)
+            e.in_scale = _dptr(scl)
+            e.out_mu = _dptr(mu)
+            e.out_sigma = float(inp["emu_out_sigma"])
+            s = desc.shear
+            nzm = np.ascontiguousarray(inp["nz_mean"], dtype=np.float64)
+            nzs = np.ascontiguousarray(inp["nz_sigma"], dtype=np.float64)
+            ell = np.ascontiguousarray(inp["ell"], dtype=np.float64)
+            keep += [nzm, nzs, ell]
+            s.n_bins = inp["n_bins"]
+            s.nz_mean = _dptr(nzm)
+            s.nz_sigma = _dptr(nzs)
+            s.n_ell = len(ell)
+            s.ell = _dptr(ell)
+            s.n_k = inp["n_k"]
+            s.lnk_min = inp["lnk_min"]
+            s.lnk_max = inp["lnk_max"]
+            s.n_z = inp["n_z"]
+            s.z_max = inp["z_max"]
+            s.n_z_emu = inp["n_z_emu"]
+            s.n_chi = inp["n_chi"]
+            s.a_min = inp["a_min"]
+            s.ia_pivot = inp["ia_pivot"]
+            s.c1rho = inp["c1rho"]
+            s.n_tmpl = inp["n_tmpl"]
+            if inp["n_tmpl"]:
+                t = np.ascontiguousarray(tmpl, dtype=np.float64)
+                keep.append(t)
+                s.tmpl = _dptr(t)
+        h = C.c_void_p()
+        L.check(self.lib.ns_problem_create(C.byref(desc), C.byref(h)), "ns_problem_create")
+        self._h = h
+
+    def _free(self):
+        if self._h:
+            self.lib.ns_problem_free(self._h)
+            self._h = C.c_void_p()
+
+    def close(self):
+        self._free()
+
+    def __del__(self):
+        try:
+            self._free()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # ------------------------------------------------------------ calls
+    def loglike(self, theta: torch.Tensor, stream=None) -> torch.Tensor:
+        """log L at physical free parameters theta (B x d, float64, CUDA)."""
+        theta = _require_cuda(theta, "theta")
+        B = theta.shape[0]
+        out = torch.empty(B, dtype=torch.float64, device=theta.device)
+        L.check(self.lib.loglike_batch(self._h, C.c_void_p(theta.data_ptr()), B, C.c_void_p(out.data_ptr()),
+                                       _stream(stream)), "loglike_batch")
+        return out
+
+    def model(self, theta: torch.Tensor, stream=None) -> torch.Tensor:
+        theta = _require_cuda(theta, "theta")
+        B = theta.shape[0]
+        D = len(self.inp["noise_eps"])
+        out = torch.empty((B, D), dtype=torch.float64, device=theta.device)
+        L.check(self.lib.ns_model_batch(self._h, C.c_void_p(theta.data_ptr()), B, C.c_void_p(out.data_ptr()),
+                                        _stream(stream)), "ns_model_batch")
+        return out
+
+    def emulator(self, theta: torch.Tensor, stream=None) -> torch.Tensor:
+        """Raw emulator output (B x n_out) in the problem precision, returned as float64."""
+        theta = _require_cuda(theta, "theta")
+        B = theta.shape[0]
+        n_out = int(np.asarray(self.inp["emu_out_mu"]).size)
+        out = torch.empty((B, n_out), dtype=torch.float64, device=theta.device)
+        L.check(self.lib.ns_emulator_batch(self._h, C.c_void_p(theta.data_ptr()), B, C.c_void_p(out.data_ptr()),
+                                           _stream(stream)), "ns_emulator_batch")
+        return out
+
+    def prior_transform(self, cube: torch.Tensor, stream=None) -> torch.Tensor:
+        cube = _require_cuda(cube, "cube")
+        out = torch.empty_like(cube)
+        L.check(self.lib.ns_prior_transform(self._h, C.c_void_p(cube.data_ptr()), cube.shape[0],
+                                            C.c_void_p(out.data_ptr()), _stream(stream)), "ns_prior_transform")
+        return out
+
+    def loglike_grad(self, theta: torch.Tensor, stream=None):
+        theta = _require_cuda(theta, "theta")
+        B = theta.shape[0]
+        out = torch.empty(B, dtype=torch.float64, device=theta.device)
+        g = torch.empty_like(theta)
+        L.check(self.lib.loglike_grad_batch(self._h, C.c_void_p(theta.data_ptr()), B, C.c_void_p(out.data_ptr()),
+                                            C.c_void_p(g.data_ptr()), _stream(stream)), "loglike_grad_batch")
+        return out, g
+
+
+@dataclass
+class RunStatus:
+    iterations: int
+    evaluations: int
+    rounds: int
+    converged: bool
+    status_bits: int
+    logZ: float
+    logX: float
+    lstar: float
+
+
+class NestedRun:
+    """One nested-sampling run on a problem (ns_init / ns_step / ns_evidence)."""
+
+    def __init__(self, problem: Problem, n_live: int, n_delete: int, repeats: int | None = None,
+                 tol: float = 1e-3, seed: int = 3, width: float = 1.0, step_cap: int = 100,
+                 ridge: float = 1e-12, rounds_per_sync: int = 0, stream=None):
+        self.lib = problem.lib
+        self.problem = problem
+        self.n_live, self.n_delete, self.d = n_live, n_delete, problem.d
+        cfg = L.Config(n_live, n_delete, 0 if repeats is None else repeats, tol, seed, width, step_cap, ridge,
+                       rounds_per_sync)
+        self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        L.check(self.lib.ns_init(problem.handle, C.byref(cfg), _stream(self._stream_obj), C.byref(h)), "ns_init")
+        self._h = h
+
+    @classmethod
+    def from_config(cls, problem, sc, **kw):
+        return cls(problem, sc.n_live, sc.n_delete, sc.repeats, sc.tol, sc.seed, sc.width, sc.step_cap, sc.ridge, **kw)
+
+    def step(self, n_iters: int = 1) -> RunStatus:
+        st = L.Status()
+        L.check(self.lib.ns_step(self._h, n_iters, C.byref(st)), "ns_step")
+        return RunStatus(st.iterations, st.evaluations, st.rounds, bool(st.converged), st.status_bits,
+                         st.logZ, st.logX, st.lstar)
+
+    def run(self, max_iters: int = 10 ** 9, chunk: int = 64) -> RunStatus:
+        st = self.step(0)
+        while not st.converged and st.iterations < max_iters:
+            st = self.step(min(chunk, max_iters - st.iterations))
+        return st
+
+    def evidence(self, n_replays: int = 200) -> dict:
+        lz, err, lx, H = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+        nd = C.c_longlong()
+        L.check(self.lib.ns_evidence(self._h, n_replays, C.byref(lz), C.byref(err), C.byref(lx), C.byref(H),
+                                     C.byref(nd)), "ns_evidence")
+        return dict(logZ=lz.value, logZ_err=err.value, logX=lx.value, H=H.value, n_dead=nd.value)
+
+    def live_points(self):
+        x = np.empty((self.n_live, self.d))
+        lg = np.empty(self.n_live)
+        L.check(self.lib.ns_live_points(self._h, x.ctypes.data_as(C.c_void_p), lg.ctypes.data_as(C.c_void_p)),
+                "ns_live_points")
+        return x, lg
+
+    def dead_points(self, max_out: int = 1 << 40):
+        st = self.step(0)
+        n = min(max_out, st.iterations * self.n_delete)
+        x = np.empty((max(n, 1), self.d))
+        lg = np.empty(max(n, 1))
+        nl = np.empty(max(n, 1), dtype=np.int32)
+        cnt = C.c_longlong()
+        L.check(self.lib.ns_dead_points(self._h, n, x.ctypes.data_as(C.c_void_p), lg.ctypes.data_as(C.c_void_p),
+                                        nl.ctypes.data_as(C.c_void_p), C.byref(cnt)), "ns_dead_points")
+        m = cnt.value
+        return x[:m], lg[:m], nl[:m]
+
+    def last_iteration(self):
+        k = self.n_delete
+        lstar = C.c_double()
+        dele = np.empty(k, dtype=np.int32)
+        sta = np.empty(k, dtype=np.int32)
+        ev = np.empty(k, dtype=np.int32)
+        L.check(self.lib.ns_last_iteration(self._h, C.byref(lstar), dele.ctypes.data_as(C.c_void_p),
+                                           sta.ctypes.data_as(C.c_void_p), ev.ctypes.data_as(C.c_void_p)),
+                "ns_last_iteration")
+        return lstar.value, dele, sta, ev
+
+    STAGES = {"off": 0, "projection": 1, "emu_out": 2, "chi2": 3, "emu_hidden": 4}
+
+    def profile_stage(self, stage: str):
+        L.check(self.lib.ns_profile_stage(self._h, self.STAGES[stage]), "ns_profile_stage")
+
+    def profile_read(self):
+        ms, n, rows = C.c_double(), C.c_longlong(), C.c_longlong()
+        L.check(self.lib.ns_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(rows)), "ns_profile_read")
+        return dict(ms=ms.value, launches=n.value, rows=rows.value)
+
+    def close(self):
+        if self._h:
+            self.lib.ns_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,330 @@
+// BF16 x BF16 -> FP32 GEMM on the 5th-generation tensor cores (tcgen05) with
+// TMA-fed shared-memory staging, used for the emulator's hidden and output
+// layers (the dense contractions of the likelihood, Sec. 2.5 / App. A).
+//
+//   C[M x N] = epi(A[M x K] W[N x K]^T + bias)
+//   A: activations, row-major (K-major), bf16;  W: weights [N][K], bf16.
+//   epi 0: tanh, stored bf16 (next layer's A);  epi 1: mu + sigma * v, FP32.
+//
+// One CTA computes a 128 x BN tile.  Warp 0 (one lane) issues TMA loads of
+// 128 x 64 and BN x 64 bf16 boxes (128-byte swizzle) into a STAGES-deep ring
+// guarded by full/empty mbarriers; warp 1 (one lane) issues
+// tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = BN, K = 16) into a TMEM
+// accumulator and releases ring slots with tcgen05.commit; warp 2 owns the
+// TMEM allocation.  All four warps then drain TMEM with tcgen05.ld (warp w
+// reads lanes 32w..32w+31 = tile rows), apply the epilogue and store.
+// Every wait is bounded: on timeout the CTA records an error and leaves.
+#include <cudaTypedefs.h>
+
+#include "likelihood.cuh"
+
+namespace gpuns {
+
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BK = 64;                 // 64 bf16 = 128 bytes = one swizzle row
+constexpr uint64_t kWaitNs = 500ull * 1000 * 1000;   // 0.5 s: a correct tile takes microseconds
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait (wall-clock limit kWaitNs); false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 0 && globaltimer() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar), "r"(x), "r"(y) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+    d |= (uint64_t)1 << 46;                          // version
+    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+template <int BN>
+__host__ __device__ constexpr uint32_t instr_desc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        :: "r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of one TMEM lane per thread.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float tanh_fast(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <int BN>
+struct Cfg {
+    static constexpr int STAGES = (BN >= 256) ? 3 : 4;
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+};
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(128, 1)
+k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          const float* __restrict__ bias, const float* __restrict__ out_mu, float out_sigma,
+          void* __restrict__ Cout, const int* __restrict__ nrows, int N, int K, int* __restrict__ err) {
+    using C = Cfg<BN>;
+    const int M = *nrows;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    if (m0 >= M) return;
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - raw);
+    const uint32_t bar0 = base + C::STAGES * C::STAGE_BYTES;        // full[s], empty[s], accf
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (C::STAGES + s); };
+    const uint32_t accf = bar0 + 8u * (2 * C::STAGES);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + C::STAGES * C::STAGE_BYTES + 8 * (2 * C::STAGES + 1));
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int s = 0; s < C::STAGES; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), 1); }
+        mbar_init(accf, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tmem_slot)), "r"(C::TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int nk = (K + BK - 1) / BK;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % C::STAGES;
+            if (kb >= C::STAGES && !mbar_wait(empty_bar(s), ((kb / C::STAGES) & 1) ^ 1)) { s_fail = 1; break; }
+            const uint32_t sa = base + s * C::STAGE_BYTES;
+            mbar_expect_tx(full_bar(s), C::STAGE_BYTES);
+            tma_load_2d(sa, &tmA, full_bar(s), kb * BK, m0);
+            tma_load_2d(sa + C::A_BYTES, &tmB, full_bar(s), kb * BK, n0);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = instr_desc<BN>();
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % C::STAGES;
+            if (!mbar_wait(full_bar(s), (kb / C::STAGES) & 1)) { s_fail = 1; break; }
+            fence_after();
+            const uint32_t sa = base + s * C::STAGE_BYTES;
+            const uint64_t da = smem_desc(sa), db = smem_desc(sa + C::A_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+                mma_bf16(tmem, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0);
+            mma_commit(empty_bar(s));
+        }
+        mma_commit(accf);
+    }
+    __syncwarp();
+
+    // Epilogue: all four warps.
+    const bool ok = mbar_wait(accf, 0);
+    fence_after();
+    __syncwarp();
+    if (ok && !s_fail) {
+        const int row = m0 + warp * 32 + lane;
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+            float v[32];
+            tmem_ld32(lane_addr + c * 32, v);
+            const int col0 = n0 + c * 32;
+            if (row >= M || col0 >= N) continue;
+            if (EPI == 0) {
+                __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(Cout) + (size_t)row * N + col0;
+                if (col0 + 32 <= N && (N % 8) == 0) {
+                    uint32_t pk[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float a0 = tanh_fast(v[2 * j] + __ldg(bias + col0 + 2 * j));
+                        const float a1 = tanh_fast(v[2 * j + 1] + __ldg(bias + col0 + 2 * j + 1));
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, a1);
+                        pk[j] = *reinterpret_cast<uint32_t*>(&h2);
+                    }
+                    uint4* o4 = reinterpret_cast<uint4*>(out);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) o4[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                } else {
+                    for (int j = 0; j < 32 && col0 + j < N; ++j)
+                        out[j] = __float2bfloat16_rn(tanh_fast(v[j] + bias[col0 + j]));
+                }
+            } else {
+                float* out = reinterpret_cast<float*>(Cout) + (size_t)row * N + col0;
+                if (col0 + 32 <= N && (N % 4) == 0) {
+                    float4* o4 = reinterpret_cast<float4*>(out);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        float4 r;
+                        r.x = __ldg(out_mu + col0 + 4 * q + 0) + out_sigma * (v[4 * q + 0] + __ldg(bias + col0 + 4 * q + 0));
+                        r.y = __ldg(out_mu + col0 + 4 * q + 1) + out_sigma * (v[4 * q + 1] + __ldg(bias + col0 + 4 * q + 1));
+                        r.z = __ldg(out_mu + col0 + 4 * q + 2) + out_sigma * (v[4 * q + 2] + __ldg(bias + col0 + 4 * q + 2));
+                        r.w = __ldg(out_mu + col0 + 4 * q + 3) + out_sigma * (v[4 * q + 3] + __ldg(bias + col0 + 4 * q + 3));
+                        o4[q] = r;
+                    }
+                } else {
+                    for (int j = 0; j < 32 && col0 + j < N; ++j)
+                        out[j] = out_mu[col0 + j] + out_sigma * (v[j] + bias[col0 + j]);
+                }
+            }
+        }
+    }
+    if ((!ok || s_fail) && threadIdx.x == 0 && err) atomicOr(err, NS_BIT_TIMEOUT);
+    fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(C::TMEM_COLS) : "memory");
+    }
+}
+
+template <int BN>
+static int launch_bn(const CUtensorMap* tmA, const CUtensorMap* tmB, const float* bias, const float* mu,
+                     float sigma, void* Cout, const int* nrows, int grid_rows, int N, int K, int epi, int* err,
+                     cudaStream_t st) {
+    using C = Cfg<BN>;
+    static bool attr = false;
+    if (!attr) {
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<BN, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<BN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+        attr = true;
+    }
+    dim3 grid((N + BN - 1) / BN, (grid_rows + BM - 1) / BM);
+    if (epi == 0) k_gemm_tc<BN, 0><<<grid, 128, C::SMEM, st>>>(*tmA, *tmB, bias, mu, sigma, Cout, nrows, N, K, err);
+    else k_gemm_tc<BN, 1><<<grid, 128, C::SMEM, st>>>(*tmA, *tmB, bias, mu, sigma, Cout, nrows, N, K, err);
+    NS_CUDA_TRY(cudaGetLastError());
+    return NS_OK;
+}
+
+}  // namespace tc
+
+int launch_gemm_tc(const CUtensorMap* tmA, const CUtensorMap* tmB, int tile_n, const float* bias,
+                   const float* out_mu, float out_sigma, void* C, const int* d_nrows, int grid_rows, int N, int K,
+                   int epi, int* d_err, cudaStream_t st) {
+    if (grid_rows <= 0) return NS_OK;
+    switch (tile_n) {
+        case 64: return tc::launch_bn<64>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, d_err, st);
+        case 128: return tc::launch_bn<128>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, d_err, st);
+        case 256: return tc::launch_bn<256>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, d_err, st);
+        default: return NS_EINVAL;
+    }
+}
+
+int gemm_tc_supported(int N, int K) {
+    // rows of A and W must be 16-byte aligned for TMA (K multiple of 8 bf16)
+    return (K % 8 == 0) && (N % 8 == 0) && K >= 16;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D bf16 tensor map over rows x K (row-major), box = box_rows x 64, 128-byte swizzle.
+int make_tensor_map_bf16(CUtensorMap* tm, const void* base, int rows, int K, int box_rows) {
+    auto enc = get_encode();
+    if (!enc) return NS_ECUDA;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (K * 2) % 16) return NS_EINVAL;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? NS_OK : NS_EINVAL;
+}
+
+}  // namespace gpuns

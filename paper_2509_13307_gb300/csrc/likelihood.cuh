@@ -1,0 +1,117 @@
+// Internal interfaces of the likelihood stages (not part of the C ABI).
+#pragma once
+
+#include <cuda.h>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gpuns {
+
+// Device-side description of the shear model (App. A), built at problem creation.
+struct ShearParams {
+    int n_params, nb, n_pairs, n_ell, n_k, n_z, N, D, n_tmpl;
+    double lnk_min, lnk_max, dlnk, ia_pivot, c1rho;
+    const double* a;      // N   scale factor at chi nodes (node 0: a = 1)
+    const double* lna;    // N
+    const double* z;      // N
+    const double* wa;     // N   trapezoid weights in a
+    const int* zrow;      // 4N  z-taps of the P table at each node (ghosts folded)
+    const double* zw;     // 4N
+    const double* lnell;  // n_ell  ln(ell + 1/2)
+    const double* nz_mean;
+    const double* nz_sigma;
+    const int* pi;        // n_pairs
+    const int* pj;
+    const double* data;   // D
+    const double* tmpl;   // D x n_tmpl
+};
+
+struct Workspace {
+    int cap = 0;
+    int* d_nrows = nullptr;       // device row count used by every stage
+    double* theta_full = nullptr; // cap x P
+    void* act[2] = {nullptr, nullptr};
+    void* table = nullptr;        // cap x n_out (emulator output)
+    void* table_fine = nullptr;   // cap x n_z*n_k (coarse-z emulators)
+    void* resid = nullptr;        // cap x D
+    double* logL = nullptr;       // cap
+    // tcgen05 tensor maps (BF16 precision): A operand of layer l >= 1 and its output
+    std::vector<CUtensorMap> tmA;
+    std::vector<void*> owned;
+};
+
+}  // namespace gpuns
+
+struct ns_problem {
+    int kind = 0, precision = 0, P = 0, d = 0, D = 0, max_batch = 0;
+    std::vector<ns_prior> priors;
+    int* d_pkind = nullptr;
+    double* d_pa = nullptr;
+    double* d_pb = nullptr;
+    int* d_free_of_full = nullptr;   // P: free index or -1
+    // gauss
+    double g_mu = 0.5, g_sigma = 0.05;
+    // emulator
+    int n_layers = 0;
+    std::vector<int> dims;
+    std::vector<void*> d_W;          // per layer, compute dtype (layer 0: FP64 or FP32)
+    std::vector<void*> d_b;          // per layer, FP64 (FP64 mode) else FP32
+    std::vector<CUtensorMap> tmB;    // BF16: weight tensor maps for layers >= 1
+    std::vector<int> tile_n;         // BF16: N tile per layer (autotuned)
+    int* d_inputs = nullptr;
+    double* d_in_center = nullptr;
+    double* d_in_scale = nullptr;
+    void* d_out_mu = nullptr;        // FP64 or FP32
+    double out_sigma = 1.0;
+    int hidden_max = 0;
+    // shear
+    gpuns::ShearParams sp{};
+    int n_z_emu = 0;
+    int* d_zi_row = nullptr;         // n_z x 4 coarse -> fine z taps
+    double* d_zi_w = nullptr;
+    // chi2
+    double c0 = 0.0;
+    double* d_LinvT64 = nullptr;     // D x D: LinvT[b*D + a] = (L^-1)[a][b]
+    float* d_LinvT32 = nullptr;
+    std::vector<void*> owned;
+    gpuns::Workspace ws;             // scratch of loglike_batch / ns_model_batch
+};
+
+namespace gpuns {
+
+int workspace_create(const ns_problem* p, int cap, Workspace* ws);
+void workspace_free(Workspace* ws);
+
+// Full likelihood pipeline on rows [0, *d_nrows) of ws->theta_full; grid_rows
+// bounds the row count for grid sizing.  Writes logL_out (FP64) or, when
+// model_out != nullptr, the shear model vectors (FP64, rows x D) instead.
+// Optional probe around one likelihood stage: events recorded on the launch
+// stream before/after it and the stage's row count copied to pinned memory.
+enum ProbeStage { PROBE_NONE = 0, PROBE_PROJECTION = 1, PROBE_EMU_OUT = 2, PROBE_CHI2 = 3, PROBE_EMU_HIDDEN = 4 };
+struct StageProbe {
+    int stage = PROBE_NONE;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int* h_rows = nullptr;   // pinned
+};
+
+int run_likelihood(const ns_problem* p, Workspace* ws, int grid_rows,
+                   double* logL_out, double* model_out, cudaStream_t st, const StageProbe* probe = nullptr);
+
+// Emulator stage only; writes the raw emulator output as FP64 (rows x n_out).
+int run_emulator_only(const ns_problem* p, Workspace* ws, int grid_rows, double* out, cudaStream_t st);
+
+// Prior transform into the workspace: cube (rows x d) -> theta_full.
+int launch_cube_to_theta(const ns_problem* p, Workspace* ws, const double* cube, int grid_rows,
+                         cudaStream_t st);
+
+// BF16 tcgen05 GEMM: C[M x N] = epi(A[M x K] * W[N x K]^T + bias), M = *d_nrows.
+// epi 0: tanh -> bf16 C (ldc = N); epi 1: mu + sigma * v -> fp32 C.
+int launch_gemm_tc(const CUtensorMap* tmA, const CUtensorMap* tmB, int tile_n,
+                   const float* bias, const float* out_mu, float out_sigma,
+                   void* C, const int* d_nrows, int grid_rows, int N, int K, int epi,
+                   int* d_err, cudaStream_t st);
+int make_tensor_map_bf16(CUtensorMap* tm, const void* base, int rows, int K, int box_rows);
+int gemm_tc_supported(int N, int K);
+
+}  // namespace gpuns

@@ -1,0 +1,827 @@
+// Batched nested slice sampling on the GPU (Sec. 2.1-2.2 of arXiv:2509.13307).
+//
+// Per iteration:
+//   k_sort_delete   sort live log L by (log L, slot) (bitonic, one block), delete
+//                   the k lowest, L* = the k-th, append them to the dead list
+//                   and update log Z / log X / H in FP64 as k sequential
+//                   deletions with n, n-1, ..., n-k+1 live points (Sec. 2.2).
+//   k_live_cov      covariance (ddof 1) of all n live cube points + ridge.
+//   k_cholesky      FP64 Cholesky of that covariance (one block).
+//   k_chains_start  chain c starts at survivor floor(u (n - k)) (Philox START).
+//   rounds          until every chain has made R slice moves: k_slice_advance
+//                   (one warp per chain) consumes the previous proposal's log L,
+//                   runs the hit-and-run slice state machine (Neal 2003:
+//                   stepping out with width w, then shrinkage) through every
+//                   decision that needs no likelihood (points outside the unit
+//                   cube) and emits at most one proposal per chain into a
+//                   compacted batch; the fused likelihood then scores the batch.
+//                   Rounds are launched as a captured CUDA graph.
+//   k_insert        chain c's point replaces the c-th deleted slot; the
+//                   termination test ln(Z + X <L_live>) - ln Z < tol.
+// All random numbers come from Philox4x32-10 with the counter layout shared
+// with the CPU oracle, so both produce the same slice bookkeeping.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "likelihood.cuh"
+
+namespace gpuns {
+
+enum Phase : int { PH_NEWMOVE = 0, PH_LEFT = 1, PH_RIGHT = 2, PH_SHRINK = 3, PH_DONE = 4 };
+
+struct Scalars {
+    double logZ, logX, H, lstar;
+    long long n_dead, iter, evals;
+    int status, n_active, batch, converged;
+};
+
+struct RunDev {
+    int n, k, d, R, cap_steps;
+    double width, tol;
+    unsigned long long seed;
+    double* live_x;
+    double* live_L;
+    int* order;
+    int* deleted;
+    int* starts;
+    double* chol;
+    double* cov;
+    double* ch_x;
+    double* ch_u;
+    double* ch_L;
+    double* ch_l;
+    double* ch_r;
+    double* ch_t;
+    int* ch_phase;
+    int* ch_move;
+    int* ch_step;
+    int* ch_evals;
+    int* ch_row;
+    double* prop;         // proposals (cap x d), cube coordinates
+    const double* logL;   // likelihood output per proposal row
+    Scalars* sc;
+    double* dead_x;
+    double* dead_L;
+    int* dead_n;
+};
+
+__device__ inline double lse2(double a, double b) {
+    if (a == -INFINITY) return b;
+    if (b == -INFINITY) return a;
+    const double m = fmax(a, b);
+    return m + log(exp(a - m) + exp(b - m));
+}
+
+// Skilling's incremental update for one deletion with nl live points.
+__device__ inline void evidence_add(double& logZ, double& logX, double& H, double L, int nl) {
+    const double logw = logX + log(-expm1(-1.0 / nl));
+    const double z_new = lse2(logZ, L + logw);
+    double h = 0.0;
+    if (z_new != -INFINITY) {
+        h = (L > -INFINITY) ? exp(logw + L - z_new) * L : 0.0;
+        if (logZ > -INFINITY) h += exp(logZ - z_new) * (H + logZ);
+        h -= z_new;
+    }
+    H = h;
+    logZ = z_new;
+    logX -= 1.0 / nl;
+}
+
+// ------------------------------------------------------------------ init
+__global__ void k_init_points(int n, int d, unsigned long long seed, double* __restrict__ prop) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int nch = (d + 1) / 2;
+    for (int j = 0; j < nch; ++j) {
+        Draw2 u = philox_uniforms(seed, P_INIT, j, 0, i, 0);
+        prop[(size_t)i * d + 2 * j] = u.a;
+        if (2 * j + 1 < d) prop[(size_t)i * d + 2 * j + 1] = u.b;
+    }
+}
+
+__global__ void k_init_finish(RunDev r, const double* __restrict__ logL) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < r.n) {
+        double v = logL[i];
+        if (!isfinite(v)) { v = -INFINITY; atomicOr(&r.sc->status, NS_BIT_NONFINITE); }
+        r.live_L[i] = v;
+        for (int j = 0; j < r.d; ++j) r.live_x[(size_t)i * r.d + j] = r.prop[(size_t)i * r.d + j];
+    }
+    if (i == 0) {
+        r.sc->logZ = -INFINITY; r.sc->logX = 0.0; r.sc->H = 0.0; r.sc->lstar = -INFINITY;
+        r.sc->n_dead = 0; r.sc->iter = 0; r.sc->evals = r.n;
+        r.sc->n_active = 0; r.sc->batch = 0; r.sc->converged = 0;
+    }
+}
+
+// ------------------------------------------------------------------ sort / delete
+// Bitonic sort of (logL, slot) ascending; n_pad power of two <= 4096.
+__device__ inline bool key_less(double a, int ia, double b, int ib) {
+    return (a < b) || (a == b && ia < ib);
+}
+
+__global__ void __launch_bounds__(1024) k_sort_delete(RunDev r, int n_pad, int delete_k, int do_dead) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* key = reinterpret_cast<double*>(smem_raw);
+    int* idx = reinterpret_cast<int*>(key + n_pad);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < n_pad; i += nt) {
+        key[i] = (i < r.n) ? r.live_L[i] : INFINITY;
+        idx[i] = i;
+    }
+    __syncthreads();
+    for (int size = 2; size <= n_pad; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < n_pad; i += nt) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = ((i & size) == 0);
+                    const bool gt = key_less(key[j], idx[j], key[i], idx[i]);
+                    if (gt == up) {
+                        const double tk = key[i]; key[i] = key[j]; key[j] = tk;
+                        const int ti = idx[i]; idx[i] = idx[j]; idx[j] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < r.n; i += nt) r.order[i] = idx[i];
+    if (!do_dead) return;
+    const int k = delete_k;
+    const long long base = r.sc->n_dead;
+    for (int j = tid; j < k; j += nt) {
+        r.deleted[j] = idx[j];
+        r.dead_L[base + j] = key[j];
+        r.dead_n[base + j] = r.n - j;
+    }
+    for (int t = tid; t < k * r.d; t += nt) {
+        const int j = t / r.d, c = t % r.d;
+        r.dead_x[(base + j) * r.d + c] = r.live_x[(size_t)idx[j] * r.d + c];
+    }
+    if (tid == 0) {
+        double logZ = r.sc->logZ, logX = r.sc->logX, H = r.sc->H;
+        for (int j = 0; j < k; ++j) evidence_add(logZ, logX, H, key[j], r.n - j);
+        r.sc->logZ = logZ; r.sc->logX = logX; r.sc->H = H;
+        r.sc->lstar = key[k - 1];
+        r.sc->n_dead = base + k;
+    }
+}
+
+// ------------------------------------------------------------------ covariance + Cholesky
+__global__ void k_live_cov(RunDev r, double ridge) {
+    const int i = blockIdx.x;           // row of the covariance
+    const int d = r.d, n = r.n;
+    __shared__ double mean[64];
+    __shared__ double red[32];
+    for (int c = threadIdx.x; c < d; c += blockDim.x) mean[c] = 0.0;
+    __syncthreads();
+    // means (each block recomputes them; n x d is small)
+    for (int c = 0; c < d; ++c) {
+        double s = 0.0;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) s += r.live_x[(size_t)p * d + c];
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) mean[c] = s / n;
+        __syncthreads();
+    }
+    for (int j = 0; j <= i; ++j) {
+        double s = 0.0;
+        for (int p = threadIdx.x; p < n; p += blockDim.x)
+            s += (r.live_x[(size_t)p * d + i] - mean[i]) * (r.live_x[(size_t)p * d + j] - mean[j]);
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) {
+            double v = s / (n - 1);
+            if (j == i) v += ridge;
+            r.cov[i * d + j] = v;
+            r.cov[j * d + i] = v;
+        }
+    }
+}
+
+__global__ void k_cholesky(RunDev r) {
+    const int d = r.d;
+    __shared__ double A[64 * 64];
+    __shared__ double red[32];
+    __shared__ int bad;
+    for (int t = threadIdx.x; t < d * d; t += blockDim.x) A[t] = r.cov[t];
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < d; ++j) {
+        double s = 0.0;
+        for (int q = threadIdx.x; q < j; q += blockDim.x) s += A[j * d + q] * A[j * d + q];
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) {
+            const double v = A[j * d + j] - s;
+            if (!(v > 0.0)) bad = 1;
+            A[j * d + j] = sqrt(fmax(v, 1e-300));
+        }
+        __syncthreads();
+        const double ljj = A[j * d + j];
+        for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) {
+            double t = A[i * d + j];
+            for (int q = 0; q < j; ++q) t -= A[i * d + q] * A[j * d + q];
+            A[i * d + j] = t / ljj;
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < d * d; t += blockDim.x) {
+        const int i = t / d, j = t % d;
+        r.chol[t] = (j <= i) ? A[t] : 0.0;
+    }
+    if (threadIdx.x == 0 && bad) atomicOr(&r.sc->status, NS_BIT_NONFINITE);
+}
+
+// ------------------------------------------------------------------ chains
+__global__ void k_chains_start(RunDev r) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int it = (int)r.sc->iter;
+    if (c < r.k) {
+        const Draw2 u = philox_uniforms(r.seed, P_START, 0, (uint32_t)it, (uint32_t)c, 0);
+        const int s = r.order[r.k + (int)floor(u.a * (double)(r.n - r.k))];
+        r.starts[c] = s;
+        for (int j = 0; j < r.d; ++j) r.ch_x[(size_t)c * r.d + j] = r.live_x[(size_t)s * r.d + j];
+        r.ch_L[c] = r.live_L[s];
+        r.ch_phase[c] = PH_NEWMOVE;
+        r.ch_move[c] = 0;
+        r.ch_step[c] = 0;
+        r.ch_evals[c] = 0;
+        r.ch_row[c] = -1;
+    }
+    if (c == 0) { r.sc->n_active = r.k; r.sc->batch = 0; }
+}
+
+// One warp per chain; lanes own dimensions lane and lane + 32.
+__global__ void __launch_bounds__(256) k_slice_advance(RunDev r) {
+    __shared__ double zs[8][64];
+    const int wib = threadIdx.x >> 5;
+    const int c = blockIdx.x * 8 + wib;
+    const int lane = threadIdx.x & 31;
+    if (c >= r.k) return;
+    int phase = r.ch_phase[c];
+    if (phase == PH_DONE) return;
+    const int d = r.d;
+    const int it = (int)r.sc->iter;
+    const double w = r.width;
+    const double lstar = r.sc->lstar;
+    double* x = r.ch_x + (size_t)c * d;
+    double* u = r.ch_u + (size_t)c * d;
+    const bool has0 = lane < d, has1 = lane + 32 < d;
+    double x0 = has0 ? x[lane] : 0.0, x1 = has1 ? x[lane + 32] : 0.0;
+    double u0v = has0 ? u[lane] : 0.0, u1v = has1 ? u[lane + 32] : 0.0;
+    int move = r.ch_move[c], step = r.ch_step[c], row = r.ch_row[c], evals = r.ch_evals[c];
+    double l = r.ch_l[c], rr = r.ch_r[c], t = r.ch_t[c], chL = r.ch_L[c];
+    int flags = 0;
+
+    if (row >= 0) {
+        const double v = r.logL[row];
+        const bool fin = isfinite(v);
+        if (!fin) flags |= NS_BIT_NONFINITE;
+        const bool inside = fin && (v > lstar);
+        if (phase == PH_LEFT) {
+            if (inside) { l -= w; ++step; } else { phase = PH_RIGHT; step = 0; }
+        } else if (phase == PH_RIGHT) {
+            if (inside) { rr += w; ++step; } else { phase = PH_SHRINK; step = 0; }
+        } else if (phase == PH_SHRINK) {
+            if (inside) {
+                x0 = __dadd_rn(x0, __dmul_rn(t, u0v));
+                x1 = __dadd_rn(x1, __dmul_rn(t, u1v));
+                chL = v;
+                ++move;
+                phase = PH_NEWMOVE;
+            } else {
+                if (t < 0.0) l = t; else rr = t;
+                ++step;
+            }
+        }
+        row = -1;
+    }
+    for (int guard = 0; guard < 4 * r.cap_steps + 8; ++guard) {
+        if (phase == PH_NEWMOVE) {
+            if (move >= r.R) { phase = PH_DONE; break; }
+            // direction: z ~ N(0, I) (Box-Muller on Philox DIR chunks), u = L_Sigma z / |z|
+            const int nch = (d + 1) / 2;
+            double z0 = 0.0, z1 = 0.0;
+            if (lane < nch) {
+                const Draw2 g = philox_uniforms(r.seed, P_DIR, lane, (uint32_t)it, (uint32_t)c, (uint32_t)move);
+                const double rad = sqrt(-2.0 * log(g.a));
+                const double ang = 6.283185307179586 * g.b;
+                z0 = rad * cos(ang);
+                z1 = rad * sin(ang);
+                zs[wib][2 * lane] = z0;
+                if (2 * lane + 1 < d) zs[wib][2 * lane + 1] = z1; else z1 = 0.0;
+            }
+            const double nrm = sqrt(warp_sum(z0 * z0 + z1 * z1));
+            __syncwarp();
+            double a0 = 0.0, a1 = 0.0;
+            if (has0) for (int b = 0; b <= lane; ++b) a0 += r.chol[lane * d + b] * (zs[wib][b] / nrm);
+            if (has1) for (int b = 0; b <= lane + 32; ++b) a1 += r.chol[(lane + 32) * d + b] * (zs[wib][b] / nrm);
+            __syncwarp();
+            u0v = a0; u1v = a1;
+            const double s0 = philox_uniforms(r.seed, P_STEPOUT, 0, (uint32_t)it, (uint32_t)c, (uint32_t)move).a;
+            l = __dmul_rn(-w, s0);
+            rr = l + w;
+            phase = PH_LEFT;
+            step = 0;
+            continue;
+        }
+        if (phase == PH_LEFT || phase == PH_RIGHT) {
+            if (step >= r.cap_steps) {
+                flags |= NS_BIT_SLICE_CAP;
+                if (phase == PH_LEFT) phase = PH_RIGHT; else phase = PH_SHRINK;
+                step = 0;
+                continue;
+            }
+            const double s = (phase == PH_LEFT) ? l : rr;
+            const double y0 = __dadd_rn(x0, __dmul_rn(s, u0v)), y1 = __dadd_rn(x1, __dmul_rn(s, u1v));
+            const bool inc = (!has0 || (y0 > 0.0 && y0 < 1.0)) && (!has1 || (y1 > 0.0 && y1 < 1.0));
+            if (!__all_sync(0xffffffffu, inc)) {
+                if (phase == PH_LEFT) phase = PH_RIGHT; else phase = PH_SHRINK;
+                step = 0;
+                continue;
+            }
+            int rw = 0;
+            if (lane == 0) rw = atomicAdd(&r.sc->batch, 1);
+            row = __shfl_sync(0xffffffffu, rw, 0);
+            if (has0) r.prop[(size_t)row * d + lane] = y0;
+            if (has1) r.prop[(size_t)row * d + lane + 32] = y1;
+            ++evals;
+            break;
+        }
+        if (phase == PH_SHRINK) {
+            if (step >= r.cap_steps) {
+                flags |= NS_BIT_SLICE_CAP;
+                ++move;
+                phase = PH_NEWMOVE;
+                continue;
+            }
+            const double us = philox_uniforms(r.seed, P_SHRINK, (uint32_t)step, (uint32_t)it, (uint32_t)c,
+                                              (uint32_t)move).a;
+            t = __dadd_rn(l, __dmul_rn(us, __dsub_rn(rr, l)));
+            const double y0 = __dadd_rn(x0, __dmul_rn(t, u0v)), y1 = __dadd_rn(x1, __dmul_rn(t, u1v));
+            const bool inc = (!has0 || (y0 > 0.0 && y0 < 1.0)) && (!has1 || (y1 > 0.0 && y1 < 1.0));
+            if (!__all_sync(0xffffffffu, inc)) {
+                if (t < 0.0) l = t; else rr = t;
+                ++step;
+                continue;
+            }
+            int rw = 0;
+            if (lane == 0) rw = atomicAdd(&r.sc->batch, 1);
+            row = __shfl_sync(0xffffffffu, rw, 0);
+            if (has0) r.prop[(size_t)row * d + lane] = y0;
+            if (has1) r.prop[(size_t)row * d + lane + 32] = y1;
+            ++evals;
+            break;
+        }
+        break;
+    }
+    if (has0) { x[lane] = x0; u[lane] = u0v; }
+    if (has1) { x[lane + 32] = x1; u[lane + 32] = u1v; }
+    if (lane == 0) {
+        r.ch_phase[c] = phase; r.ch_move[c] = move; r.ch_step[c] = step; r.ch_row[c] = row;
+        r.ch_evals[c] = evals; r.ch_l[c] = l; r.ch_r[c] = rr; r.ch_t[c] = t; r.ch_L[c] = chL;
+        if (flags) atomicOr(&r.sc->status, flags);
+        if (phase == PH_DONE) atomicSub(&r.sc->n_active, 1);
+    }
+}
+
+__global__ void k_insert(RunDev r) {
+    __shared__ double red[32];
+    __shared__ long long ev_sh;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) ev_sh = 0;
+    __syncthreads();
+    long long ev = 0;
+    for (int c = tid; c < r.k; c += nt) {
+        const int s = r.deleted[c];
+        r.live_L[s] = r.ch_L[c];
+        for (int j = 0; j < r.d; ++j) r.live_x[(size_t)s * r.d + j] = r.ch_x[(size_t)c * r.d + j];
+        ev += r.ch_evals[c];
+    }
+    atomicAdd((unsigned long long*)&ev_sh, (unsigned long long)ev);
+    __syncthreads();
+    // termination: ln(Z + X mean(L_live)) - ln Z < tol
+    // block max
+    double mx = -INFINITY;
+    for (int i = tid; i < r.n; i += nt) mx = fmax(mx, r.live_L[i]);
+    mx = warp_max(mx);
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    if (tid < 32) {
+        double v = (tid < (nt + 31) / 32) ? red[tid] : -INFINITY;
+        v = warp_max(v);
+        if (tid == 0) red[0] = v;
+    }
+    __syncthreads();
+    mx = red[0];
+    __syncthreads();
+    double s = 0.0;
+    if (mx > -INFINITY)
+        for (int i = tid; i < r.n; i += nt) s += exp(r.live_L[i] - mx);
+    s = block_sum(s, red);
+    if (tid == 0) {
+        r.sc->evals += ev_sh;
+        r.sc->iter += 1;
+        const double lz = r.sc->logZ;
+        const double lzl = (mx > -INFINITY) ? r.sc->logX + mx + log(s) - log((double)r.n) : -INFINITY;
+        r.sc->converged = (lz > -INFINITY) && (lse2(lz, lzl) - lz < r.tol);
+    }
+}
+
+// ------------------------------------------------------------------ evidence
+__global__ void k_final_evidence(RunDev r, double* out /* logZ, logX, H */) {
+    if (threadIdx.x != 0) return;
+    double logZ = r.sc->logZ, logX = r.sc->logX, H = r.sc->H;
+    for (int j = 0; j < r.n; ++j) evidence_add(logZ, logX, H, r.live_L[r.order[j]], r.n - j);
+    out[0] = logZ; out[1] = logX; out[2] = H;
+}
+
+// One block per replay: ln t_i = ln(U_{s,i}) / n_i; ln Z_s = LSE_i(L_i + ln X_{i-1} + ln(1 - t_i)).
+__global__ void __launch_bounds__(256) k_err_replays(RunDev r, long long n_dead, double* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* red = reinterpret_cast<double*>(smem_raw);     // 64
+    const int s = blockIdx.x;
+    const long long N = n_dead + r.n;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const long long chunk = (N + nt - 1) / nt;
+    const long long lo = min(N, (long long)tid * chunk), hi = min(N, lo + chunk);
+    auto Lof = [&](long long i) -> double { return (i < n_dead) ? r.dead_L[i] : r.live_L[r.order[i - n_dead]]; };
+    auto nof = [&](long long i) -> int { return (i < n_dead) ? r.dead_n[i] : (int)(r.n - (i - n_dead)); };
+    auto lnt = [&](long long i) -> double {
+        const Draw2 u = philox_uniforms(r.seed, P_ERR, 0, (uint32_t)s, (uint32_t)i, 0);
+        return log(u.a) / nof(i);
+    };
+    double tot = 0.0;
+    for (long long i = lo; i < hi; ++i) tot += lnt(i);
+    // exclusive scan of per-thread totals
+    double* sc = red;   // 32 + 32
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    double inc = tot;
+    for (int o = 1; o < 32; o <<= 1) { double y = __shfl_up_sync(0xffffffffu, inc, o); if (lane >= o) inc += y; }
+    if (lane == 31) sc[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        double v = (lane < nw) ? sc[lane] : 0.0, vi = v;
+        for (int o = 1; o < 32; o <<= 1) { double y = __shfl_up_sync(0xffffffffu, vi, o); if (lane >= o) vi += y; }
+        if (lane < nw) sc[lane] = vi - v;
+    }
+    __syncthreads();
+    double logX = sc[wid] + inc - tot;   // ln X before my first point
+    __syncthreads();
+    double mx = -INFINITY, acc = 0.0;    // running LSE
+    for (long long i = lo; i < hi; ++i) {
+        const double lt = lnt(i);
+        const double term = Lof(i) + logX + log(-expm1(lt));
+        if (term > mx) { acc = acc * exp(mx - term) + 1.0; mx = term; }
+        else if (term > -INFINITY) acc += exp(term - mx);
+        logX += lt;
+    }
+    // combine (mx, acc) across the block
+    double gmx = warp_max(mx);
+    if (lane == 0) red[32 + wid] = gmx;
+    __syncthreads();
+    if (wid == 0) {
+        double v = (lane < nw) ? red[32 + lane] : -INFINITY;
+        v = warp_max(v);
+        if (lane == 0) red[32] = v;
+    }
+    __syncthreads();
+    gmx = red[32];
+    __syncthreads();
+    double part = (mx > -INFINITY) ? acc * exp(mx - gmx) : 0.0;
+    part = block_sum(part, red);
+    if (tid == 0) out[s] = gmx + log(part);
+}
+
+}  // namespace gpuns
+
+using namespace gpuns;
+
+struct ns_run {
+    const ns_problem* p = nullptr;
+    ns_config cfg{};
+    int n = 0, k = 0, d = 0, R = 0, n_pad = 0;
+    cudaStream_t st = nullptr;
+    Workspace ws;
+    RunDev rd{};
+    Scalars* sc = nullptr;
+    Scalars* h_sc = nullptr;          // pinned mirror
+    long long dead_cap = 0;
+    std::vector<void*> owned;
+    cudaStream_t cap_st = nullptr;    // private stream used only to capture the round graph
+    cudaGraphExec_t graph = nullptr;
+    int graph_rounds = 0;
+    long long rounds = 0;
+    int last_valid = 0;
+    StageProbe probe;                 // optional timing of one stage in round 0 of each graph launch
+    double prof_ms = 0.0;
+    long long prof_launches = 0, prof_rows = 0;
+};
+
+static int run_alloc(ns_run* r, size_t bytes, void** p) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) return NS_ENOMEM;
+    r->owned.push_back(*p);
+    return NS_OK;
+}
+
+static int grow_dead(ns_run* r, long long need) {
+    if (need <= r->dead_cap) return NS_OK;
+    long long cap = std::max(need, 2 * r->dead_cap + 4 * (long long)r->n);
+    double *x, *L;
+    int* nl;
+    if (cudaMalloc(&x, sizeof(double) * cap * r->d) != cudaSuccess) return NS_ENOMEM;
+    if (cudaMalloc(&L, sizeof(double) * cap) != cudaSuccess) { cudaFree(x); return NS_ENOMEM; }
+    if (cudaMalloc(&nl, sizeof(int) * cap) != cudaSuccess) { cudaFree(x); cudaFree(L); return NS_ENOMEM; }
+    NS_CUDA_TRY(cudaStreamSynchronize(r->st));
+    const long long used = r->h_sc->n_dead;
+    if (r->rd.dead_x && used > 0) {
+        NS_CUDA_TRY(cudaMemcpy(x, r->rd.dead_x, sizeof(double) * used * r->d, cudaMemcpyDeviceToDevice));
+        NS_CUDA_TRY(cudaMemcpy(L, r->rd.dead_L, sizeof(double) * used, cudaMemcpyDeviceToDevice));
+        NS_CUDA_TRY(cudaMemcpy(nl, r->rd.dead_n, sizeof(int) * used, cudaMemcpyDeviceToDevice));
+    }
+    cudaFree(r->rd.dead_x); cudaFree(r->rd.dead_L); cudaFree(r->rd.dead_n);
+    r->rd.dead_x = x; r->rd.dead_L = L; r->rd.dead_n = nl;
+    r->dead_cap = cap;
+    if (r->graph) { cudaGraphExecDestroy(r->graph); r->graph = nullptr; }
+    return NS_OK;
+}
+
+static int sync_scalars(ns_run* r) {
+    NS_CUDA_TRY(cudaMemcpyAsync(r->h_sc, r->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, r->st));
+    NS_CUDA_TRY(cudaStreamSynchronize(r->st));
+    return NS_OK;
+}
+
+static int launch_round(ns_run* r, cudaStream_t st, const StageProbe* probe) {
+    NS_CUDA_TRY(cudaMemsetAsync(&r->sc->batch, 0, sizeof(int), st));
+    k_slice_advance<<<(r->k + 7) / 8, 256, 0, st>>>(r->rd);
+    NS_CUDA_TRY(cudaGetLastError());
+    NS_TRY(launch_cube_to_theta(r->p, &r->ws, r->rd.prop, r->k, st));
+    return run_likelihood(r->p, &r->ws, r->k, r->ws.logL, nullptr, st, probe);
+}
+
+static int build_graph(ns_run* r, int rounds) {
+    if (r->graph) { cudaGraphExecDestroy(r->graph); r->graph = nullptr; }
+    cudaGraph_t g;
+    if (!r->cap_st) NS_CUDA_TRY(cudaStreamCreateWithFlags(&r->cap_st, cudaStreamNonBlocking));
+    NS_CUDA_TRY(cudaStreamBeginCapture(r->cap_st, cudaStreamCaptureModeThreadLocal));
+    int s = NS_OK;
+    for (int i = 0; i < rounds && s == NS_OK; ++i)
+        s = launch_round(r, r->cap_st, (i == 0 && r->probe.stage != PROBE_NONE) ? &r->probe : nullptr);
+    cudaError_t e = cudaStreamEndCapture(r->cap_st, &g);
+    if (s != NS_OK) { if (e == cudaSuccess) cudaGraphDestroy(g); return s; }
+    NS_CUDA_TRY(e);
+    e = cudaGraphInstantiate(&r->graph, g, 0);
+    cudaGraphDestroy(g);
+    NS_CUDA_TRY(e);
+    r->graph_rounds = rounds;
+    return NS_OK;
+}
+
+static void run_release(ns_run* r) {
+    if (!r) return;
+    if (r->graph) cudaGraphExecDestroy(r->graph);
+    if (r->cap_st) cudaStreamDestroy(r->cap_st);
+    if (r->probe.ev0) cudaEventDestroy(r->probe.ev0);
+    if (r->probe.ev1) cudaEventDestroy(r->probe.ev1);
+    if (r->probe.h_rows) cudaFreeHost(r->probe.h_rows);
+    cudaFree(r->rd.dead_x); cudaFree(r->rd.dead_L); cudaFree(r->rd.dead_n);
+    for (void* q : r->owned) cudaFree(q);
+    if (r->h_sc) cudaFreeHost(r->h_sc);
+    workspace_free(&r->ws);
+    delete r;
+}
+
+extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, ns_run** out) {
+    if (!p || !cfg || !out) return NS_EINVAL;
+    *out = nullptr;
+    const int n = cfg->n_live, k = cfg->n_delete, d = p->d;
+    if (n < 2 || n > 4096 || k < 1 || k >= n || d < 1 || d > 64) return NS_EINVAL;
+    if (!(cfg->width > 0) || cfg->step_cap < 1 || !(cfg->tol > 0)) return NS_EINVAL;
+    ns_run* r = new (std::nothrow) ns_run();
+    if (!r) return NS_ENOMEM;
+    auto fail = [&](int s) { run_release(r); return s; };
+    r->p = p;
+    r->cfg = *cfg;
+    r->n = n; r->k = k; r->d = d;
+    r->R = cfg->repeats > 0 ? cfg->repeats : 5 * d;
+    r->st = (cudaStream_t)stream;
+    r->n_pad = 1;
+    while (r->n_pad < n) r->n_pad <<= 1;
+    int s;
+    const int cap = std::max(n, k);
+    if ((s = workspace_create(p, cap, &r->ws))) return fail(s);
+    RunDev& rd = r->rd;
+    rd.n = n; rd.k = k; rd.d = d; rd.R = r->R; rd.cap_steps = cfg->step_cap;
+    rd.width = cfg->width; rd.tol = cfg->tol; rd.seed = cfg->seed;
+    void* v;
+#define RA(field, bytes) do { if ((s = run_alloc(r, (bytes), &v))) return fail(s); rd.field = (decltype(rd.field))v; } while (0)
+    RA(live_x, sizeof(double) * n * d);
+    RA(live_L, sizeof(double) * n);
+    RA(order, sizeof(int) * r->n_pad);
+    RA(deleted, sizeof(int) * k);
+    RA(starts, sizeof(int) * k);
+    RA(chol, sizeof(double) * d * d);
+    RA(cov, sizeof(double) * d * d);
+    RA(ch_x, sizeof(double) * k * d);
+    RA(ch_u, sizeof(double) * k * d);
+    RA(ch_L, sizeof(double) * k);
+    RA(ch_l, sizeof(double) * k);
+    RA(ch_r, sizeof(double) * k);
+    RA(ch_t, sizeof(double) * k);
+    RA(ch_phase, sizeof(int) * k);
+    RA(ch_move, sizeof(int) * k);
+    RA(ch_step, sizeof(int) * k);
+    RA(ch_evals, sizeof(int) * k);
+    RA(ch_row, sizeof(int) * k);
+    RA(prop, sizeof(double) * cap * d);
+    RA(sc, sizeof(Scalars));
+#undef RA
+    rd.logL = r->ws.logL;
+    r->sc = rd.sc;
+    if (cudaMallocHost(&r->h_sc, sizeof(Scalars)) != cudaSuccess) return fail(NS_ENOMEM);
+    std::memset(r->h_sc, 0, sizeof(Scalars));
+    if (cudaMemsetAsync(rd.ch_phase, 0xff, sizeof(int) * k, r->st) != cudaSuccess) return fail(NS_ECUDA);
+    if (cudaMemsetAsync(rd.sc, 0, sizeof(Scalars), r->st) != cudaSuccess) return fail(NS_ECUDA);
+    if ((s = grow_dead(r, 16LL * k + n))) return fail(s);
+    // the workspace row count is the round's batch counter
+    r->ws.d_nrows = &rd.sc->batch;
+    // initial live points
+    k_init_points<<<(n + 127) / 128, 128, 0, r->st>>>(n, d, cfg->seed, rd.prop);
+    k_set_int<<<1, 1, 0, r->st>>>(&rd.sc->batch, n);
+    if (cudaGetLastError() != cudaSuccess) return fail(NS_ECUDA);
+    if ((s = launch_cube_to_theta(p, &r->ws, rd.prop, n, r->st))) return fail(s);
+    if ((s = run_likelihood(p, &r->ws, n, r->ws.logL, nullptr, r->st))) return fail(s);
+    k_init_finish<<<(n + 127) / 128, 128, 0, r->st>>>(rd, r->ws.logL);
+    if (cudaGetLastError() != cudaSuccess) return fail(NS_ECUDA);
+    if ((s = sync_scalars(r))) return fail(s);
+    *out = r;
+    return NS_OK;
+}
+
+static int rounds_per_sync(const ns_run* r) {
+    if (r->cfg.rounds_per_sync > 0) return r->cfg.rounds_per_sync;
+    return 16;
+}
+
+static int one_iteration(ns_run* r) {
+    RunDev& rd = r->rd;
+    cudaStream_t st = r->st;
+    NS_TRY(grow_dead(r, r->h_sc->n_dead + r->k));
+    const size_t sm = (size_t)r->n_pad * (sizeof(double) + sizeof(int));
+    k_sort_delete<<<1, 1024, sm, st>>>(rd, r->n_pad, r->k, 1);
+    NS_CUDA_TRY(cudaGetLastError());
+    k_live_cov<<<r->d, 256, 0, st>>>(rd, r->cfg.ridge);
+    k_cholesky<<<1, 128, 0, st>>>(rd);
+    k_chains_start<<<(r->k + 127) / 128, 128, 0, st>>>(rd);
+    NS_CUDA_TRY(cudaGetLastError());
+    const int R = rounds_per_sync(r);
+    if (!r->graph || r->graph_rounds != R) NS_TRY(build_graph(r, R));
+    // a chain needs at most repeats * (2 step caps + shrink cap) evaluations
+    const long long max_rounds = (long long)r->R * (3LL * r->cfg.step_cap + 2) + 8;
+    for (long long done = 0;; done += R) {
+        NS_CUDA_TRY(cudaGraphLaunch(r->graph, st));
+        r->rounds += R;
+        NS_TRY(sync_scalars(r));
+        if (r->probe.stage != PROBE_NONE && *r->probe.h_rows > 0) {
+            float ms = 0.f;
+            NS_CUDA_TRY(cudaEventElapsedTime(&ms, r->probe.ev0, r->probe.ev1));
+            r->prof_ms += ms;
+            r->prof_launches += 1;
+            r->prof_rows += *r->probe.h_rows;
+        }
+        if (r->h_sc->n_active == 0) break;
+        if (done > max_rounds) { r->h_sc->status |= NS_BIT_TIMEOUT; return NS_ETIMEOUT; }
+    }
+    k_insert<<<1, 1024, 0, st>>>(rd);
+    NS_CUDA_TRY(cudaGetLastError());
+    NS_TRY(sync_scalars(r));
+    r->last_valid = 1;
+    return NS_OK;
+}
+
+extern "C" int ns_step(ns_run* r, int n_iters, ns_status* st) {
+    if (!r || n_iters < 0) return NS_EINVAL;
+    int s = NS_OK;
+    for (int i = 0; i < n_iters; ++i) {
+        if (r->h_sc->converged) break;
+        if ((s = one_iteration(r)) != NS_OK) break;
+    }
+    if (st) {
+        st->iterations = r->h_sc->iter;
+        st->evaluations = r->h_sc->evals;
+        st->rounds = r->rounds;
+        st->converged = r->h_sc->converged;
+        st->status_bits = r->h_sc->status;
+        st->logZ = r->h_sc->logZ;
+        st->logX = r->h_sc->logX;
+        st->lstar = r->h_sc->lstar;
+    }
+    return s;
+}
+
+extern "C" int ns_evidence(const ns_run* rc, int n_replays, double* logZ, double* logZ_err, double* logX,
+                           double* H, long long* n_dead) {
+    if (!rc) return NS_EINVAL;
+    ns_run* r = const_cast<ns_run*>(rc);
+    if (n_replays <= 0) n_replays = 200;
+    cudaStream_t st = r->st;
+    NS_TRY(sync_scalars(r));
+    const size_t sm = (size_t)r->n_pad * (sizeof(double) + sizeof(int));
+    k_sort_delete<<<1, 1024, sm, st>>>(r->rd, r->n_pad, 0, 0);   // order of the live set only
+    NS_CUDA_TRY(cudaGetLastError());
+    double* dout;
+    if (cudaMalloc(&dout, sizeof(double) * (3 + n_replays)) != cudaSuccess) return NS_ENOMEM;
+    k_final_evidence<<<1, 32, 0, st>>>(r->rd, dout);
+    k_err_replays<<<n_replays, 256, 128 * sizeof(double), st>>>(r->rd, r->h_sc->n_dead, dout + 3);
+    std::vector<double> h(3 + n_replays);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), dout, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(dout);
+    if (e != cudaSuccess) { ns_set_last_cuda_error(e, "ns_evidence", __FILE__, __LINE__); return NS_ECUDA; }
+    double mean = 0.0;
+    for (int i = 0; i < n_replays; ++i) mean += h[3 + i];
+    mean /= n_replays;
+    double var = 0.0;
+    for (int i = 0; i < n_replays; ++i) var += (h[3 + i] - mean) * (h[3 + i] - mean);
+    var /= std::max(1, n_replays - 1);
+    if (logZ) *logZ = h[0];
+    if (logX) *logX = h[1];
+    if (H) *H = h[2];
+    if (logZ_err) *logZ_err = std::sqrt(var);
+    if (n_dead) *n_dead = r->h_sc->n_dead + r->n;
+    return NS_OK;
+}
+
+extern "C" int ns_live_points(const ns_run* r, double* x, double* logL) {
+    if (!r) return NS_EINVAL;
+    NS_CUDA_TRY(cudaStreamSynchronize(r->st));
+    if (x) NS_CUDA_TRY(cudaMemcpy(x, r->rd.live_x, sizeof(double) * r->n * r->d, cudaMemcpyDeviceToHost));
+    if (logL) NS_CUDA_TRY(cudaMemcpy(logL, r->rd.live_L, sizeof(double) * r->n, cudaMemcpyDeviceToHost));
+    return NS_OK;
+}
+
+extern "C" int ns_dead_points(const ns_run* r, long long max_out, double* x, double* logL, int* nl,
+                              long long* n_out) {
+    if (!r || max_out < 0) return NS_EINVAL;
+    NS_CUDA_TRY(cudaStreamSynchronize(r->st));
+    const long long m = std::min(max_out, r->h_sc->n_dead);
+    if (m > 0) {
+        if (x) NS_CUDA_TRY(cudaMemcpy(x, r->rd.dead_x, sizeof(double) * m * r->d, cudaMemcpyDeviceToHost));
+        if (logL) NS_CUDA_TRY(cudaMemcpy(logL, r->rd.dead_L, sizeof(double) * m, cudaMemcpyDeviceToHost));
+        if (nl) NS_CUDA_TRY(cudaMemcpy(nl, r->rd.dead_n, sizeof(int) * m, cudaMemcpyDeviceToHost));
+    }
+    if (n_out) *n_out = m;
+    return NS_OK;
+}
+
+extern "C" int ns_last_iteration(const ns_run* r, double* lstar, int* deleted, int* starts, int* evals) {
+    if (!r || !r->last_valid) return NS_EINVAL;
+    NS_CUDA_TRY(cudaStreamSynchronize(r->st));
+    if (lstar) *lstar = r->h_sc->lstar;
+    if (deleted) NS_CUDA_TRY(cudaMemcpy(deleted, r->rd.deleted, sizeof(int) * r->k, cudaMemcpyDeviceToHost));
+    if (starts) NS_CUDA_TRY(cudaMemcpy(starts, r->rd.starts, sizeof(int) * r->k, cudaMemcpyDeviceToHost));
+    if (evals) NS_CUDA_TRY(cudaMemcpy(evals, r->rd.ch_evals, sizeof(int) * r->k, cudaMemcpyDeviceToHost));
+    return NS_OK;
+}
+
+extern "C" int ns_profile_stage(ns_run* r, int stage) {
+    if (!r || stage < PROBE_NONE || stage > PROBE_EMU_HIDDEN) return NS_EINVAL;
+    NS_CUDA_TRY(cudaStreamSynchronize(r->st));
+    if (stage != PROBE_NONE && !r->probe.ev0) {
+        NS_CUDA_TRY(cudaEventCreate(&r->probe.ev0));
+        NS_CUDA_TRY(cudaEventCreate(&r->probe.ev1));
+        if (cudaMallocHost(&r->probe.h_rows, sizeof(int)) != cudaSuccess) return NS_ENOMEM;
+        *r->probe.h_rows = 0;
+    }
+    r->probe.stage = stage;
+    r->prof_ms = 0.0;
+    r->prof_launches = 0;
+    r->prof_rows = 0;
+    if (r->graph) { cudaGraphExecDestroy(r->graph); r->graph = nullptr; }
+    return NS_OK;
+}
+
+extern "C" int ns_profile_read(const ns_run* r, double* total_ms, long long* launches, long long* rows) {
+    if (!r) return NS_EINVAL;
+    if (total_ms) *total_ms = r->prof_ms;
+    if (launches) *launches = r->prof_launches;
+    if (rows) *rows = r->prof_rows;
+    return NS_OK;
+}
+
+extern "C" int ns_free(ns_run* r) {
+    if (!r) return NS_EINVAL;
+    cudaStreamSynchronize(r->st);
+    run_release(r);
+    return NS_OK;
+}
+
+extern "C" int loglike_grad_batch(const ns_problem* p, const double* theta_dev, int B, double* logL_dev,
+                                  double* grad_dev, void* stream) {
+    (void)p; (void)theta_dev; (void)B; (void)logL_dev; (void)grad_dev; (void)stream;
+    return NS_ENOTSUP;
+}

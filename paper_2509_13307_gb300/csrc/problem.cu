@@ -1,0 +1,447 @@
+// Problem construction and the batched-likelihood entry points of the C ABI.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "likelihood.cuh"
+
+static thread_local char g_last_err[512] = {0};
+
+void ns_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+    snprintf(g_last_err, sizeof(g_last_err), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+}
+
+extern "C" const char* ns_strerror(int code) {
+    switch (code) {
+        case NS_OK: return "ok";
+        case NS_EINVAL: return "invalid argument";
+        case NS_ECUDA: return g_last_err[0] ? g_last_err : "CUDA error";
+        case NS_ENOMEM: return "out of memory";
+        case NS_ETIMEOUT: return "device wait timed out";
+        case NS_ESLICE: return "slice step cap reached";
+        case NS_ENONFINITE: return "non-finite log-likelihood";
+        case NS_ENOTSUP: return "not supported";
+        default: return "unknown status";
+    }
+}
+
+namespace gpuns {
+
+template <typename T>
+static int upload(const T* host, size_t n, T** dev, std::vector<void*>& owned) {
+    *dev = nullptr;
+    if (n == 0) return NS_OK;
+    if (cudaMalloc((void**)dev, n * sizeof(T)) != cudaSuccess) return NS_ENOMEM;
+    owned.push_back(*dev);
+    NS_CUDA_TRY(cudaMemcpy(*dev, host, n * sizeof(T), cudaMemcpyHostToDevice));
+    return NS_OK;
+}
+
+static int dalloc(size_t bytes, void** dev, std::vector<void*>& owned) {
+    *dev = nullptr;
+    if (bytes == 0) return NS_OK;
+    if (cudaMalloc(dev, bytes) != cudaSuccess) return NS_ENOMEM;
+    owned.push_back(*dev);
+    return NS_OK;
+}
+
+static uint16_t f32_to_bf16_rne(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);   // inf / nan
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+// Catmull-Rom taps of coordinate s on a uniform grid [lo, lo + (n-1) step], ghosts folded.
+static void cr_taps(double s, double lo, double step, int n, int idx[4], double w[4]) {
+    const double u = (s - lo) / step;
+    int i = (int)std::floor(u);
+    if (i < 0) i = 0;
+    if (i > n - 2) i = n - 2;
+    double wi[4];
+    catmull_rom<double>(u - i, wi);
+    fold_taps<double>(i, n, wi, idx, w);
+}
+
+// Host FP64 Cholesky C = L L^T (lower, row-major) and L^-1; false if not SPD.
+static bool cholesky_inverse(const double* C, int D, std::vector<double>& L, std::vector<double>& Linv) {
+    L.assign((size_t)D * D, 0.0);
+    for (int j = 0; j < D; ++j) {
+        double s = C[(size_t)j * D + j];
+        for (int k = 0; k < j; ++k) s -= L[(size_t)j * D + k] * L[(size_t)j * D + k];
+        if (!(s > 0.0)) return false;
+        const double ljj = std::sqrt(s);
+        L[(size_t)j * D + j] = ljj;
+        for (int i = j + 1; i < D; ++i) {
+            double t = C[(size_t)i * D + j];
+            for (int k = 0; k < j; ++k) t -= L[(size_t)i * D + k] * L[(size_t)j * D + k];
+            L[(size_t)i * D + j] = t / ljj;
+        }
+    }
+    Linv.assign((size_t)D * D, 0.0);
+    for (int c = 0; c < D; ++c) {          // solve L x = e_c
+        for (int i = c; i < D; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) s -= L[(size_t)i * D + k] * Linv[(size_t)k * D + c];
+            Linv[(size_t)i * D + c] = s / L[(size_t)i * D + i];
+        }
+    }
+    return true;
+}
+
+int workspace_create(const ns_problem* p, int cap, Workspace* ws) {
+    ws->cap = cap;
+    void* v;
+    NS_TRY(dalloc(sizeof(int), &v, ws->owned));
+    ws->d_nrows = (int*)v;
+    NS_TRY(dalloc(sizeof(double) * (size_t)cap * p->P, &v, ws->owned));
+    ws->theta_full = (double*)v;
+    NS_TRY(dalloc(sizeof(double) * (size_t)cap, &v, ws->owned));
+    ws->logL = (double*)v;
+    if (p->kind != NS_KIND_SHEAR) return NS_OK;
+    const int elt = (p->precision == NS_PREC_FP64) ? 8 : (p->precision == NS_PREC_FP32 ? 4 : 2);
+    const int tab_elt = (p->precision == NS_PREC_FP64) ? 8 : 4;
+    const int rows_pad = ((cap + 127) / 128) * 128;
+    for (int i = 0; i < 2; ++i) {
+        NS_TRY(dalloc((size_t)elt * rows_pad * p->hidden_max, &v, ws->owned));
+        ws->act[i] = v;
+        NS_CUDA_TRY(cudaMemset(v, 0, (size_t)elt * rows_pad * p->hidden_max));
+    }
+    const int n_out = p->dims.back();
+    NS_TRY(dalloc((size_t)tab_elt * cap * n_out, &v, ws->owned));
+    ws->table = v;
+    if (p->n_z_emu != p->sp.n_z) {
+        NS_TRY(dalloc((size_t)tab_elt * cap * p->sp.n_z * p->sp.n_k, &v, ws->owned));
+        ws->table_fine = v;
+    }
+    NS_TRY(dalloc((size_t)tab_elt * cap * p->sp.D, &v, ws->owned));
+    ws->resid = v;
+    if (p->precision == NS_PREC_BF16 || p->precision == NS_PREC_BF16_F64CHI2) {
+        ws->tmA.resize(p->n_layers);
+        int cur = 0;
+        for (int l = 1; l < p->n_layers; ++l) {
+            NS_TRY(make_tensor_map_bf16(&ws->tmA[l], ws->act[cur], rows_pad, p->dims[l], 128));
+            cur ^= 1;
+        }
+    }
+    return NS_OK;
+}
+
+void workspace_free(Workspace* ws) {
+    for (void* q : ws->owned) cudaFree(q);
+    ws->owned.clear();
+}
+
+static int validate_desc(const ns_problem_desc* d) {
+    if (!d || !d->priors || d->n_params < 1 || d->n_params > 256 || d->max_batch < 1) return NS_EINVAL;
+    if (d->precision < 0 || d->precision > NS_PREC_BF16_F64CHI2) return NS_EINVAL;
+    int nfree = 0;
+    for (int i = 0; i < d->n_params; ++i) {
+        const ns_prior& q = d->priors[i];
+        if (q.kind == NS_PRIOR_FIXED) continue;
+        if (q.kind == NS_PRIOR_UNIFORM && !(q.b > q.a)) return NS_EINVAL;
+        if (q.kind == NS_PRIOR_GAUSS && !(q.b > 0)) return NS_EINVAL;
+        if (q.kind != NS_PRIOR_UNIFORM && q.kind != NS_PRIOR_GAUSS) return NS_EINVAL;
+        ++nfree;
+    }
+    if (nfree < 1 || nfree > 64) return NS_EINVAL;
+    if (d->kind == NS_KIND_GAUSS) return (d->gauss.sigma > 0) ? NS_OK : NS_EINVAL;
+    if (d->kind != NS_KIND_SHEAR) return NS_EINVAL;
+    const ns_shear_desc& s = d->shear;
+    const ns_emulator_desc& e = d->emu;
+    if (s.n_bins < 1 || s.n_ell < 1 || s.n_k < 4 || s.n_z < 4 || s.n_chi < 3 || !(s.a_min > 0 && s.a_min < 1))
+        return NS_EINVAL;
+    if (s.n_z_emu < 4 || s.n_z_emu > s.n_z) return NS_EINVAL;
+    if (d->n_params != 11 + 2 * s.n_bins + s.n_tmpl) return NS_EINVAL;
+    const int D = s.n_bins * (s.n_bins + 1) / 2 * s.n_ell;
+    if (d->n_data != D || !d->data || !d->cov) return NS_EINVAL;
+    if (s.n_tmpl > 0 && !s.tmpl) return NS_EINVAL;
+    if (e.n_layers < 2 || !e.dims || !e.W || !e.b || !e.inputs || !e.in_center || !e.in_scale || !e.out_mu)
+        return NS_EINVAL;
+    if (e.dims[0] < 1 || e.dims[0] > 32) return NS_EINVAL;
+    if (e.dims[e.n_layers] != s.n_k * s.n_z_emu) return NS_EINVAL;
+    for (int j = 0; j < e.dims[0]; ++j)
+        if (e.inputs[j] < 0 || e.inputs[j] >= d->n_params || !(e.in_scale[j] != 0)) return NS_EINVAL;
+    return NS_OK;
+}
+
+}  // namespace gpuns
+
+using namespace gpuns;
+
+static void problem_release(ns_problem* p) {
+    if (!p) return;
+    workspace_free(&p->ws);
+    for (void* q : p->owned) cudaFree(q);
+    delete p;
+}
+
+extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) {
+    if (!out) return NS_EINVAL;
+    *out = nullptr;
+    NS_TRY(validate_desc(desc));
+    ns_problem* p = new (std::nothrow) ns_problem();
+    if (!p) return NS_ENOMEM;
+    auto fail = [&](int code) { problem_release(p); return code; };
+    p->kind = desc->kind;
+    p->precision = desc->precision;
+    p->P = desc->n_params;
+    p->max_batch = desc->max_batch;
+    p->priors.assign(desc->priors, desc->priors + desc->n_params);
+    {
+        std::vector<int> kind(p->P), fof(p->P);
+        std::vector<double> pa(p->P), pb(p->P);
+        int f = 0;
+        for (int i = 0; i < p->P; ++i) {
+            kind[i] = p->priors[i].kind;
+            pa[i] = p->priors[i].a;
+            pb[i] = p->priors[i].b;
+            fof[i] = (kind[i] == NS_PRIOR_FIXED) ? -1 : f++;
+        }
+        p->d = f;
+        int s;
+        if ((s = upload(kind.data(), kind.size(), &p->d_pkind, p->owned))) return fail(s);
+        if ((s = upload(pa.data(), pa.size(), &p->d_pa, p->owned))) return fail(s);
+        if ((s = upload(pb.data(), pb.size(), &p->d_pb, p->owned))) return fail(s);
+        if ((s = upload(fof.data(), fof.size(), &p->d_free_of_full, p->owned))) return fail(s);
+    }
+    if (p->kind == NS_KIND_GAUSS) {
+        p->g_mu = desc->gauss.mu;
+        p->g_sigma = desc->gauss.sigma;
+        int s = workspace_create(p, p->max_batch, &p->ws);
+        if (s) return fail(s);
+        *out = p;
+        return NS_OK;
+    }
+
+    // ---------------- emulator
+    const ns_emulator_desc& e = desc->emu;
+    const bool bf16 = (p->precision == NS_PREC_BF16 || p->precision == NS_PREC_BF16_F64CHI2);
+    const bool f64 = (p->precision == NS_PREC_FP64);
+    p->n_layers = e.n_layers;
+    p->dims.assign(e.dims, e.dims + e.n_layers + 1);
+    p->hidden_max = 0;
+    for (int l = 1; l < e.n_layers; ++l) p->hidden_max = std::max(p->hidden_max, p->dims[l]);
+    if (bf16) {
+        for (int l = 1; l < e.n_layers; ++l)
+            if (!gemm_tc_supported(p->dims[l + 1], p->dims[l]) && !(l == e.n_layers - 1 && p->dims[l + 1] % 4 == 0 &&
+                                                                   p->dims[l] % 8 == 0))
+                return fail(NS_ENOTSUP);
+    }
+    p->d_W.assign(e.n_layers, nullptr);
+    p->d_b.assign(e.n_layers, nullptr);
+    for (int l = 0; l < e.n_layers; ++l) {
+        const size_t nw = (size_t)p->dims[l + 1] * p->dims[l];
+        const size_t nb = p->dims[l + 1];
+        int s;
+        if (f64) {
+            double* w; double* b;
+            if ((s = upload(e.W[l], nw, &w, p->owned))) return fail(s);
+            if ((s = upload(e.b[l], nb, &b, p->owned))) return fail(s);
+            p->d_W[l] = w; p->d_b[l] = b;
+        } else {
+            std::vector<float> bf(nb);
+            for (size_t i = 0; i < nb; ++i) bf[i] = (float)e.b[l][i];
+            float* b;
+            if ((s = upload(bf.data(), nb, &b, p->owned))) return fail(s);
+            p->d_b[l] = b;
+            if (bf16 && l >= 1) {
+                std::vector<uint16_t> wb(nw);
+                for (size_t i = 0; i < nw; ++i) wb[i] = f32_to_bf16_rne((float)e.W[l][i]);
+                uint16_t* w;
+                if ((s = upload(wb.data(), nw, &w, p->owned))) return fail(s);
+                p->d_W[l] = w;
+            } else {
+                std::vector<float> wf(nw);
+                for (size_t i = 0; i < nw; ++i) wf[i] = (float)e.W[l][i];
+                float* w;
+                if ((s = upload(wf.data(), nw, &w, p->owned))) return fail(s);
+                p->d_W[l] = w;
+            }
+        }
+    }
+    {
+        int s;
+        if ((s = upload(e.inputs, (size_t)p->dims[0], &p->d_inputs, p->owned))) return fail(s);
+        if ((s = upload(e.in_center, (size_t)p->dims[0], &p->d_in_center, p->owned))) return fail(s);
+        if ((s = upload(e.in_scale, (size_t)p->dims[0], &p->d_in_scale, p->owned))) return fail(s);
+        const size_t no = p->dims.back();
+        if (f64) {
+            double* m;
+            if ((s = upload(e.out_mu, no, &m, p->owned))) return fail(s);
+            p->d_out_mu = m;
+        } else {
+            std::vector<float> mf(no);
+            for (size_t i = 0; i < no; ++i) mf[i] = (float)e.out_mu[i];
+            float* m;
+            if ((s = upload(mf.data(), no, &m, p->owned))) return fail(s);
+            p->d_out_mu = m;
+        }
+        p->out_sigma = e.out_sigma;
+    }
+    if (bf16) {
+        p->tmB.resize(e.n_layers);
+        p->tile_n.assign(e.n_layers, 128);
+        for (int l = 1; l < e.n_layers; ++l) {
+            const int N = p->dims[l + 1];
+            const bool last = (l == e.n_layers - 1);
+            int tn = last ? 128 : 64;
+            if (N < tn) tn = 64;
+            p->tile_n[l] = tn;
+            int s = make_tensor_map_bf16(&p->tmB[l], p->d_W[l], N, p->dims[l], tn);
+            if (s) return fail(s);
+        }
+    }
+
+    // ---------------- shear grids and constants
+    const ns_shear_desc& sd = desc->shear;
+    ShearParams& sp = p->sp;
+    sp.n_params = p->P;
+    sp.nb = sd.n_bins;
+    sp.n_pairs = sd.n_bins * (sd.n_bins + 1) / 2;
+    sp.n_ell = sd.n_ell;
+    sp.n_k = sd.n_k;
+    sp.n_z = sd.n_z;
+    sp.N = sd.n_chi;
+    sp.D = desc->n_data;
+    sp.n_tmpl = sd.n_tmpl;
+    sp.lnk_min = sd.lnk_min;
+    sp.lnk_max = sd.lnk_max;
+    sp.dlnk = (sd.lnk_max - sd.lnk_min) / (sd.n_k - 1);
+    sp.ia_pivot = sd.ia_pivot;
+    sp.c1rho = sd.c1rho;
+    p->D = sp.D;
+    p->n_z_emu = sd.n_z_emu;
+    {
+        const int N = sp.N;
+        const double da = (1.0 - sd.a_min) / (N - 1);
+        std::vector<double> a(N), lna(N), z(N), wa(N, da), zw(4 * N);
+        std::vector<int> zrow(4 * N);
+        const double dz = sd.z_max / (sd.n_z - 1);
+        for (int n = 0; n < N; ++n) {
+            a[n] = 1.0 - da * n;
+            lna[n] = std::log(a[n]);
+            z[n] = 1.0 / a[n] - 1.0;
+            cr_taps(z[n], 0.0, dz, sd.n_z, &zrow[4 * n], &zw[4 * n]);
+        }
+        wa[0] *= 0.5;
+        wa[N - 1] *= 0.5;
+        std::vector<double> lnell(sd.n_ell);
+        for (int l = 0; l < sd.n_ell; ++l) lnell[l] = std::log(sd.ell[l] + 0.5);
+        std::vector<int> pi, pj;
+        for (int i = 0; i < sd.n_bins; ++i)
+            for (int j = i; j < sd.n_bins; ++j) { pi.push_back(i); pj.push_back(j); }
+        double *da_, *dlna, *dz_, *dwa, *dzw, *dlnell, *dmu, *dsg, *ddata, *dtm = nullptr;
+        int *dzrow, *dpi, *dpj;
+        int s;
+        if ((s = upload(a.data(), N, &da_, p->owned)) || (s = upload(lna.data(), N, &dlna, p->owned)) ||
+            (s = upload(z.data(), N, &dz_, p->owned)) || (s = upload(wa.data(), N, &dwa, p->owned)) ||
+            (s = upload(zw.data(), 4 * N, &dzw, p->owned)) || (s = upload(zrow.data(), 4 * N, &dzrow, p->owned)) ||
+            (s = upload(lnell.data(), sd.n_ell, &dlnell, p->owned)) ||
+            (s = upload(sd.nz_mean, sd.n_bins, &dmu, p->owned)) || (s = upload(sd.nz_sigma, sd.n_bins, &dsg, p->owned)) ||
+            (s = upload(pi.data(), pi.size(), &dpi, p->owned)) || (s = upload(pj.data(), pj.size(), &dpj, p->owned)) ||
+            (s = upload(desc->data, sp.D, &ddata, p->owned)))
+            return fail(s);
+        if (sd.n_tmpl > 0 && (s = upload(sd.tmpl, (size_t)sp.D * sd.n_tmpl, &dtm, p->owned))) return fail(s);
+        sp.a = da_; sp.lna = dlna; sp.z = dz_; sp.wa = dwa; sp.zw = dzw; sp.zrow = dzrow; sp.lnell = dlnell;
+        sp.nz_mean = dmu; sp.nz_sigma = dsg; sp.pi = dpi; sp.pj = dpj; sp.data = ddata; sp.tmpl = dtm;
+        if (p->n_z_emu != sd.n_z) {
+            std::vector<int> zr(4 * sd.n_z);
+            std::vector<double> zwt(4 * sd.n_z);
+            const double dzc = sd.z_max / (p->n_z_emu - 1);
+            for (int j = 0; j < sd.n_z; ++j)
+                cr_taps(j * dz, 0.0, dzc, p->n_z_emu, &zr[4 * j], &zwt[4 * j]);
+            if ((s = upload(zr.data(), zr.size(), &p->d_zi_row, p->owned)) ||
+                (s = upload(zwt.data(), zwt.size(), &p->d_zi_w, p->owned)))
+                return fail(s);
+        }
+    }
+    // ---------------- Gaussian likelihood: FP64 Cholesky, L^-1, constant
+    {
+        const int D = sp.D;
+        std::vector<double> L, Linv;
+        if (!cholesky_inverse(desc->cov, D, L, Linv)) return fail(NS_EINVAL);
+        double c0 = -0.5 * D * std::log(2.0 * M_PI);
+        for (int a = 0; a < D; ++a) c0 -= std::log(L[(size_t)a * D + a]);
+        p->c0 = c0;
+        std::vector<double> LT((size_t)D * D);
+        std::vector<float> LT32((size_t)D * D);
+        for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b) {
+                LT[(size_t)b * D + a] = Linv[(size_t)a * D + b];
+                LT32[(size_t)b * D + a] = (float)Linv[(size_t)a * D + b];
+            }
+        int s;
+        if ((s = upload(LT.data(), LT.size(), &p->d_LinvT64, p->owned))) return fail(s);
+        if ((s = upload(LT32.data(), LT32.size(), &p->d_LinvT32, p->owned))) return fail(s);
+    }
+    int s = workspace_create(p, p->max_batch, &p->ws);
+    if (s) return fail(s);
+    *out = p;
+    return NS_OK;
+}
+
+extern "C" int ns_problem_free(ns_problem* p) {
+    if (!p) return NS_EINVAL;
+    cudaDeviceSynchronize();
+    problem_release(p);
+    return NS_OK;
+}
+
+extern "C" int ns_problem_dim(const ns_problem* p, int* d) {
+    if (!p || !d) return NS_EINVAL;
+    *d = p->d;
+    return NS_OK;
+}
+
+namespace gpuns {
+int launch_cube_to_free(const ns_problem* p, const double* cube, int B, double* theta, cudaStream_t st);
+int launch_free_to_full(const ns_problem* p, const double* theta, int B, double* theta_full, cudaStream_t st);
+}
+
+extern "C" int ns_prior_transform(const ns_problem* p, const double* cube_dev, int B, double* theta_dev,
+                                  void* stream) {
+    if (!p || B < 0 || B > p->max_batch || (B > 0 && (!cube_dev || !theta_dev))) return NS_EINVAL;
+    if (B == 0) return NS_OK;
+    return launch_cube_to_free(p, cube_dev, B, theta_dev, (cudaStream_t)stream);
+}
+
+static int batch_common(const ns_problem* p, const double* theta_dev, int B, cudaStream_t st) {
+    ns_problem* mp = const_cast<ns_problem*>(p);
+    NS_TRY(launch_free_to_full(p, theta_dev, B, mp->ws.theta_full, st));
+    k_set_int<<<1, 1, 0, st>>>(mp->ws.d_nrows, B);
+    NS_CUDA_TRY(cudaGetLastError());
+    return NS_OK;
+}
+
+extern "C" int loglike_batch(const ns_problem* p, const double* theta_dev, int B, double* logL_dev, void* stream) {
+    if (!p || B < 0 || B > p->max_batch || (B > 0 && (!theta_dev || !logL_dev))) return NS_EINVAL;
+    if (B == 0) return NS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    NS_TRY(batch_common(p, theta_dev, B, st));
+    return run_likelihood(p, const_cast<Workspace*>(&p->ws), B, logL_dev, nullptr, st);
+}
+
+extern "C" int ns_model_batch(const ns_problem* p, const double* theta_dev, int B, double* model_dev, void* stream) {
+    if (!p || p->kind != NS_KIND_SHEAR || B < 0 || B > p->max_batch || (B > 0 && (!theta_dev || !model_dev)))
+        return NS_EINVAL;
+    if (B == 0) return NS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    NS_TRY(batch_common(p, theta_dev, B, st));
+    return run_likelihood(p, const_cast<Workspace*>(&p->ws), B, nullptr, model_dev, st);
+}
+
+extern "C" int ns_emulator_batch(const ns_problem* p, const double* theta_dev, int B, double* out_dev,
+                                 void* stream) {
+    if (!p || p->kind != NS_KIND_SHEAR || B < 0 || B > p->max_batch || (B > 0 && (!theta_dev || !out_dev)))
+        return NS_EINVAL;
+    if (B == 0) return NS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    NS_TRY(batch_common(p, theta_dev, B, st));
+    return run_emulator_only(p, const_cast<Workspace*>(&p->ws), B, out_dev, st);
+}

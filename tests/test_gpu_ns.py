@@ -1,0 +1,132 @@
+"""GPU nested sampler against the CPU oracle on the same Philox streams
+(rows A1-A5, A11): the slice bookkeeping (deleted slots, start slots,
+evaluations per chain) must match exactly; thresholds, live points and the
+evidence accumulators to FP64 round-off."""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as w
+from gpu_helpers import cuda_problem, oracle_for
+from oracle.gauss import GaussOracle
+from oracle.ns import NestedSampler
+
+pytestmark = pytest.mark.gpu
+
+
+def _gauss_pair(d, n, k, repeats, seed):
+    from paper_2509_13307_gb300 import Problem, NestedRun
+    cfg = w.gauss_test(d, n_live=n, n_delete=k, repeats=repeats, seed=seed)
+    inp = w.make_gauss_inputs(cfg)
+    orc = GaussOracle(inp)
+    ons = NestedSampler.from_config(orc.loglike, d, cfg.sampler)
+    ons.initialise()
+    prob = Problem(inp, "fp64", max_batch=max(n, k))
+    run = NestedRun.from_config(prob, cfg.sampler)
+    return ons, prob, run
+
+
+def _compare_iterations(ons, run, n_iter):
+    for _ in range(n_iter):
+        ons.iterate()
+        st = run.step(1)
+        rec = ons.records[-1]
+        lstar, dele, starts, evals = run.last_iteration()
+        assert lstar == pytest.approx(rec.lstar, rel=1e-12, abs=1e-12)
+        assert np.array_equal(dele, rec.deleted)
+        assert np.array_equal(starts, rec.starts)
+        assert np.array_equal(evals, rec.evals), (evals, rec.evals)
+        assert st.logZ == pytest.approx(ons.acc.logZ, rel=1e-12, abs=1e-12)
+        assert st.logX == pytest.approx(ons.acc.logX, rel=1e-13)
+    x, lg = run.live_points()
+    assert np.allclose(x, ons.x, rtol=0, atol=1e-10)
+    assert np.allclose(lg, ons.logL, rtol=1e-10, atol=1e-10)
+    assert st.evaluations == ons.n_evals
+
+
+@pytest.mark.parametrize("k", [1, 6])
+def test_bookkeeping_gauss(k):
+    ons, prob, run = _gauss_pair(5, 60, k, None, 7)
+    _compare_iterations(ons, run, 4)
+
+
+def test_bookkeeping_shear5_plain_ns():
+    """The 5-parameter toy with k = 1 (plain nested sampling)."""
+    from paper_2509_13307_gb300 import NestedRun
+    inp, orc = oracle_for("shear5")
+    sc = w.shear5().sampler
+    prob = cuda_problem("shear5", "fp64", max_batch=sc.n_live)
+    ons = NestedSampler.from_config(orc.loglike_cube, prob.d, sc)
+    ons.initialise()
+    run = NestedRun.from_config(prob, sc)
+    _compare_iterations(ons, run, 3)
+
+
+def test_bookkeeping_shear_tiny_batched():
+    from paper_2509_13307_gb300 import NestedRun
+    inp, orc = oracle_for("shear_tiny")
+    sc = w.shear_tiny(repeats=6).sampler
+    prob = cuda_problem("shear_tiny", "fp64", max_batch=sc.n_live)
+    ons = NestedSampler.from_config(orc.loglike_cube, prob.d, sc)
+    ons.initialise()
+    run = NestedRun.from_config(prob, sc)
+    _compare_iterations(ons, run, 2)
+
+
+def test_full_run_matches_oracle():
+    """Both samplers to convergence: same number of dead points, log Z, H and
+    the simulated-shrinkage error (same Philox replays)."""
+    ons, prob, run = _gauss_pair(3, 40, 4, None, 11)
+    ons.run()
+    st = run.run()
+    assert st.converged and st.iterations == ons.it
+    e_o = ons.evidence(n_replays=50)
+    e_g = run.evidence(n_replays=50)
+    assert e_g["n_dead"] == e_o["n_dead"]
+    assert e_g["logZ"] == pytest.approx(e_o["logZ"], rel=1e-11, abs=1e-11)
+    assert e_g["H"] == pytest.approx(e_o["H"], rel=1e-9, abs=1e-10)
+    assert e_g["logX"] == pytest.approx(e_o["logX"], rel=1e-12)
+    assert e_g["logZ_err"] == pytest.approx(e_o["logZ_err"], rel=1e-8)
+    xd, ld, nd = run.dead_points()
+    assert np.allclose(ld, np.array(ons.dead_logL), rtol=1e-11, atol=1e-11)
+    assert np.array_equal(nd, np.array(ons.dead_nlive))
+
+
+def test_gaussian_evidence_closed_form():
+    from paper_2509_13307_gb300 import Problem, NestedRun
+    d = 5
+    cfg = w.gauss_test(d, n_live=200, n_delete=40, seed=21)
+    inp = w.make_gauss_inputs(cfg)
+    orc = GaussOracle(inp)
+    prob = Problem(inp, "fp64", max_batch=200)
+    zs = []
+    for seed in range(4):
+        run = NestedRun(prob, 200, 40, seed=100 + seed)
+        st = run.run()
+        e = run.evidence()
+        assert st.status_bits == 0
+        zs.append((e["logZ"] - orc.log_evidence()) / e["logZ_err"])
+        assert abs(e["H"] - orc.information()) < 1.0
+    assert np.all(np.abs(zs) < 4.0), zs
+
+
+def test_slice_cap_is_reported():
+    from paper_2509_13307_gb300 import Problem, NestedRun
+    cfg = w.gauss_test(4, n_live=50, n_delete=5)
+    prob = Problem(w.make_gauss_inputs(cfg), "fp64", max_batch=50)
+    run = NestedRun(prob, 50, 5, width=1e-3, step_cap=2)
+    st = run.step(2)
+    assert st.status_bits & 1
+
+
+def test_invalid_run_settings():
+    from paper_2509_13307_gb300 import Problem, NestedRun
+    from paper_2509_13307_gb300._lib import GpunsError
+    cfg = w.gauss_test(4, n_live=50, n_delete=5)
+    prob = Problem(w.make_gauss_inputs(cfg), "fp64", max_batch=50)
+    for n, k in [(50, 50), (50, 0), (5000, 10)]:
+        with pytest.raises(GpunsError):
+            NestedRun(prob, n, k)
