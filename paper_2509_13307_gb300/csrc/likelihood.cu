@@ -4,13 +4,8 @@
 //   emulator          MLP stand-in for CosmoPower (Sec. 2.5): input layer on
 //                     CUDA cores, hidden/output layers as GEMMs (SIMT here,
 //                     tcgen05 tensor cores for BF16 in gemm_tc.cu)
-//   k_shear_eval      App. A: chi(a) by composite 4-point Gauss-Legendre per
-//                     a-interval + block prefix sum; growth by the trapezoid
-//                     in ln a; shifted n_i(z); W^gamma (Eq. 5) by exclusive
-//                     suffix sums S0 - chi S1 (algebraically the direct double
-//                     sum); W^I (Eq. 6); Catmull-Rom P(k, z) lookup and the
-//                     Limber sum (Eq. 3-4); multiplicative bias; templates.
-//   k_chi2            whitening y = L^-1 r and chi^2 (Gaussian likelihood).
+//   projection.cu     App. A projection (distances, windows, P lookup, Limber,
+//                     data vector) and the whitened chi^2.
 #include <algorithm>
 
 #include "likelihood.cuh"
@@ -216,265 +211,6 @@ __global__ void k_zinterp(const T* __restrict__ coarse, int nzc, const int* __re
     }
 }
 
-// ------------------------------------------------------------ shear likelihood
-template <typename T> __device__ inline T dsqrt(T x) { return sqrt(x); }
-
-template <typename T, int NB>
-__global__ void __launch_bounds__(256)
-k_shear_eval(const ShearParams sp, const double* __restrict__ theta_full, const T* __restrict__ table,
-             T* __restrict__ resid, double* __restrict__ model_out, const int* __restrict__ nrows) {
-    constexpr int NP = NB * (NB + 1) / 2;
-    const int row = blockIdx.x;
-    if (row >= *nrows) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = sp.N;
-    T* chi = reinterpret_cast<T*>(smem_raw);
-    T* Ez = chi + N;
-    T* Dg = Ez + N;
-    T* omw = Dg + N;
-    T* V = omw + N;            // NB x N
-    T* t0 = V + NB * N;        // N (scan buffers)
-    T* t1 = t0 + N;
-    T* t2 = t1 + N;
-    T* Cl = t2 + N;            // NP x n_ell
-    T* th = Cl + NP * sp.n_ell;
-    T* red = th + sp.n_params; // 64
-    const int tid = threadIdx.x, nt = blockDim.x;
-
-    for (int i = tid; i < sp.n_params; i += nt) th[i] = (T)theta_full[(size_t)row * sp.n_params + i];
-    __syncthreads();
-    const T h = th[2];
-    const T om = (th[0] + th[1]) / (h * h);
-    const T w0 = th[5], wa = th[6];
-    const T pde = T(3) * (T(1) + w0 + wa);
-    const T chiH = T(kCover100) / h;
-    const T gamma = T(0.55) + T(0.05) * (T(1) + w0 + T(0.5) * wa);
-
-    // E(a) at the nodes and chi increments over each a-interval (4-point GL).
-    for (int n = tid; n < N; n += nt) {
-        const T a = (T)sp.a[n], lna = (T)sp.lna[n];
-        const T e2 = om * dexp<T>(T(-3) * lna) + (T(1) - om) * dexp<T>(-pde * lna - T(3) * wa * (T(1) - a));
-        Ez[n] = dsqrt<T>(e2);
-        if (n < N - 1) {
-            const T a1 = (T)sp.a[n + 1];
-            const T mid = T(0.5) * (a + a1), half = T(0.5) * (a - a1);
-            T acc = T(0);
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                const T ag = mid + half * (T)c_glx[g];
-                const T lg = dlog<T>(ag);
-                const T eg = om * dexp<T>(T(-3) * lg) + (T(1) - om) * dexp<T>(-pde * lg - T(3) * wa * (T(1) - ag));
-                acc += (T)c_glw[g] / (ag * ag * dsqrt<T>(eg));
-            }
-            t0[n] = chiH * half * acc;
-        } else {
-            t0[n] = T(0);
-        }
-    }
-    __syncthreads();
-    block_exclusive_scan(t0, N, red);   // t0[n] = chi_n
-    // growth: f = Omega_m(a)^gamma, ln D_n = -sum_{m<n} (f_m + f_{m+1})/2 (ln a_m - ln a_{m+1})
-    for (int n = tid; n < N; n += nt) {
-        chi[n] = t0[n];
-        const T lna = (T)sp.lna[n];
-        const T oma = om * dexp<T>(T(-3) * lna) / (Ez[n] * Ez[n]);
-        t1[n] = dexp<T>(gamma * dlog<T>(oma));
-        omw[n] = (T)sp.wa[n] * chiH / ((T)sp.a[n] * (T)sp.a[n] * Ez[n]);
-    }
-    __syncthreads();
-    for (int n = tid; n < N; n += nt)
-        t2[n] = (n < N - 1) ? T(0.5) * (t1[n] + t1[n + 1]) * ((T)sp.lna[n] - (T)sp.lna[n + 1]) : T(0);
-    __syncthreads();
-    block_exclusive_scan(t2, N, red);
-    for (int n = tid; n < N; n += nt) Dg[n] = dexp<T>(-t2[n]);
-    __syncthreads();
-
-    const T pref = T(1.5) * om / (chiH * chiH);
-    const T A_IA = th[9], eta = th[10];
-    for (int i = 0; i < NB; ++i) {
-        const T dz = th[11 + i];
-        const T mu = (T)sp.nz_mean[i], sg = (T)sp.nz_sigma[i];
-        T part = T(0);
-        for (int n = tid; n < N; n += nt) {
-            const T u = ((T)sp.z[n] - dz - mu) / sg;
-            const T raw = dexp<T>(T(-0.5) * u * u);
-            t1[n] = raw;
-            part += (T)sp.wa[n] * raw / ((T)sp.a[n] * (T)sp.a[n]);
-        }
-        const T norm = block_sum(part, red);
-        for (int n = tid; n < N; n += nt) {
-            const T nchi = t1[n] * Ez[n] / (chiH * norm);
-            t1[n] = nchi;
-            const T a0 = (n >= 1) ? omw[n] * nchi : T(0);
-            t0[n] = a0;
-            t2[n] = (n >= 1) ? a0 / chi[n] : T(0);
-        }
-        __syncthreads();
-        block_exclusive_suffix_scan(t0, N, red);   // sum_{m>n} omega n
-        block_exclusive_suffix_scan(t2, N, red);   // sum_{m>n} omega n / chi
-        for (int n = tid; n < N; n += nt) {
-            T v = T(0);
-            if (n >= 1) {
-                const T c = chi[n];
-                const T Wg = pref * c / (T)sp.a[n] * (t0[n] - c * t2[n]);
-                const T amp = A_IA * dexp<T>(eta * dlog<T>((T(1) + (T)sp.z[n]) / (T)sp.ia_pivot));
-                const T WI = -amp * (T)sp.c1rho * om / Dg[n] * t1[n];
-                v = dsqrt<T>(omw[n] / (c * c)) * (Wg + WI);
-            }
-            V[i * N + n] = v;
-        }
-        __syncthreads();
-    }
-    // ln chi for the k of each multipole
-    for (int n = tid; n < N; n += nt) t0[n] = (n >= 1) ? dlog<T>(chi[n]) : T(0);
-    __syncthreads();
-
-    // Limber (Eq. 4) with the Catmull-Rom lookup of log10 P; one warp per multipole.
-    const int lane = tid & 31, wid = tid >> 5, nwarp = nt >> 5;
-    const T* tab = table + (size_t)row * sp.n_z * sp.n_k;
-    const T lkmin = (T)sp.lnk_min, lkmax = (T)sp.lnk_max, inv_dk = T(1) / (T)sp.dlnk;
-    for (int l = wid; l < sp.n_ell; l += nwarp) {
-        T acc[NP];
-#pragma unroll
-        for (int p = 0; p < NP; ++p) acc[p] = T(0);
-        const T lne = (T)sp.lnell[l];
-        for (int n = 1 + lane; n < N; n += 32) {
-            T s = lne - t0[n];
-            s = fmin(fmax(s, lkmin), lkmax);
-            const T u = (s - lkmin) * inv_dk;
-            int ik = (int)floor(u);
-            ik = min(max(ik, 0), sp.n_k - 2);
-            T wk[4], cw[4];
-            int ci[4];
-            catmull_rom<T>(u - (T)ik, wk);
-            fold_taps<T>(ik, sp.n_k, wk, ci, cw);
-            T v = T(0);
-#pragma unroll
-            for (int pz = 0; pz < 4; ++pz) {
-                const T* trow = tab + sp.zrow[4 * n + pz] * sp.n_k;
-                const T rv = cw[0] * trow[ci[0]] + cw[1] * trow[ci[1]] + cw[2] * trow[ci[2]] + cw[3] * trow[ci[3]];
-                v += (T)sp.zw[4 * n + pz] * rv;
-            }
-            const T P = dexp<T>(v * (T)kLn10);
-            T tv[NB];
-#pragma unroll
-            for (int i = 0; i < NB; ++i) tv[i] = V[i * N + n] * P;
-            int p = 0;
-#pragma unroll
-            for (int i = 0; i < NB; ++i)
-#pragma unroll
-                for (int j = i; j < NB; ++j) acc[p++] += tv[i] * V[j * N + n];
-        }
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            const T s = warp_sum(acc[p]);
-            if (lane == 0) Cl[p * sp.n_ell + l] = s;
-        }
-    }
-    __syncthreads();
-
-    // data vector: (1 + m_i)(1 + m_j) C_ij(ell) + T b; residual d - m
-    for (int a = tid; a < sp.D; a += nt) {
-        const int p = a / sp.n_ell, e = a % sp.n_ell;
-        const int i = sp.pi[p], j = sp.pj[p];
-        T m = (T(1) + th[11 + NB + i]) * (T(1) + th[11 + NB + j]) * Cl[p * sp.n_ell + e];
-        for (int t = 0; t < sp.n_tmpl; ++t) m += (T)sp.tmpl[(size_t)a * sp.n_tmpl + t] * th[11 + 2 * NB + t];
-        if (model_out) model_out[(size_t)row * sp.D + a] = (double)m;
-        else resid[(size_t)row * sp.D + a] = (T)sp.data[a] - m;
-    }
-}
-
-// chi^2 = |L^-1 r|^2 for R rows per block; LinvT[b*D + a] = (L^-1)[a][b].
-template <typename TR, typename TA, int R>
-__global__ void __launch_bounds__(256)
-k_chi2(const TR* __restrict__ resid, int D, const TA* __restrict__ LinvT, double c0,
-       double* __restrict__ logL, const int* __restrict__ nrows) {
-    const int M = *nrows;
-    const int row0 = blockIdx.x * R;
-    if (row0 >= M) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TA* r = reinterpret_cast<TA*>(smem_raw);        // R x D
-    TA* red = r + R * D;                            // 32
-    for (int i = threadIdx.x; i < R * D; i += blockDim.x) {
-        const int rr = i / D, a = i % D;
-        r[i] = (row0 + rr < M) ? (TA)resid[(size_t)(row0 + rr) * D + a] : TA(0);
-    }
-    __syncthreads();
-    TA sq[R];
-#pragma unroll
-    for (int rr = 0; rr < R; ++rr) sq[rr] = TA(0);
-    for (int a = threadIdx.x; a < D; a += blockDim.x) {
-        TA y[R];
-#pragma unroll
-        for (int rr = 0; rr < R; ++rr) y[rr] = TA(0);
-        for (int b = 0; b <= a; ++b) {
-            const TA l = LinvT[(size_t)b * D + a];
-#pragma unroll
-            for (int rr = 0; rr < R; ++rr) y[rr] += l * r[rr * D + b];
-        }
-#pragma unroll
-        for (int rr = 0; rr < R; ++rr) sq[rr] += y[rr] * y[rr];
-    }
-#pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-        const TA s = block_sum(sq[rr], red);
-        if (threadIdx.x == 0 && row0 + rr < M) logL[row0 + rr] = c0 - 0.5 * (double)s;
-    }
-}
-
-// ------------------------------------------------------------ launchers
-static size_t shear_smem_bytes(const ShearParams& sp, int elt) {
-    const int NP = sp.nb * (sp.nb + 1) / 2;
-    return (size_t)elt * ((size_t)sp.N * (7 + sp.nb) + (size_t)NP * sp.n_ell + sp.n_params + 64);
-}
-
-template <typename T, int NB>
-static int launch_shear_nb(const ShearParams& sp, const double* theta_full, const T* table, T* resid,
-                           double* model_out, const int* nrows, int grid_rows, cudaStream_t st) {
-    const size_t smem = shear_smem_bytes(sp, sizeof(T));
-    static bool attr_done = false;   // per instantiation
-    if (!attr_done) {
-        NS_CUDA_TRY(cudaFuncSetAttribute(k_shear_eval<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024));
-        attr_done = true;
-    }
-    if (smem > 227 * 1024) return NS_ENOTSUP;
-    k_shear_eval<T, NB><<<grid_rows, 256, smem, st>>>(sp, theta_full, table, resid, model_out, nrows);
-    NS_CUDA_TRY(cudaGetLastError());
-    return NS_OK;
-}
-
-template <typename T>
-static int launch_shear(const ShearParams& sp, const double* theta_full, const T* table, T* resid,
-                        double* model_out, const int* nrows, int grid_rows, cudaStream_t st) {
-    switch (sp.nb) {
-        case 1: return launch_shear_nb<T, 1>(sp, theta_full, table, resid, model_out, nrows, grid_rows, st);
-        case 2: return launch_shear_nb<T, 2>(sp, theta_full, table, resid, model_out, nrows, grid_rows, st);
-        case 3: return launch_shear_nb<T, 3>(sp, theta_full, table, resid, model_out, nrows, grid_rows, st);
-        case 4: return launch_shear_nb<T, 4>(sp, theta_full, table, resid, model_out, nrows, grid_rows, st);
-        case 5: return launch_shear_nb<T, 5>(sp, theta_full, table, resid, model_out, nrows, grid_rows, st);
-        case 10: return launch_shear_nb<T, 10>(sp, theta_full, table, resid, model_out, nrows, grid_rows, st);
-        default: return NS_ENOTSUP;
-    }
-}
-
-template <typename TR, typename TA>
-static int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL, const int* nrows,
-                       int grid_rows, cudaStream_t st) {
-    constexpr int R = 4;
-    const size_t smem = sizeof(TA) * ((size_t)R * D + 32);
-    static bool attr_done = false;
-    if (!attr_done) {
-        NS_CUDA_TRY(cudaFuncSetAttribute(k_chi2<TR, TA, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024));
-        attr_done = true;
-    }
-    if (smem > 227 * 1024) return NS_ENOTSUP;
-    k_chi2<TR, TA, R><<<(grid_rows + R - 1) / R, 256, smem, st>>>(resid, D, LinvT, c0, logL, nrows);
-    NS_CUDA_TRY(cudaGetLastError());
-    return NS_OK;
-}
-
 template <typename T>
 static int launch_gemm_simt(const T* A, const T* W, const T* bias, const T* mu, T sigma, T* C,
                             const int* nrows, int grid_rows, int N, int K, int epi, cudaStream_t st);
@@ -541,12 +277,12 @@ static int run_emulator_simt(const ns_problem* p, Workspace* ws, int grid_rows, 
 static int probe_begin(const StageProbe* pr, int stage, Workspace* ws, cudaStream_t st) {
     if (!pr || pr->stage != stage) return NS_OK;
     NS_CUDA_TRY(cudaMemcpyAsync(pr->h_rows, ws->d_nrows, sizeof(int), cudaMemcpyDeviceToHost, st));
-    NS_CUDA_TRY(cudaEventRecord(pr->ev0, st));
+    NS_CUDA_TRY(cudaEventRecordWithFlags(pr->ev0, st, cudaEventRecordExternal));
     return NS_OK;
 }
 static int probe_end(const StageProbe* pr, int stage, cudaStream_t st) {
     if (!pr || pr->stage != stage) return NS_OK;
-    NS_CUDA_TRY(cudaEventRecord(pr->ev1, st));
+    NS_CUDA_TRY(cudaEventRecordWithFlags(pr->ev1, st, cudaEventRecordExternal));
     return NS_OK;
 }
 
@@ -625,7 +361,7 @@ int run_likelihood(const ns_problem* p, Workspace* ws, int grid_rows, double* lo
                                     grid_rows, st));
         if (model_out) return NS_OK;
         return launch_chi2<double, double>((const double*)ws->resid, sp.D, p->d_LinvT64, p->c0, logL_out,
-                                           ws->d_nrows, grid_rows, st);
+                                           ws->chi2_part, ws->d_nrows, grid_rows, st);
     }
     // FP32 stages (FP32 / BF16 / BF16_F64CHI2)
     if (p->precision == NS_PREC_FP32) NS_TRY(run_emulator_simt<float>(p, ws, grid_rows, st));
@@ -646,10 +382,10 @@ int run_likelihood(const ns_problem* p, Workspace* ws, int grid_rows, double* lo
     NS_TRY(probe_begin(probe, PROBE_CHI2, ws, st));
     if (p->precision == NS_PREC_BF16_F64CHI2)
         NS_TRY(launch_chi2<float, double>((const float*)ws->resid, sp.D, p->d_LinvT64, p->c0, logL_out,
-                                          ws->d_nrows, grid_rows, st));
+                                          ws->chi2_part, ws->d_nrows, grid_rows, st));
     else
         NS_TRY(launch_chi2<float, float>((const float*)ws->resid, sp.D, p->d_LinvT32, p->c0, logL_out,
-                                         ws->d_nrows, grid_rows, st));
+                                         ws->chi2_part, ws->d_nrows, grid_rows, st));
     return probe_end(probe, PROBE_CHI2, st);
 }
 

@@ -12,6 +12,11 @@ namespace gpuns {
 struct ShearParams {
     int n_params, nb, n_pairs, n_ell, n_k, n_z, N, D, n_tmpl;
     double lnk_min, lnk_max, dlnk, ia_pivot, c1rho;
+    double dz;            // table z spacing
+    const float* a_f;     // FP32 copies of the node constants
+    const float* lna_f;
+    const float* z_f;
+    const float* wa_f;
     const double* a;      // N   scale factor at chi nodes (node 0: a = 1)
     const double* lna;    // N
     const double* z;      // N
@@ -35,6 +40,7 @@ struct Workspace {
     void* table = nullptr;        // cap x n_out (emulator output)
     void* table_fine = nullptr;   // cap x n_z*n_k (coarse-z emulators)
     void* resid = nullptr;        // cap x D
+    void* chi2_part = nullptr;    // cap x ceil(D / 64) partial chi^2 sums (FP64-sized)
     double* logL = nullptr;       // cap
     // tcgen05 tensor maps (BF16 precision): A operand of layer l >= 1 and its output
     std::vector<CUtensorMap> tmA;
@@ -104,6 +110,16 @@ int run_emulator_only(const ns_problem* p, Workspace* ws, int grid_rows, double*
 // Prior transform into the workspace: cube (rows x d) -> theta_full.
 int launch_cube_to_theta(const ns_problem* p, Workspace* ws, const double* cube, int grid_rows,
                          cudaStream_t st);
+
+// Shear projection (projection.cu): residual (or model vector) per row.
+template <typename T>
+int launch_shear(const ShearParams& sp, const double* theta_full, const T* table, T* resid, double* model_out,
+                 const int* nrows, int grid_rows, cudaStream_t st);
+size_t projection_smem_bytes(const ShearParams& sp, int elt);
+// Whitened chi^2 and log L = c0 - chi^2 / 2 (projection.cu).
+template <typename TR, typename TA>
+int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL, void* partial, const int* nrows,
+                int grid_rows, cudaStream_t st);
 
 // BF16 tcgen05 GEMM: C[M x N] = epi(A[M x K] * W[N x K]^T + bias), M = *d_nrows.
 // epi 0: tanh -> bf16 C (ldc = N); epi 1: mu + sigma * v -> fp32 C.

@@ -121,6 +121,8 @@ int workspace_create(const ns_problem* p, int cap, Workspace* ws) {
     }
     NS_TRY(dalloc((size_t)tab_elt * cap * p->sp.D, &v, ws->owned));
     ws->resid = v;
+    NS_TRY(dalloc(sizeof(double) * (size_t)cap * ((p->sp.D + 63) / 64), &v, ws->owned));
+    ws->chi2_part = v;
     if (p->precision == NS_PREC_BF16 || p->precision == NS_PREC_BF16_F64CHI2) {
         ws->tmA.resize(p->n_layers);
         int cur = 0;
@@ -154,7 +156,7 @@ static int validate_desc(const ns_problem_desc* d) {
     if (d->kind != NS_KIND_SHEAR) return NS_EINVAL;
     const ns_shear_desc& s = d->shear;
     const ns_emulator_desc& e = d->emu;
-    if (s.n_bins < 1 || s.n_ell < 1 || s.n_k < 4 || s.n_z < 4 || s.n_chi < 3 || !(s.a_min > 0 && s.a_min < 1))
+    if (s.n_bins < 1 || s.n_bins > 5 || s.n_ell < 1 || s.n_k < 4 || s.n_z < 4 || s.n_chi < 3 || !(s.a_min > 0 && s.a_min < 1))
         return NS_EINVAL;
     if (s.n_z_emu < 4 || s.n_z_emu > s.n_z) return NS_EINVAL;
     if (d->n_params != 11 + 2 * s.n_bins + s.n_tmpl) return NS_EINVAL;
@@ -349,6 +351,16 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
             return fail(s);
         if (sd.n_tmpl > 0 && (s = upload(sd.tmpl, (size_t)sp.D * sd.n_tmpl, &dtm, p->owned))) return fail(s);
         sp.a = da_; sp.lna = dlna; sp.z = dz_; sp.wa = dwa; sp.zw = dzw; sp.zrow = dzrow; sp.lnell = dlnell;
+        sp.dz = dz;
+        {
+            std::vector<float> af(a.begin(), a.end()), lf(lna.begin(), lna.end()), zf(z.begin(), z.end()),
+                wf(wa.begin(), wa.end());
+            float *daf, *dlf, *dzf, *dwf;
+            if ((s = upload(af.data(), N, &daf, p->owned)) || (s = upload(lf.data(), N, &dlf, p->owned)) ||
+                (s = upload(zf.data(), N, &dzf, p->owned)) || (s = upload(wf.data(), N, &dwf, p->owned)))
+                return fail(s);
+            sp.a_f = daf; sp.lna_f = dlf; sp.z_f = dzf; sp.wa_f = dwf;
+        }
         sp.nz_mean = dmu; sp.nz_sigma = dsg; sp.pi = dpi; sp.pj = dpj; sp.data = ddata; sp.tmpl = dtm;
         if (p->n_z_emu != sd.n_z) {
             std::vector<int> zr(4 * sd.n_z);
