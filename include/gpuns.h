@@ -222,6 +222,29 @@ int ns_step(ns_run* r, int n_iters, ns_status* st);
 int ns_evidence(const ns_run* r, int n_replays, double* logZ, double* logZ_err,
                 double* logX, double* H, long long* n_dead);
 
+/* Evidence of a dead-point sequence that the caller holds on the device, for
+ * callers that cannot allocate device memory when they need it (work recorded
+ * into a CUDA graph under a strict capture mode, where cudaMalloc is an error;
+ * frameworks that own all device memory through their own pool).  It allocates
+ * nothing: the per-replay values live in a library-owned array of 4096 doubles
+ * that every GPU loading the library keeps until the process exits.  The paper
+ * has no counterpart; this is an interface convenience.
+ *   logL_dev  (n) log L of the dead points in deletion order, the final live
+ *             points appended in ascending order;
+ *   nlive_dev (n) live-point count booked for each (n_live - j within a batch;
+ *             n_live, n_live - 1, ..., 1 for the appended live points);
+ *   out_dev   (3) ln Z by the expected shrinkage, its simulated-shrinkage
+ *             standard deviation (ddof 1) over n_replays Philox replays
+ *             (counters (ERR, replay, index, 0) with key `seed`, so the same
+ *             sequence and seed give ns_evidence's error), and the final ln X.
+ * n_replays <= 0 means 200; 2 <= n_replays <= 4096 else NS_EINVAL.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current: make that first call before any stream capture.
+ * All calls on a device share the array, so calls that overlap on the GPU race;
+ * each call writes every slot it reads, so nothing needs clearing. */
+int ns_evidence_noalloc(const double* logL_dev, const int* nlive_dev, long long n,
+                        unsigned long long seed, int n_replays, double* out_dev, void* stream);
+
 /* Copy out the live set (x: n x d cube coordinates, logL: n); either may be NULL. */
 int ns_live_points(const ns_run* r, double* x, double* logL);
 
