@@ -133,7 +133,7 @@ class ClockSampler:
 
 
 def projection_flops_per_eval(cfg) -> float:
-    """Algorithmic FLOPs of the shear projection kernel per evaluation (the
+    """Algorithmic FLOPs of the fused projection kernel per evaluation (the
     count stated in the design notes): per (ell, chi-node) a 16-tap bicubic
     lookup (32) + bracket/weights (10) + nb window products + 2 n_pairs Limber
     FMAs; per node interval the 4-point distance quadrature (4 x 12); per node
@@ -141,8 +141,9 @@ def projection_flops_per_eval(cfg) -> float:
     N = cfg.n_chi
     nb = cfg.n_bins
     npairs = nb * (nb + 1) // 2
+    D = cfg.n_data
     return (cfg.n_ell * (N - 1) * (32 + 10 + nb + 2 * npairs) + (N - 1) * 48 + N * nb * 25
-            + cfg.n_data * (3 + 2 * cfg.n_tmpl))
+            + D * (3 + 2 * cfg.n_tmpl))
 
 
 def fp32_alu_peak_tflops(sm_mhz: float) -> float:
@@ -289,7 +290,7 @@ def ours(args):
         achieved = prof["rows"] * flops / (prof["ms"] * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
-                    "kernel": "k_shear_eval<float,5> (A8-A12: distances, windows, P lookup, Limber, data vector)",
+                    "kernel": "k_projection<float,5,fast> (A8-A12: distances, windows, P lookup, Limber, data vector)",
                     "flop_per_eval": flops, "avg_launch_ms": prof["ms"] / prof["launches"],
                     "avg_rows_per_launch": prof["rows"] / prof["launches"],
                     "peak_basis": "FP32 ALU 152 SM x 128 lanes x 2 x 2070 MHz (no measured FP32 peak in MEASURED_PEAKS.json)"}

@@ -357,8 +357,8 @@ int run_likelihood(const ns_problem* p, Workspace* ws, int grid_rows, double* lo
             NS_CUDA_TRY(cudaGetLastError());
             tab = (const double*)ws->table_fine;
         }
-        NS_TRY(launch_shear<double>(sp, ws->theta_full, tab, (double*)ws->resid, model_out, ws->d_nrows,
-                                    grid_rows, st));
+        NS_TRY(launch_projection<double, false>(sp, ws->theta_full, tab, (double*)ws->resid, model_out,
+                                                ws->d_nrows, grid_rows, st));
         if (model_out) return NS_OK;
         return launch_chi2<double, double>((const double*)ws->resid, sp.D, p->d_LinvT64, p->c0, logL_out,
                                            ws->chi2_part, ws->d_nrows, grid_rows, st);
@@ -375,8 +375,12 @@ int run_likelihood(const ns_problem* p, Workspace* ws, int grid_rows, double* lo
         tab = (const float*)ws->table_fine;
     }
     NS_TRY(probe_begin(probe, PROBE_PROJECTION, ws, st));
-    NS_TRY(launch_shear<float>(sp, ws->theta_full, tab, (float*)ws->resid, model_out, ws->d_nrows, grid_rows,
-                               st));
+    if (p->precision == NS_PREC_FP32)
+        NS_TRY(launch_projection<float, false>(sp, ws->theta_full, tab, (float*)ws->resid, model_out, ws->d_nrows,
+                                               grid_rows, st));
+    else
+        NS_TRY(launch_projection<float, true>(sp, ws->theta_full, tab, (float*)ws->resid, model_out, ws->d_nrows,
+                                              grid_rows, st));
     NS_TRY(probe_end(probe, PROBE_PROJECTION, st));
     if (model_out) return NS_OK;
     NS_TRY(probe_begin(probe, PROBE_CHI2, ws, st));

@@ -17,6 +17,9 @@ struct ShearParams {
     const float* lna_f;
     const float* z_f;
     const float* wa_f;
+    const int* zrp;       // N   padded-table row of each node's first z-tap
+    const float* zw4f;    // 4N  doubled Catmull-Rom z-weights (unfolded)
+    const double* zw4d;
     const double* a;      // N   scale factor at chi nodes (node 0: a = 1)
     const double* lna;    // N
     const double* z;      // N
@@ -39,7 +42,7 @@ struct Workspace {
     void* act[2] = {nullptr, nullptr};
     void* table = nullptr;        // cap x n_out (emulator output)
     void* table_fine = nullptr;   // cap x n_z*n_k (coarse-z emulators)
-    void* resid = nullptr;        // cap x D
+    void* resid = nullptr;        // cap x D residuals
     void* chi2_part = nullptr;    // cap x ceil(D / 64) partial chi^2 sums (FP64-sized)
     double* logL = nullptr;       // cap
     // tcgen05 tensor maps (BF16 precision): A operand of layer l >= 1 and its output
@@ -111,11 +114,12 @@ int run_emulator_only(const ns_problem* p, Workspace* ws, int grid_rows, double*
 int launch_cube_to_theta(const ns_problem* p, Workspace* ws, const double* cube, int grid_rows,
                          cudaStream_t st);
 
-// Shear projection (projection.cu): residual (or model vector) per row.
-template <typename T>
-int launch_shear(const ShearParams& sp, const double* theta_full, const T* table, T* resid, double* model_out,
-                 const int* nrows, int grid_rows, cudaStream_t st);
-size_t projection_smem_bytes(const ShearParams& sp, int elt);
+// Shear projection (projection.cu): residual d - m per row, or the model
+// vectors when model_out != nullptr.  FAST selects SFU transcendentals.
+template <typename T, bool FAST>
+int launch_projection(const ShearParams& sp, const double* theta_full, const T* table, T* resid, double* model_out,
+                      const int* nrows, int grid_rows, cudaStream_t st);
+size_t projection_smem_bytes(const ShearParams& sp, int elt, int elt_acc);
 // Whitened chi^2 and log L = c0 - chi^2 / 2 (projection.cu).
 template <typename TR, typename TA>
 int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL, void* partial, const int* nrows,

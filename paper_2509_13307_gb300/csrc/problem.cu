@@ -123,6 +123,7 @@ int workspace_create(const ns_problem* p, int cap, Workspace* ws) {
     ws->resid = v;
     NS_TRY(dalloc(sizeof(double) * (size_t)cap * ((p->sp.D + 63) / 64), &v, ws->owned));
     ws->chi2_part = v;
+
     if (p->precision == NS_PREC_BF16 || p->precision == NS_PREC_BF16_F64CHI2) {
         ws->tmA.resize(p->n_layers);
         int cur = 0;
@@ -360,6 +361,26 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
                 (s = upload(zf.data(), N, &dzf, p->owned)) || (s = upload(wf.data(), N, &dwf, p->owned)))
                 return fail(s);
             sp.a_f = daf; sp.lna_f = dlf; sp.z_f = dzf; sp.wa_f = dwf;
+            // padded-table z-taps: the cell bracket, unfolded (ghost rows exist) and doubled
+            std::vector<int> zrp(N);
+            std::vector<double> z4(4 * N);
+            std::vector<float> z4f(4 * N);
+            for (int n = 0; n < N; ++n) {
+                const double u = z[n] / dz;
+                int j = (int)std::floor(u);
+                j = std::max(0, std::min(j, sd.n_z - 2));
+                double w[4];
+                catmull_rom<double>(u - j, w);
+                zrp[n] = j;
+                for (int q = 0; q < 4; ++q) { z4[4 * n + q] = 2.0 * w[q]; z4f[4 * n + q] = (float)(2.0 * w[q]); }
+            }
+            int* dzr;
+            double* dz4;
+            float* dz4f;
+            if ((s = upload(zrp.data(), N, &dzr, p->owned)) || (s = upload(z4.data(), 4 * N, &dz4, p->owned)) ||
+                (s = upload(z4f.data(), 4 * N, &dz4f, p->owned)))
+                return fail(s);
+            sp.zrp = dzr; sp.zw4d = dz4; sp.zw4f = dz4f;
         }
         sp.nz_mean = dmu; sp.nz_sigma = dsg; sp.pi = dpi; sp.pj = dpj; sp.data = ddata; sp.tmpl = dtm;
         if (p->n_z_emu != sd.n_z) {
