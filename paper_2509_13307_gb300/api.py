@@ -218,6 +218,27 @@ class Problem:
         return out, g
 
 
+class LogLike(torch.autograd.Function):
+    """log L(theta) as a differentiable torch op: forward calls the library's
+    hand-written adjoint (loglike_grad_batch) once and keeps the gradient;
+    backward scales it by the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, theta, problem):
+        logL, grad = problem.loglike_grad(theta.detach())
+        ctx.save_for_backward(grad)
+        return logL
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (grad,) = ctx.saved_tensors
+        return grad_out[:, None] * grad, None
+
+
+def loglike_autograd(problem: "Problem", theta: torch.Tensor) -> torch.Tensor:
+    return LogLike.apply(theta, problem)
+
+
 @dataclass
 class RunStatus:
     iterations: int

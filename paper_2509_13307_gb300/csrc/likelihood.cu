@@ -408,3 +408,22 @@ int launch_free_to_full(const ns_problem* p, const double* theta, int B, double*
     return NS_OK;
 }
 }  // namespace gpuns
+
+namespace gpuns {
+int launch_zinterp_generic(const ns_problem* p, const void* coarse, void* fine, const int* nrows, int grid_rows, int elt,
+                           cudaStream_t st) {
+    const ShearParams& sp = p->sp;
+    dim3 g((sp.n_z * sp.n_k + 255) / 256, grid_rows);
+    if (elt == 8)
+        k_zinterp<double><<<g, 256, 0, st>>>((const double*)coarse, p->n_z_emu, p->d_zi_row, p->d_zi_w, (double*)fine,
+                                             sp.n_z, sp.n_k, nrows);
+    else
+        k_zinterp<float><<<g, 256, 0, st>>>((const float*)coarse, p->n_z_emu, p->d_zi_row, p->d_zi_w, (float*)fine,
+                                            sp.n_z, sp.n_k, nrows);
+    NS_CUDA_TRY(cudaGetLastError());
+    return NS_OK;
+}
+int launch_free_to_full_ext(const ns_problem* p, const double* theta, int B, double* theta_full, cudaStream_t st) {
+    return launch_free_to_full(p, theta, B, theta_full, st);
+}
+}  // namespace gpuns

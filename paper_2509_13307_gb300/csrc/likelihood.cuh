@@ -125,6 +125,17 @@ template <typename TR, typename TA>
 int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL, void* partial, const int* nrows,
                 int grid_rows, cudaStream_t st);
 
+// Adjoint of the shear projection (adjoint.cu).
+int adjoint_scratch_elems(const ShearParams& sp);
+template <typename T>
+int launch_projection_adj(const ShearParams& sp, const double* theta_full, const T* table, const T* LinvT, double c0,
+                          T* scratch, T* gtab, double* gfull, double* logL, const int* nrows, int grid_rows,
+                          cudaStream_t st);
+int launch_free_to_full(const ns_problem* p, const double* theta, int B, double* theta_full, cudaStream_t st);
+int launch_zinterp_generic(const ns_problem* p, const void* coarse, void* fine, const int* nrows, int grid_rows,
+                           int elt, cudaStream_t st);
+int launch_free_to_full_ext(const ns_problem* p, const double* theta, int B, double* theta_full, cudaStream_t st);
+
 // BF16 tcgen05 GEMM: C[M x N] = epi(A[M x K] * W[N x K]^T + bias), M = *d_nrows.
 // epi 0: tanh -> bf16 C (ldc = N); epi 1: mu + sigma * v -> fp32 C.
 int launch_gemm_tc(const CUtensorMap* tmA, const CUtensorMap* tmB, int tile_n,

@@ -819,9 +819,3 @@ extern "C" int ns_free(ns_run* r) {
     run_release(r);
     return NS_OK;
 }
-
-extern "C" int loglike_grad_batch(const ns_problem* p, const double* theta_dev, int B, double* logL_dev,
-                                  double* grad_dev, void* stream) {
-    (void)p; (void)theta_dev; (void)B; (void)logL_dev; (void)grad_dev; (void)stream;
-    return NS_ENOTSUP;
-}

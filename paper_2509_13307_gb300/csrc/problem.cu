@@ -177,8 +177,11 @@ static int validate_desc(const ns_problem_desc* d) {
 
 using namespace gpuns;
 
+void gpuns_release_grad_state(const ns_problem* p);
+
 static void problem_release(ns_problem* p) {
     if (!p) return;
+    gpuns_release_grad_state(p);
     workspace_free(&p->ws);
     for (void* q : p->owned) cudaFree(q);
     delete p;
