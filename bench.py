@@ -307,6 +307,29 @@ def ours(args):
     extra["iters_per_s"] = res["iters"] / t_local
     extra["rounds_per_step"] = res["rounds"] / max(res["iters"], 1)
 
+    # ---------------- adjoint throughput (B = 4096 parameter vectors, hand-written adjoint)
+    try:
+        Bg = 4096
+        pg = Problem(inp, args.precision, max_batch=Bg)
+        rng_g = np.random.default_rng(4 + rank)
+        free_g = [i for i, p in enumerate(inp["priors"]) if p[0] != "F"]
+        thg = pg.prior_transform(torch.tensor(rng_g.uniform(0.02, 0.98, (Bg, len(free_g))), device=dev))
+        for _ in range(2):
+            pg.loglike_grad(thg)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            pg.loglike_grad(thg)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        extra["grad_evals_per_s"] = 3 * Bg / (e0.elapsed_time(e1) / 1e3)
+        extra["grad_batch"] = Bg
+        pg.close()
+    except Exception as exc:  # report, do not hide, a failure of this extra measurement
+        extra["grad_error"] = repr(exc)[:200]
+
     # ---------------- wall time to a converged log Z (BF16), from ns_init
     if not args.no_full_run:
         torch.cuda.synchronize()

@@ -155,15 +155,31 @@ class ShearOracle:
         return np.array(W), omega
 
     # ------------------------------------------------------------ emulator
-    def emulator(self, theta):
-        """log10 P on the emulator's (z, k) grid, shape (n_z_emu, n_k)."""
+    @staticmethod
+    def to_bf16(a):
+        """Round to the nearest bfloat16 (ties to even) through float32, returned as float64."""
+        f = np.asarray(a, dtype=np.float32).copy()
+        u = f.view(np.uint32)
+        u += np.uint32(0x7FFF) + ((u >> np.uint32(16)) & np.uint32(1))
+        u &= np.uint32(0xFFFF0000)
+        return u.view(np.float32).astype(np.float64)
+
+    def emulator(self, theta, bf16=False):
+        """log10 P on the emulator's (z, k) grid, shape (n_z_emu, n_k).  With
+        bf16=True the weights of layers >= 1 and every hidden activation are
+        rounded to bfloat16 (arithmetic stays FP64): the model the tensor-core
+        path computes, up to its FP32 accumulation order."""
         inp = self.inp
         x = (theta[inp["emu_inputs"]] - inp["emu_in_center"]) / inp["emu_in_scale"]
         Ws, bs = inp["emu_W"], inp["emu_b"]
         h = x
         for l in range(len(Ws) - 1):
-            h = np.tanh(Ws[l] @ h + bs[l])
-        y = Ws[-1] @ h + bs[-1]
+            W = self.to_bf16(Ws[l]) if (bf16 and l >= 1) else Ws[l]
+            h = np.tanh(W @ h + bs[l])
+            if bf16:
+                h = self.to_bf16(h)
+        Wl = self.to_bf16(Ws[-1]) if bf16 else Ws[-1]
+        y = Wl @ h + bs[-1]
         t = inp["emu_out_mu"] + inp["emu_out_sigma"] * y
         return t.reshape(self.n_z_emu, self.n_k)
 

@@ -1,0 +1,90 @@
+"""Reduced-precision likelihood paths against the FP64 oracle.
+
+BF16 emulator: compared with the oracle's bf16-aware emulator (weights of
+layers >= 1 and every hidden activation rounded to bfloat16, arithmetic FP64),
+i.e. the model the tcgen05 path computes up to FP32 accumulation order.  The
+accumulation-order differences (~1e-6 relative) flip the bf16 rounding of an
+activation now and then; one flip moves that unit by 2^-8 and four stacked
+1024-wide layers spread it: measured 1.2e-4 dex on the 39-d emulator (3e-4
+against the FP64 emulator); the bound is 2e-4.
+
+FP32 log L: a model vector with relative error eps_m shifts chi^2 by
+2 y . L^-1 dm, so |d log L| <= eps_m sum_a |y_a| (|L^-1| |m|)_a with
+y = L^-1 (d - m).  The FP32 stages give eps_m ~ 1e-6 (1024-term FP32
+contractions in the emulator, 16-tap lookups, 1024-node Limber sums); the test
+uses eps_m = 2e-6 (measured errors reach 0.2 of that bound).  BF16 log L against the bf16-aware oracle obeys the same
+bound (its FP32 stages are the same)."""
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import cuda_problem, free_theta, oracle_for, random_cube
+from oracle.priors import free_indices
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _full(inp, th):
+    full = np.array([p[1] for p in inp["priors"]], float)
+    full[free_indices(inp["priors"])] = th
+    return full
+
+
+def _fp32_bound(orc, full, eps_m=2e-6):
+    m = orc.model(full)
+    y = orc.forward_subst(orc.data - m)
+    Linv = np.linalg.inv(orc.L)
+    return eps_m * np.sum(np.abs(y) * (np.abs(Linv) @ np.abs(m)))
+
+
+@pytest.mark.parametrize("name", ["shear_tiny", "shear39"])
+def test_emulator_bf16_against_bf16_aware_oracle(name):
+    inp, orc = oracle_for(name)
+    p = cuda_problem(name, "bf16", max_batch=64)
+    th = free_theta(inp, random_cube(37 if name == "shear_tiny" else 6, p.d, 31))
+    got = p.emulator(_t(th)).cpu().numpy()
+    worst_plain = 0.0
+    for b in range(len(th)):
+        full = _full(inp, th[b])
+        ref = orc.emulator(full, bf16=True).reshape(-1)
+        err = np.max(np.abs(got[b] - ref))
+        worst_plain = max(worst_plain, np.max(np.abs(got[b] - orc.emulator(full).reshape(-1))))
+        assert err < 2e-4, (b, err)
+    print(f"bf16 emulator vs FP64 emulator: max |d log10 P| = {worst_plain:.2e}")
+
+
+@pytest.mark.parametrize("name,prec", [("shear5", "fp32"), ("shear39", "fp32"), ("shear_tiny", "fp32"),
+                                       ("shear39", "bf16")])
+def test_loglike_reduced_precision_bound(name, prec):
+    inp, orc = oracle_for(name)
+    p = cuda_problem(name, prec, max_batch=64)
+    fid = np.asarray(inp["fiducial"])[free_indices(inp["priors"])]
+    rng = np.random.default_rng(41)
+    near = fid[None, :] * (1 + 1e-3 * rng.standard_normal((3, fid.size))) + 1e-4
+    far = free_theta(inp, random_cube(3, p.d, 42))
+    th = np.vstack([near, far])
+    got = p.loglike(_t(th)).cpu().numpy()
+    for b in range(len(th)):
+        full = _full(inp, th[b])
+        if prec == "bf16":
+            # the oracle with the bf16-rounded emulator: the remaining error is the FP32 stages'
+            class _O:  # noqa: N801
+                pass
+            save = orc.emulator
+            orc.emulator = lambda t, _s=save: _s(t, bf16=True)
+            try:
+                ref = orc.loglike_full(full)
+                bound = _fp32_bound(orc, full)
+            finally:
+                orc.emulator = save
+        else:
+            ref = orc.loglike_full(full)
+            bound = _fp32_bound(orc, full)
+        err = abs(got[b] - ref)
+        print(f"{name} {prec} row {b}: |dlogL| = {err:.3e}, bound {bound:.3e}, ratio {err / bound:.3f}")
+        assert err <= bound

@@ -337,3 +337,12 @@ def test_complex_step_matches_central_differences(tiny):
         tm[i] -= hstep
         fd = (o.loglike(tp) - o.loglike(tm)) / (2 * hstep)
         assert abs(fd - g[i]) <= 1e-5 * max(abs(g[i]), 1.0), (i, fd, g[i])
+
+
+def test_bf16_rounding_matches_library_conversion():
+    import torch
+    rng = np.random.default_rng(12)
+    a = np.concatenate([rng.standard_normal(2000) * 10.0 ** rng.integers(-6, 6, 2000),
+                        [1.0, 1.00390625, 1.005859375, -0.0, 65504.0]])
+    ref = torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).double().numpy()
+    assert np.array_equal(ShearOracle.to_bf16(a), ref)
