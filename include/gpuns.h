@@ -131,6 +131,7 @@ typedef struct {
 
 typedef struct ns_problem ns_problem;
 typedef struct ns_run ns_run;
+typedef struct ns_multi ns_multi;
 
 /* Nested-sampling settings (Sec. 2.1-2.2 and the recorded readings of the
  * slice-sampler internals). */
@@ -256,6 +257,29 @@ int ns_dead_points(const ns_run* r, long long max_out, double* x, double* logL,
 /* Record of the last completed iteration: L*, deleted live slots (k, ascending
  * (log L, slot)), start slots (k), evaluations per chain (k).  Any may be NULL. */
 int ns_last_iteration(const ns_run* r, double* lstar, int* deleted, int* starts, int* evals);
+
+/* Packed runs: n_runs independent nested-sampling runs (Sec. 2.1-2.2 each)
+ * whose problems share one likelihood model (same kind, precision, emulator,
+ * data and covariance: problems[0]'s model is used for every likelihood call)
+ * but may differ in their priors -- hence in their dimension, e.g. the 37-d
+ * LCDM and 39-d w0-wa models of one data set -- and in cfgs[i] (n_live,
+ * n_delete, seed, ...).  Every round packs the proposals of all runs' chains
+ * into one batch, tagged with the run index for the prior transform, and
+ * scores it with one likelihood launch; each run keeps its own iteration
+ * cycle, started and finished by the host between graph launches.
+ * Errors: NS_EINVAL for mismatched problems or n_runs outside [1, 64]. */
+int ns_multi_init(const ns_problem* const* problems, int n_runs, const ns_config* cfgs, void* stream,
+                  ns_multi** out);
+
+/* Each run not yet converged makes up to n_iters more iterations; st (may be
+ * NULL) receives n_runs statuses.  Synchronises the stream. */
+int ns_multi_step(ns_multi* m, int n_iters, ns_status* st);
+
+/* Borrow run i (for ns_evidence, ns_live_points, ns_dead_points, ...); it
+ * stays owned by m: do not ns_free it. */
+int ns_multi_run(const ns_multi* m, int i, ns_run** out);
+
+int ns_multi_free(ns_multi* m);
 
 /* Stage timing for roofline reporting: with stage != 0, every graph launch of
  * likelihood rounds records CUDA events on its stream around that stage in its

@@ -18,7 +18,8 @@ NS_PRIOR = {"U": 0, "N": 1, "F": 2}
 EXPORTS = ["ns_strerror", "ns_problem_create", "ns_problem_free", "ns_problem_dim", "ns_prior_transform",
            "loglike_batch", "ns_model_batch", "ns_emulator_batch", "loglike_grad_batch", "ns_init", "ns_step", "ns_evidence",
            "ns_live_points", "ns_dead_points", "ns_last_iteration", "ns_profile_stage", "ns_profile_read",
-           "ns_evidence_noalloc", "ns_free"]
+           "ns_evidence_noalloc", "ns_multi_init", "ns_multi_step", "ns_multi_run",
+           "ns_multi_free", "ns_free"]
 
 
 class Prior(C.Structure):
@@ -97,6 +98,10 @@ def load():
     lib.ns_profile_stage.argtypes = [vp, C.c_int]
     lib.ns_profile_read.argtypes = [vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     lib.ns_evidence_noalloc.argtypes = [vp, vp, C.c_longlong, C.c_ulonglong, C.c_int, vp, vp]
+    lib.ns_multi_init.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(Config), vp, C.POINTER(vp)]
+    lib.ns_multi_step.argtypes = [vp, C.c_int, C.POINTER(Status)]
+    lib.ns_multi_run.argtypes = [vp, C.c_int, C.POINTER(vp)]
+    lib.ns_multi_free.argtypes = [vp]
     lib.ns_free.argtypes = [vp]
     for name in EXPORTS:
         getattr(lib, name).restype = C.c_char_p if name == "ns_strerror" else C.c_int

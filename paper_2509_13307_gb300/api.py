@@ -340,3 +340,68 @@ class NestedRun:
             self.close()
         except Exception:
             pass
+
+
+class MultiRun:
+    """Several nested-sampling runs of one model packed into shared likelihood
+    batches (ns_multi_*).  problems share the model; each has its own priors."""
+
+    def __init__(self, problems, samplers, stream=None):
+        self.lib = problems[0].lib
+        self.problems = problems
+        n = len(problems)
+        arr = (C.c_void_p * n)(*[p.handle.value for p in problems])
+        cfgs = (L.Config * n)(*[L.Config(sc.n_live, sc.n_delete, 0 if sc.repeats is None else sc.repeats, sc.tol,
+                                         sc.seed, sc.width, sc.step_cap, sc.ridge, 0) for sc in samplers])
+        self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        L.check(self.lib.ns_multi_init(arr, n, cfgs, _stream(self._stream_obj), C.byref(h)), "ns_multi_init")
+        self._h = h
+        self.n = n
+        self.samplers = samplers
+
+    def step(self, n_iters: int = 1):
+        st = (L.Status * self.n)()
+        L.check(self.lib.ns_multi_step(self._h, n_iters, st), "ns_multi_step")
+        return [RunStatus(s.iterations, s.evaluations, s.rounds, bool(s.converged), s.status_bits, s.logZ, s.logX,
+                          s.lstar) for s in st]
+
+    def run(self, max_iters: int = 10 ** 9, chunk: int = 64):
+        sts = self.step(0)
+        while not all(s.converged for s in sts) and min(s.iterations for s in sts) < max_iters:
+            sts = self.step(chunk)
+        return sts
+
+    def _run(self, i):
+        r = C.c_void_p()
+        L.check(self.lib.ns_multi_run(self._h, i, C.byref(r)), "ns_multi_run")
+        return r
+
+    def evidence(self, i: int, n_replays: int = 200) -> dict:
+        lz, err, lx, H = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+        nd = C.c_longlong()
+        L.check(self.lib.ns_evidence(self._run(i), n_replays, C.byref(lz), C.byref(err), C.byref(lx), C.byref(H),
+                                     C.byref(nd)), "ns_evidence")
+        return dict(logZ=lz.value, logZ_err=err.value, logX=lx.value, H=H.value, n_dead=nd.value)
+
+    def last_iteration(self, i: int):
+        k = self.samplers[i].n_delete
+        lstar = C.c_double()
+        dele = np.empty(k, dtype=np.int32)
+        sta = np.empty(k, dtype=np.int32)
+        ev = np.empty(k, dtype=np.int32)
+        L.check(self.lib.ns_last_iteration(self._run(i), C.byref(lstar), dele.ctypes.data_as(C.c_void_p),
+                                           sta.ctypes.data_as(C.c_void_p), ev.ctypes.data_as(C.c_void_p)),
+                "ns_last_iteration")
+        return lstar.value, dele, sta, ev
+
+    def close(self):
+        if self._h:
+            self.lib.ns_multi_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

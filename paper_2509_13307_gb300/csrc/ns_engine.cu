@@ -60,7 +60,11 @@ struct RunDev {
     int* ch_step;
     int* ch_evals;
     int* ch_row;
-    double* prop;         // proposals (cap x d), cube coordinates
+    double* prop;         // proposals (rows x prop_stride), cube coordinates
+    int prop_stride;      // d for a single run; the largest d when runs share the batch
+    int* batch_ctr;       // row counter of the round's batch (shared by packed runs)
+    int* row_run;         // row -> run index when runs share the batch (else null)
+    int run_id;
     const double* logL;   // likelihood output per proposal row
     Scalars* sc;
     double* dead_x;
@@ -100,6 +104,12 @@ __global__ void k_init_points(int n, int d, unsigned long long seed, double* __r
         prop[(size_t)i * d + 2 * j] = u.a;
         if (2 * j + 1 < d) prop[(size_t)i * d + 2 * j + 1] = u.b;
     }
+}
+
+// Chains start finished with no pending proposal until their first iteration.
+__global__ void k_reset_chains(RunDev r) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < r.k) { r.ch_phase[c] = PH_DONE; r.ch_row[c] = -1; r.ch_evals[c] = 0; }
 }
 
 __global__ void k_init_finish(RunDev r, const double* __restrict__ logL) {
@@ -253,13 +263,9 @@ __global__ void k_chains_start(RunDev r) {
     if (c == 0) { r.sc->n_active = r.k; r.sc->batch = 0; }
 }
 
-// One warp per chain; lanes own dimensions lane and lane + 32.
-__global__ void __launch_bounds__(256) k_slice_advance(RunDev r) {
-    __shared__ double zs[8][64];
-    const int wib = threadIdx.x >> 5;
-    const int c = blockIdx.x * 8 + wib;
-    const int lane = threadIdx.x & 31;
-    if (c >= r.k) return;
+// One warp per chain; lanes own dimensions lane and lane + 32.  zsw: 64
+// doubles of shared memory owned by the warp.
+__device__ void advance_chain(const RunDev& r, int c, int lane, double* zsw) {
     int phase = r.ch_phase[c];
     if (phase == PH_DONE) return;
     const int d = r.d;
@@ -310,14 +316,14 @@ __global__ void __launch_bounds__(256) k_slice_advance(RunDev r) {
                 const double ang = 6.283185307179586 * g.b;
                 z0 = rad * cos(ang);
                 z1 = rad * sin(ang);
-                zs[wib][2 * lane] = z0;
-                if (2 * lane + 1 < d) zs[wib][2 * lane + 1] = z1; else z1 = 0.0;
+                zsw[2 * lane] = z0;
+                if (2 * lane + 1 < d) zsw[2 * lane + 1] = z1; else z1 = 0.0;
             }
             const double nrm = sqrt(warp_sum(z0 * z0 + z1 * z1));
             __syncwarp();
             double a0 = 0.0, a1 = 0.0;
-            if (has0) for (int b = 0; b <= lane; ++b) a0 += r.chol[lane * d + b] * (zs[wib][b] / nrm);
-            if (has1) for (int b = 0; b <= lane + 32; ++b) a1 += r.chol[(lane + 32) * d + b] * (zs[wib][b] / nrm);
+            if (has0) for (int b = 0; b <= lane; ++b) a0 += r.chol[lane * d + b] * (zsw[b] / nrm);
+            if (has1) for (int b = 0; b <= lane + 32; ++b) a1 += r.chol[(lane + 32) * d + b] * (zsw[b] / nrm);
             __syncwarp();
             u0v = a0; u1v = a1;
             const double s0 = philox_uniforms(r.seed, P_STEPOUT, 0, (uint32_t)it, (uint32_t)c, (uint32_t)move).a;
@@ -343,10 +349,13 @@ __global__ void __launch_bounds__(256) k_slice_advance(RunDev r) {
                 continue;
             }
             int rw = 0;
-            if (lane == 0) rw = atomicAdd(&r.sc->batch, 1);
+            if (lane == 0) {
+                rw = atomicAdd(r.batch_ctr, 1);
+                if (r.row_run) r.row_run[rw] = r.run_id;
+            }
             row = __shfl_sync(0xffffffffu, rw, 0);
-            if (has0) r.prop[(size_t)row * d + lane] = y0;
-            if (has1) r.prop[(size_t)row * d + lane + 32] = y1;
+            if (has0) r.prop[(size_t)row * r.prop_stride + lane] = y0;
+            if (has1) r.prop[(size_t)row * r.prop_stride + lane + 32] = y1;
             ++evals;
             break;
         }
@@ -368,10 +377,13 @@ __global__ void __launch_bounds__(256) k_slice_advance(RunDev r) {
                 continue;
             }
             int rw = 0;
-            if (lane == 0) rw = atomicAdd(&r.sc->batch, 1);
+            if (lane == 0) {
+                rw = atomicAdd(r.batch_ctr, 1);
+                if (r.row_run) r.row_run[rw] = r.run_id;
+            }
             row = __shfl_sync(0xffffffffu, rw, 0);
-            if (has0) r.prop[(size_t)row * d + lane] = y0;
-            if (has1) r.prop[(size_t)row * d + lane + 32] = y1;
+            if (has0) r.prop[(size_t)row * r.prop_stride + lane] = y0;
+            if (has1) r.prop[(size_t)row * r.prop_stride + lane + 32] = y1;
             ++evals;
             break;
         }
@@ -385,6 +397,28 @@ __global__ void __launch_bounds__(256) k_slice_advance(RunDev r) {
         if (flags) atomicOr(&r.sc->status, flags);
         if (phase == PH_DONE) atomicSub(&r.sc->n_active, 1);
     }
+}
+
+__global__ void __launch_bounds__(256) k_slice_advance(RunDev r) {
+    __shared__ double zs[8][64];
+    const int wib = threadIdx.x >> 5;
+    const int c = blockIdx.x * 8 + wib;
+    if (c >= r.k) return;
+    advance_chain(r, c, threadIdx.x & 31, zs[wib]);
+}
+
+// All chains of several packed runs: global warp g -> (run, chain) through the
+// prefix offsets chain_off[0..n_runs].
+__global__ void __launch_bounds__(256) k_slice_advance_multi(const RunDev* __restrict__ runs,
+                                                             const int* __restrict__ chain_off, int n_runs) {
+    __shared__ double zs[8][64];
+    const int wib = threadIdx.x >> 5;
+    const int g = blockIdx.x * 8 + wib;
+    if (g >= chain_off[n_runs]) return;
+    int r = 0;
+    while (r + 1 < n_runs && chain_off[r + 1] <= g) ++r;
+    const RunDev rd = runs[r];
+    advance_chain(rd, g - chain_off[r], threadIdx.x & 31, zs[wib]);
 }
 
 __global__ void k_insert(RunDev r) {
@@ -640,10 +674,14 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
     RA(sc, sizeof(Scalars));
 #undef RA
     rd.logL = r->ws.logL;
+    k_reset_chains<<<(k + 127) / 128, 128, 0, r->st>>>(rd);
+    rd.prop_stride = d;
+    rd.batch_ctr = &rd.sc->batch;
+    rd.row_run = nullptr;
+    rd.run_id = 0;
     r->sc = rd.sc;
     if (cudaMallocHost(&r->h_sc, sizeof(Scalars)) != cudaSuccess) return fail(NS_ENOMEM);
     std::memset(r->h_sc, 0, sizeof(Scalars));
-    if (cudaMemsetAsync(rd.ch_phase, 0xff, sizeof(int) * k, r->st) != cudaSuccess) return fail(NS_ECUDA);
     if (cudaMemsetAsync(rd.sc, 0, sizeof(Scalars), r->st) != cudaSuccess) return fail(NS_ECUDA);
     if ((s = grow_dead(r, 16LL * k + n))) return fail(s);
     // the workspace row count is the round's batch counter
@@ -817,5 +855,275 @@ extern "C" int ns_free(ns_run* r) {
     if (!r) return NS_EINVAL;
     cudaStreamSynchronize(r->st);
     run_release(r);
+    return NS_OK;
+}
+
+// ======================================================================
+// Packed runs (row A15): several independent runs of one model (same
+// emulator, data and covariance), each with its own priors (so its own
+// dimension), live-point count and deletion count.  Each run keeps its own
+// state and iteration cycle; their chains' proposals share one batch per
+// round, tagged with the run index, so one likelihood launch serves all.
+// ======================================================================
+namespace gpuns {
+
+__global__ void k_cube_to_theta_multi(const double* __restrict__ cube, int stride, const int* __restrict__ row_run,
+                                      int P, const int* __restrict__ kind, const double* __restrict__ pa,
+                                      const double* __restrict__ pb, const int* __restrict__ fof,
+                                      double* __restrict__ theta_full, const int* __restrict__ nrows) {
+    const int row = blockIdx.x;
+    if (row >= *nrows) return;
+    const int base = row_run[row] * P;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int f = fof[base + i];
+        double v;
+        if (f < 0) {
+            v = pa[base + i];
+        } else {
+            const double c = cube[(size_t)row * stride + f];
+            v = (kind[base + i] == NS_PRIOR_UNIFORM) ? pa[base + i] + (pb[base + i] - pa[base + i]) * c
+                                                      : pa[base + i] + pb[base + i] * normcdfinv(c);
+        }
+        theta_full[(size_t)row * P + i] = v;
+    }
+}
+
+}  // namespace gpuns
+
+struct ns_multi {
+    int n_runs = 0;
+    std::vector<ns_run*> runs;
+    const ns_problem* model = nullptr;
+    cudaStream_t st = nullptr;
+    cudaStream_t cap_st = nullptr;
+    Workspace ws;
+    int stride = 0, total_chains = 0;
+    double* prop = nullptr;
+    int* row_run = nullptr;
+    RunDev* d_runs = nullptr;
+    int* d_chain_off = nullptr;
+    int *d_kind = nullptr, *d_fof = nullptr;
+    double *d_pa = nullptr, *d_pb = nullptr;
+    std::vector<void*> owned;
+    cudaGraphExec_t graph = nullptr;
+    int graph_rounds = 0;
+    long long rounds = 0;
+    std::vector<int> state;           // 0 idle (start next iteration), 1 running
+};
+
+static void multi_release(ns_multi* m) {
+    if (!m) return;
+    if (m->graph) cudaGraphExecDestroy(m->graph);
+    if (m->cap_st) cudaStreamDestroy(m->cap_st);
+    for (ns_run* r : m->runs) run_release(r);
+    for (void* q : m->owned) cudaFree(q);
+    workspace_free(&m->ws);
+    delete m;
+}
+
+static int multi_refresh_runs(ns_multi* m) {
+    // device copies of every run's state with the packed batch fields
+    std::vector<RunDev> h(m->n_runs);
+    for (int i = 0; i < m->n_runs; ++i) {
+        h[i] = m->runs[i]->rd;
+        h[i].prop = m->prop;
+        h[i].prop_stride = m->stride;
+        h[i].batch_ctr = m->ws.d_nrows;
+        h[i].row_run = m->row_run;
+        h[i].run_id = i;
+        h[i].logL = m->ws.logL;
+    }
+    NS_CUDA_TRY(cudaMemcpyAsync(m->d_runs, h.data(), sizeof(RunDev) * m->n_runs, cudaMemcpyHostToDevice, m->st));
+    NS_CUDA_TRY(cudaStreamSynchronize(m->st));
+    return NS_OK;
+}
+
+static int multi_launch_round(ns_multi* m, cudaStream_t st) {
+    NS_CUDA_TRY(cudaMemsetAsync(m->ws.d_nrows, 0, sizeof(int), st));
+    k_slice_advance_multi<<<(m->total_chains + 7) / 8, 256, 0, st>>>(m->d_runs, m->d_chain_off, m->n_runs);
+    NS_CUDA_TRY(cudaGetLastError());
+    k_cube_to_theta_multi<<<m->total_chains, 64, 0, st>>>(m->prop, m->stride, m->row_run, m->model->P, m->d_kind,
+                                                          m->d_pa, m->d_pb, m->d_fof, m->ws.theta_full, m->ws.d_nrows);
+    NS_CUDA_TRY(cudaGetLastError());
+    return run_likelihood(m->model, &m->ws, m->total_chains, m->ws.logL, nullptr, st);
+}
+
+static int multi_build_graph(ns_multi* m, int rounds) {
+    if (m->graph) { cudaGraphExecDestroy(m->graph); m->graph = nullptr; }
+    if (!m->cap_st) NS_CUDA_TRY(cudaStreamCreateWithFlags(&m->cap_st, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    NS_CUDA_TRY(cudaStreamBeginCapture(m->cap_st, cudaStreamCaptureModeThreadLocal));
+    int s = NS_OK;
+    for (int i = 0; i < rounds && s == NS_OK; ++i) s = multi_launch_round(m, m->cap_st);
+    cudaError_t e = cudaStreamEndCapture(m->cap_st, &g);
+    if (s != NS_OK) { if (e == cudaSuccess) cudaGraphDestroy(g); return s; }
+    NS_CUDA_TRY(e);
+    e = cudaGraphInstantiate(&m->graph, g, 0);
+    cudaGraphDestroy(g);
+    NS_CUDA_TRY(e);
+    m->graph_rounds = rounds;
+    return NS_OK;
+}
+
+extern "C" int ns_multi_init(const ns_problem* const* problems, int n_runs, const ns_config* cfgs, void* stream,
+                             ns_multi** out) {
+    if (!problems || !cfgs || !out || n_runs < 1 || n_runs > 64) return NS_EINVAL;
+    *out = nullptr;
+    const ns_problem* p0 = problems[0];
+    if (!p0) return NS_EINVAL;
+    for (int i = 0; i < n_runs; ++i) {
+        const ns_problem* p = problems[i];
+        if (!p || p->kind != p0->kind || p->precision != p0->precision || p->P != p0->P || p->D != p0->D)
+            return NS_EINVAL;
+    }
+    ns_multi* m = new (std::nothrow) ns_multi();
+    if (!m) return NS_ENOMEM;
+    auto fail = [&](int s) { multi_release(m); return s; };
+    m->n_runs = n_runs;
+    m->model = p0;
+    m->st = (cudaStream_t)stream;
+    std::vector<int> off(n_runs + 1, 0);
+    for (int i = 0; i < n_runs; ++i) {
+        ns_run* r = nullptr;
+        int s = ns_init(problems[i], &cfgs[i], stream, &r);
+        if (s) return fail(s);
+        m->runs.push_back(r);
+        m->stride = std::max(m->stride, r->d);
+        off[i + 1] = off[i] + r->k;
+    }
+    m->total_chains = off[n_runs];
+    int s;
+    if ((s = workspace_create(p0, m->total_chains, &m->ws))) return fail(s);
+    void* v;
+    auto alloc = [&](size_t bytes) -> void* {
+        void* q = nullptr;
+        if (cudaMalloc(&q, bytes) != cudaSuccess) return nullptr;
+        m->owned.push_back(q);
+        return q;
+    };
+    const int P = p0->P;
+    m->prop = (double*)alloc(sizeof(double) * (size_t)m->total_chains * m->stride);
+    m->row_run = (int*)alloc(sizeof(int) * (size_t)m->total_chains);
+    m->d_runs = (RunDev*)alloc(sizeof(RunDev) * n_runs);
+    m->d_chain_off = (int*)alloc(sizeof(int) * (n_runs + 1));
+    m->d_kind = (int*)alloc(sizeof(int) * (size_t)n_runs * P);
+    m->d_fof = (int*)alloc(sizeof(int) * (size_t)n_runs * P);
+    m->d_pa = (double*)alloc(sizeof(double) * (size_t)n_runs * P);
+    m->d_pb = (double*)alloc(sizeof(double) * (size_t)n_runs * P);
+    if (!m->prop || !m->row_run || !m->d_runs || !m->d_chain_off || !m->d_kind || !m->d_fof || !m->d_pa || !m->d_pb)
+        return fail(NS_ENOMEM);
+    (void)v;
+    for (int i = 0; i < n_runs; ++i) {
+        const ns_problem* p = problems[i];
+        if (cudaMemcpy(m->d_kind + i * P, p->d_pkind, sizeof(int) * P, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+            cudaMemcpy(m->d_fof + i * P, p->d_free_of_full, sizeof(int) * P, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+            cudaMemcpy(m->d_pa + i * P, p->d_pa, sizeof(double) * P, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+            cudaMemcpy(m->d_pb + i * P, p->d_pb, sizeof(double) * P, cudaMemcpyDeviceToDevice) != cudaSuccess)
+            return fail(NS_ECUDA);
+    }
+    if (cudaMemcpy(m->d_chain_off, off.data(), sizeof(int) * (n_runs + 1), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(NS_ECUDA);
+    m->state.assign(n_runs, 0);
+    if ((s = multi_refresh_runs(m))) return fail(s);
+    *out = m;
+    return NS_OK;
+}
+
+static int multi_start_iteration(ns_multi* m, int i) {
+    ns_run* r = m->runs[i];
+    NS_TRY(grow_dead(r, r->h_sc->n_dead + r->k));
+    const size_t sm = (size_t)r->n_pad * (sizeof(double) + sizeof(int));
+    k_sort_delete<<<1, 1024, sm, m->st>>>(r->rd, r->n_pad, r->k, 1);
+    k_live_cov<<<r->d, 256, 0, m->st>>>(r->rd, r->cfg.ridge);
+    k_cholesky<<<1, 128, 0, m->st>>>(r->rd);
+    k_chains_start<<<(r->k + 127) / 128, 128, 0, m->st>>>(r->rd);
+    NS_CUDA_TRY(cudaGetLastError());
+    return NS_OK;
+}
+
+extern "C" int ns_multi_step(ns_multi* m, int n_iters, ns_status* st) {
+    if (!m || n_iters < 0) return NS_EINVAL;
+    const int nr = m->n_runs;
+    std::vector<int> todo(nr);
+    for (int i = 0; i < nr; ++i) {
+        NS_CUDA_TRY(cudaMemcpyAsync(m->runs[i]->h_sc, m->runs[i]->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, m->st));
+    }
+    NS_CUDA_TRY(cudaStreamSynchronize(m->st));
+    for (int i = 0; i < nr; ++i) todo[i] = m->runs[i]->h_sc->converged ? 0 : n_iters;
+    const int R = 16;
+    if (!m->graph || m->graph_rounds != R) NS_TRY(multi_build_graph(m, R));
+    long long guard = 0;
+    long long max_rounds = 0;
+    for (ns_run* r : m->runs) max_rounds = std::max(max_rounds, (long long)r->R * (3LL * r->cfg.step_cap + 2) + 8);
+    for (;;) {
+        bool started = false;
+        for (int i = 0; i < nr; ++i)
+            if (m->state[i] == 0 && todo[i] > 0) {
+                const long long cap_before = m->runs[i]->dead_cap;
+                NS_TRY(multi_start_iteration(m, i));
+                m->state[i] = 1;
+                started = true;
+                (void)cap_before;
+            }
+        if (started) { NS_TRY(multi_refresh_runs(m)); guard = 0; }
+        bool any = false;
+        for (int i = 0; i < nr; ++i) any = any || (m->state[i] == 1);
+        if (!any) break;
+        NS_CUDA_TRY(cudaGraphLaunch(m->graph, m->st));
+        m->rounds += R;
+        guard += R;
+        for (int i = 0; i < nr; ++i)
+            if (m->state[i] == 1)
+                NS_CUDA_TRY(cudaMemcpyAsync(m->runs[i]->h_sc, m->runs[i]->sc, sizeof(Scalars), cudaMemcpyDeviceToHost,
+                                            m->st));
+        NS_CUDA_TRY(cudaStreamSynchronize(m->st));
+        bool finished = false;
+        for (int i = 0; i < nr; ++i)
+            if (m->state[i] == 1 && m->runs[i]->h_sc->n_active == 0) {
+                k_insert<<<1, 1024, 0, m->st>>>(m->runs[i]->rd);
+                NS_CUDA_TRY(cudaGetLastError());
+                m->state[i] = 2;
+                finished = true;
+            }
+        if (finished) {
+            for (int i = 0; i < nr; ++i)
+                if (m->state[i] == 2)
+                    NS_CUDA_TRY(cudaMemcpyAsync(m->runs[i]->h_sc, m->runs[i]->sc, sizeof(Scalars),
+                                                cudaMemcpyDeviceToHost, m->st));
+            NS_CUDA_TRY(cudaStreamSynchronize(m->st));
+            for (int i = 0; i < nr; ++i)
+                if (m->state[i] == 2) {
+                    m->state[i] = 0;
+                    m->runs[i]->last_valid = 1;
+                    todo[i] = m->runs[i]->h_sc->converged ? 0 : todo[i] - 1;
+                }
+        }
+        if (guard > max_rounds) return NS_ETIMEOUT;
+    }
+    if (st)
+        for (int i = 0; i < nr; ++i) {
+            const Scalars* h = m->runs[i]->h_sc;
+            st[i].iterations = h->iter;
+            st[i].evaluations = h->evals;
+            st[i].rounds = m->rounds;
+            st[i].converged = h->converged;
+            st[i].status_bits = h->status;
+            st[i].logZ = h->logZ;
+            st[i].logX = h->logX;
+            st[i].lstar = h->lstar;
+        }
+    return NS_OK;
+}
+
+extern "C" int ns_multi_run(const ns_multi* m, int i, ns_run** out) {
+    if (!m || !out || i < 0 || i >= m->n_runs) return NS_EINVAL;
+    *out = m->runs[i];
+    return NS_OK;
+}
+
+extern "C" int ns_multi_free(ns_multi* m) {
+    if (!m) return NS_EINVAL;
+    cudaStreamSynchronize(m->st);
+    multi_release(m);
     return NS_OK;
 }

@@ -288,3 +288,27 @@ def cmb6(n_ell: int = 2507, **sampler_kw) -> CMBConfig:
     kw.update(sampler_kw)
     return CMBConfig(name="cmb6", n_ell=n_ell, emu_hidden=(512,) * 4,
                      sampler=SamplerConfig(**kw))
+
+
+def shear39_interp(**sampler_kw) -> ShearConfig:
+    """shear39 with the emulator evaluated on 10 coarse z nodes, Catmull-Rom
+    interpolated to the 50-node table (output 200 k x 10 z = 2000)."""
+    return replace(shear39(**sampler_kw), name="shear39_interp", coarse_z=10)
+
+
+def shear37_interp(**sampler_kw) -> ShearConfig:
+    return replace(shear37_lcdm(**sampler_kw), name="shear37_interp", coarse_z=10)
+
+
+def uneven_runs():
+    """The packed-runs workload: (model, dimension, n_live) for eight runs with
+    k = n_live / 2, all on the interpolated emulator."""
+    spec = [("lcdm", 250), ("w0wa", 500), ("lcdm", 1000), ("w0wa", 2000), ("w0wa33", 250),
+            ("w0wa", 1000), ("lcdm", 500), ("w0wa", 250)]
+    out = []
+    for i, (model, n) in enumerate(spec):
+        base = {"lcdm": shear37_interp, "w0wa": shear39_interp,
+                "w0wa33": lambda **kw: replace(shear39_interp(**kw), name="shear33_interp",
+                                               fixed={f"b_{t}": 0.0 for t in range(12, 18)})}[model]
+        out.append(base(n_live=n, n_delete=n // 2, seed=3 + i))
+    return out
