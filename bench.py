@@ -146,6 +146,11 @@ def projection_flops_per_eval(cfg) -> float:
             + D * (3 + 2 * cfg.n_tmpl))
 
 
+def replace_seed(sc, rank):
+    from dataclasses import replace
+    return replace(sc, seed=sc.seed + 100 * rank)
+
+
 def fp32_alu_peak_tflops(sm_mhz: float) -> float:
     """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -160,6 +165,7 @@ def main():
     ap.add_argument("--precision", default="bf16")
     ap.add_argument("--no-full-run", action="store_true", help="skip the time-to-converged-logZ run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-multi", action="store_true", help="skip the packed-runs measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -329,6 +335,37 @@ def ours(args):
         pg.close()
     except Exception as exc:  # report, do not hide, a failure of this extra measurement
         extra["grad_error"] = repr(exc)[:200]
+
+    # ---------------- packed uneven runs (8 runs, interpolated emulator)
+    if not args.no_multi:
+        try:
+            from paper_2509_13307_gb300 import MultiRun
+            cfgs = w.uneven_runs()
+            base = w.make_shear_inputs(cfgs[1])
+            probs = []
+            for c in cfgs:
+                ci = w.make_shear_inputs(c)
+                probs.append(Problem(ci, args.precision, max_batch=c.sampler.n_live,
+                                     data=None if not probs else probs[0].data,
+                                     cov=None if not probs else probs[0].cov))
+            mr = MultiRun(probs, [replace_seed(c.sampler, rank) for c in cfgs])
+            mr.step(1)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            ev0 = sum(s.evaluations for s in mr.step(0))
+            e0.record(stream)
+            sts = mr.step(2)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            extra["packed_runs_evals_per_s"] = (sum(s.evaluations for s in sts) - ev0) / (e0.elapsed_time(e1) / 1e3)
+            extra["packed_runs"] = "8 runs, d in {37, 39, 33}, n_live in {250, 500, 1000, 2000}, k = n/2, emulator on 10 z nodes interpolated to 50"
+            mr.close()
+            for q in probs:
+                q.close()
+            del base
+        except Exception as exc:
+            extra["packed_runs_error"] = repr(exc)[:200]
 
     # ---------------- wall time to a converged log Z (BF16), from ns_init
     if not args.no_full_run:

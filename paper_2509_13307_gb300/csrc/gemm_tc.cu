@@ -128,7 +128,9 @@ __device__ __forceinline__ float tanh_fast(float x) {
 
 template <int BN>
 struct Cfg {
-    static constexpr int STAGES = (BN >= 256) ? 3 : 4;
+    // as many stages as fit in ~200 KB of shared memory (more bytes in flight
+    // hide the TMA latency; the tiles here are L2-resident)
+    static constexpr int STAGES = (BN >= 256) ? 4 : (BN >= 128 ? 6 : 8);
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -288,6 +290,7 @@ int launch_gemm_tc(const CUtensorMap* tmA, const CUtensorMap* tmB, int tile_n, c
                    int epi, int* d_err, cudaStream_t st) {
     if (grid_rows <= 0) return NS_OK;
     switch (tile_n) {
+        case 32: return tc::launch_bn<32>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, d_err, st);
         case 64: return tc::launch_bn<64>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, d_err, st);
         case 128: return tc::launch_bn<128>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, d_err, st);
         case 256: return tc::launch_bn<256>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, d_err, st);
