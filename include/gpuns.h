@@ -198,6 +198,12 @@ int ns_model_batch(const ns_problem* p, const double* theta_dev, int B,
 int ns_emulator_batch(const ns_problem* p, const double* theta_dev, int B,
                       double* out_dev, void* stream);
 
+/* Device status bits of the problem's batch calls (NS_BIT_TIMEOUT: a bounded
+ * device wait inside a likelihood kernel gave up; the affected rows are NaN).
+ * Synchronises the device first; clear != 0 resets the bits.  Runs check the
+ * same bits at every host synchronisation and stop with NS_ETIMEOUT. */
+int ns_problem_status(ns_problem* p, int* bits, int clear);
+
 /* Log-likelihood and its gradient d log L / d theta (B x d) by a hand-written
  * adjoint of the likelihood stages.  NS_ENOTSUP where not built. */
 int loglike_grad_batch(const ns_problem* p, const double* theta_dev, int B,
@@ -283,9 +289,11 @@ int ns_multi_free(ns_multi* m);
 
 /* Stage timing for roofline reporting: with stage != 0, every graph launch of
  * likelihood rounds records CUDA events on its stream around that stage in its
- * first round (1 = shear projection kernel: background, windows, P lookup,
- * Limber, data vector; 2 = emulator output GEMM; 3 = whitening / chi^2;
- * 4 = first hidden emulator GEMM) and the stage's batch size.  0 turns it off.
+ * first round (1 = shear Limber stage: P lookup, Limber sums, data vector,
+ * including any wait for the windows stage; 2 = emulator output GEMM;
+ * 3 = whitening / chi^2; 4 = first hidden emulator GEMM; 5 = shear windows
+ * stage: distances, growth, windows, on its own stream beside the emulator)
+ * and the stage's batch size.  0 turns it off.
  * Resets the accumulators. */
 int ns_profile_stage(ns_run* r, int stage);
 

@@ -201,6 +201,13 @@ class Problem:
                                            _stream(stream)), "ns_emulator_batch")
         return out
 
+    def device_status(self, clear: bool = False) -> int:
+        """Status bits of earlier batch calls (NS_BIT_TIMEOUT = 4: a bounded
+        device wait gave up and the affected rows are NaN).  Synchronises."""
+        bits = C.c_int(0)
+        L.check(self.lib.ns_problem_status(self._h, C.byref(bits), int(clear)), "ns_problem_status")
+        return bits.value
+
     def prior_transform(self, cube: torch.Tensor, stream=None) -> torch.Tensor:
         cube = _require_cuda(cube, "cube")
         out = torch.empty_like(cube)
@@ -320,7 +327,7 @@ class NestedRun:
                 "ns_last_iteration")
         return lstar.value, dele, sta, ev
 
-    STAGES = {"off": 0, "projection": 1, "emu_out": 2, "chi2": 3, "emu_hidden": 4}
+    STAGES = {"off": 0, "projection": 1, "emu_out": 2, "chi2": 3, "emu_hidden": 4, "windows": 5}
 
     def profile_stage(self, stage: str):
         L.check(self.lib.ns_profile_stage(self._h, self.STAGES[stage]), "ns_profile_stage")

@@ -304,7 +304,7 @@ static int run_emulator_bf16(const ns_problem* p, Workspace* ws, int grid_rows, 
         NS_TRY(probe_begin(probe, stage, ws, st));
         NS_TRY(launch_gemm_tc(&ws->tmA[l], &p->tmB[l], p->tile_n[l], (const float*)p->d_b[l],
                               (const float*)p->d_out_mu, (float)p->out_sigma, out, ws->d_nrows, grid_rows,
-                              N, K, last ? 1 : 0, nullptr, st));
+                              N, K, last ? 1 : 0, ws->d_err, st));
         NS_TRY(probe_end(probe, stage, st));
         cur ^= 1;
     }
@@ -347,7 +347,19 @@ int run_likelihood(const ns_problem* p, Workspace* ws, int grid_rows, double* lo
     }
     const ShearParams& sp = p->sp;
     const bool coarse = p->n_z_emu != sp.n_z;
-    if (p->precision == NS_PREC_FP64) {
+    const bool f64 = p->precision == NS_PREC_FP64;
+    // fork: the windows stage needs only theta, so it runs on the side stream
+    // while the emulator runs on `st`; the Limber stage joins both.
+    NS_CUDA_TRY(cudaEventRecord(ws->ev_fork, st));
+    NS_CUDA_TRY(cudaStreamWaitEvent(ws->side, ws->ev_fork, 0));
+    NS_TRY(probe_begin(probe, PROBE_WINDOWS, ws, ws->side));
+    if (f64) NS_TRY(launch_windows<double, false>(sp, ws->theta_full, (double*)ws->win, ws->d_nrows, grid_rows, ws->side));
+    else if (p->precision == NS_PREC_FP32)
+        NS_TRY(launch_windows<float, false>(sp, ws->theta_full, (float*)ws->win, ws->d_nrows, grid_rows, ws->side));
+    else NS_TRY(launch_windows<float, true>(sp, ws->theta_full, (float*)ws->win, ws->d_nrows, grid_rows, ws->side));
+    NS_TRY(probe_end(probe, PROBE_WINDOWS, ws->side));
+    NS_CUDA_TRY(cudaEventRecord(ws->ev_join, ws->side));
+    if (f64) {
         NS_TRY(run_emulator_simt<double>(p, ws, grid_rows, st));
         const double* tab = (const double*)ws->table;
         if (coarse) {
@@ -357,8 +369,9 @@ int run_likelihood(const ns_problem* p, Workspace* ws, int grid_rows, double* lo
             NS_CUDA_TRY(cudaGetLastError());
             tab = (const double*)ws->table_fine;
         }
-        NS_TRY(launch_projection<double, false>(sp, ws->theta_full, tab, (double*)ws->resid, model_out,
-                                                ws->d_nrows, grid_rows, st));
+        NS_CUDA_TRY(cudaStreamWaitEvent(st, ws->ev_join, 0));
+        NS_TRY(launch_limber<double, false>(sp, ws->theta_full, tab, (const double*)ws->win, (double*)ws->resid,
+                                            model_out, ws->d_nrows, grid_rows, ws->d_err, st));
         if (model_out) return NS_OK;
         return launch_chi2<double, double>((const double*)ws->resid, sp.D, p->d_LinvT64, p->c0, logL_out,
                                            ws->chi2_part, ws->d_nrows, grid_rows, st);
@@ -374,13 +387,14 @@ int run_likelihood(const ns_problem* p, Workspace* ws, int grid_rows, double* lo
         NS_CUDA_TRY(cudaGetLastError());
         tab = (const float*)ws->table_fine;
     }
+    NS_CUDA_TRY(cudaStreamWaitEvent(st, ws->ev_join, 0));
     NS_TRY(probe_begin(probe, PROBE_PROJECTION, ws, st));
     if (p->precision == NS_PREC_FP32)
-        NS_TRY(launch_projection<float, false>(sp, ws->theta_full, tab, (float*)ws->resid, model_out, ws->d_nrows,
-                                               grid_rows, st));
+        NS_TRY(launch_limber<float, false>(sp, ws->theta_full, tab, (const float*)ws->win, (float*)ws->resid,
+                                           model_out, ws->d_nrows, grid_rows, ws->d_err, st));
     else
-        NS_TRY(launch_projection<float, true>(sp, ws->theta_full, tab, (float*)ws->resid, model_out, ws->d_nrows,
-                                              grid_rows, st));
+        NS_TRY(launch_limber<float, true>(sp, ws->theta_full, tab, (const float*)ws->win, (float*)ws->resid,
+                                          model_out, ws->d_nrows, grid_rows, ws->d_err, st));
     NS_TRY(probe_end(probe, PROBE_PROJECTION, st));
     if (model_out) return NS_OK;
     NS_TRY(probe_begin(probe, PROBE_CHI2, ws, st));

@@ -38,16 +38,22 @@ struct ShearParams {
 struct Workspace {
     int cap = 0;
     int* d_nrows = nullptr;       // device row count used by every stage
+    int* d_err = nullptr;         // device status bits (NS_BIT_TIMEOUT when a bounded wait gave up)
+    int* h_err = nullptr;         // pinned mirror of d_err
     double* theta_full = nullptr; // cap x P
     void* act[2] = {nullptr, nullptr};
     void* table = nullptr;        // cap x n_out (emulator output)
     void* table_fine = nullptr;   // cap x n_z*n_k (coarse-z emulators)
     void* resid = nullptr;        // cap x D residuals
+    void* win = nullptr;          // cap x (nb + 1) x pitch: ln chi and windows (pitch = N rounded up to 4)
     void* chi2_part = nullptr;    // cap x ceil(D / 64) partial chi^2 sums (FP64-sized)
     double* logL = nullptr;       // cap
     // tcgen05 tensor maps (BF16 precision): A operand of layer l >= 1 and its output
     std::vector<CUtensorMap> tmA;
     std::vector<void*> owned;
+    // second stream for the emulator-independent windows stage; fork/join events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 }  // namespace gpuns
@@ -90,6 +96,10 @@ struct ns_problem {
 namespace gpuns {
 
 int workspace_create(const ns_problem* p, int cap, Workspace* ws);
+// Queue a copy of the device status bits into the pinned mirror on `st`; after
+// the stream has synchronised, workspace_err_bits returns them.
+int workspace_err_fetch(Workspace* ws, cudaStream_t st);
+inline int workspace_err_bits(const Workspace* ws) { return ws->h_err ? *ws->h_err : 0; }
 void workspace_free(Workspace* ws);
 
 // Full likelihood pipeline on rows [0, *d_nrows) of ws->theta_full; grid_rows
@@ -97,7 +107,9 @@ void workspace_free(Workspace* ws);
 // model_out != nullptr, the shear model vectors (FP64, rows x D) instead.
 // Optional probe around one likelihood stage: events recorded on the launch
 // stream before/after it and the stage's row count copied to pinned memory.
-enum ProbeStage { PROBE_NONE = 0, PROBE_PROJECTION = 1, PROBE_EMU_OUT = 2, PROBE_CHI2 = 3, PROBE_EMU_HIDDEN = 4 };
+enum ProbeStage {
+    PROBE_NONE = 0, PROBE_PROJECTION = 1, PROBE_EMU_OUT = 2, PROBE_CHI2 = 3, PROBE_EMU_HIDDEN = 4, PROBE_WINDOWS = 5
+};
 struct StageProbe {
     int stage = PROBE_NONE;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -114,12 +126,19 @@ int run_emulator_only(const ns_problem* p, Workspace* ws, int grid_rows, double*
 int launch_cube_to_theta(const ns_problem* p, Workspace* ws, const double* cube, int grid_rows,
                          cudaStream_t st);
 
-// Shear projection (projection.cu): residual d - m per row, or the model
-// vectors when model_out != nullptr.  FAST selects SFU transcendentals.
+// Shear projection (projection.cu), two stages.  Windows: per row ln chi and
+// the lensing/IA windows into `win` (rows x (nb + 1) x N); independent of the
+// emulator, so it may run on a second stream beside it.  Limber: P lookup,
+// Limber sums and the data vector; writes the residual d - m per row, or the
+// model vectors when model_out != nullptr.  FAST selects SFU transcendentals.
 template <typename T, bool FAST>
-int launch_projection(const ShearParams& sp, const double* theta_full, const T* table, T* resid, double* model_out,
-                      const int* nrows, int grid_rows, cudaStream_t st);
-size_t projection_smem_bytes(const ShearParams& sp, int elt, int elt_acc);
+int launch_windows(const ShearParams& sp, const double* theta_full, T* win, const int* nrows, int grid_rows,
+                   cudaStream_t st);
+template <typename T, bool FAST>
+int launch_limber(const ShearParams& sp, const double* theta_full, const T* table, const T* win, T* resid,
+                  double* model_out, const int* nrows, int grid_rows, int* err, cudaStream_t st);
+// Whether both projection stages fit the shared memory of one CTA (elt = 4 or 8).
+bool projection_fits(const ShearParams& sp, int elt);
 // Whitened chi^2 and log L = c0 - chi^2 / 2 (projection.cu).
 template <typename TR, typename TA>
 int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL, void* partial, const int* nrows,

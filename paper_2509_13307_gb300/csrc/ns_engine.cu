@@ -7,6 +7,7 @@
 //                   deletions with n, n-1, ..., n-k+1 live points (Sec. 2.2).
 //   k_live_cov      covariance (ddof 1) of all n live cube points + ridge.
 //   k_cholesky      FP64 Cholesky of that covariance (one block).
+//   k_directions    every (chain, move) slice direction of the iteration.
 //   k_chains_start  chain c starts at survivor floor(u (n - k)) (Philox START).
 //   rounds          until every chain has made R slice moves: k_slice_advance
 //                   (one warp per chain) consumes the previous proposal's log L,
@@ -49,6 +50,7 @@ struct RunDev {
     int* starts;
     double* chol;
     double* cov;
+    double* dirs;         // k x R x d slice directions u = L_Sigma z / |z| of the iteration
     double* ch_x;
     double* ch_u;
     double* ch_L;
@@ -263,9 +265,48 @@ __global__ void k_chains_start(RunDev r) {
     if (c == 0) { r.sc->n_active = r.k; r.sc->batch = 0; }
 }
 
-// One warp per chain; lanes own dimensions lane and lane + 32.  zsw: 64
-// doubles of shared memory owned by the warp.
-__device__ void advance_chain(const RunDev& r, int c, int lane, double* zsw) {
+// Slice directions for every (chain, move) of the iteration, one warp each:
+// z ~ N(0, I) by Box-Muller on the Philox DIR chunks, u = L_Sigma (z / |z|).
+// They depend only on the counters and the iteration's Cholesky factor, so
+// they are formed once, fully parallel, instead of inside the latency-bound
+// round (FP64 transcendentals run at a small fraction of the FP32 rate).
+__global__ void __launch_bounds__(256) k_directions(RunDev r) {
+    __shared__ double zs[8][64];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long g = (long long)blockIdx.x * 8 + wib;
+    if (g >= (long long)r.k * r.R) return;
+    const int c = (int)(g / r.R), move = (int)(g % r.R);
+    const int d = r.d;
+    const int it = (int)r.sc->iter;
+    double* zsw = zs[wib];
+    const int nch = (d + 1) / 2;
+    double z0 = 0.0, z1 = 0.0;
+    if (lane < nch) {
+        const Draw2 q = philox_uniforms(r.seed, P_DIR, lane, (uint32_t)it, (uint32_t)c, (uint32_t)move);
+        const double rad = sqrt(-2.0 * log(q.a));
+        const double ang = 6.283185307179586 * q.b;
+        z0 = rad * cos(ang);
+        z1 = rad * sin(ang);
+        zsw[2 * lane] = z0;
+        if (2 * lane + 1 < d) zsw[2 * lane + 1] = z1; else z1 = 0.0;
+    }
+    const double nrm = sqrt(warp_sum(z0 * z0 + z1 * z1));
+    __syncwarp();
+    double* out = r.dirs + (size_t)g * d;
+    if (lane < d) {
+        double a0 = 0.0;
+        for (int b = 0; b <= lane; ++b) a0 += r.chol[lane * d + b] * (zsw[b] / nrm);
+        out[lane] = a0;
+    }
+    if (lane + 32 < d) {
+        double a1 = 0.0;
+        for (int b = 0; b <= lane + 32; ++b) a1 += r.chol[(lane + 32) * d + b] * (zsw[b] / nrm);
+        out[lane + 32] = a1;
+    }
+}
+
+// One warp per chain; lanes own dimensions lane and lane + 32.
+__device__ void advance_chain(const RunDev& r, int c, int lane) {
     int phase = r.ch_phase[c];
     if (phase == PH_DONE) return;
     const int d = r.d;
@@ -307,25 +348,10 @@ __device__ void advance_chain(const RunDev& r, int c, int lane, double* zsw) {
     for (int guard = 0; guard < 4 * r.cap_steps + 8; ++guard) {
         if (phase == PH_NEWMOVE) {
             if (move >= r.R) { phase = PH_DONE; break; }
-            // direction: z ~ N(0, I) (Box-Muller on Philox DIR chunks), u = L_Sigma z / |z|
-            const int nch = (d + 1) / 2;
-            double z0 = 0.0, z1 = 0.0;
-            if (lane < nch) {
-                const Draw2 g = philox_uniforms(r.seed, P_DIR, lane, (uint32_t)it, (uint32_t)c, (uint32_t)move);
-                const double rad = sqrt(-2.0 * log(g.a));
-                const double ang = 6.283185307179586 * g.b;
-                z0 = rad * cos(ang);
-                z1 = rad * sin(ang);
-                zsw[2 * lane] = z0;
-                if (2 * lane + 1 < d) zsw[2 * lane + 1] = z1; else z1 = 0.0;
-            }
-            const double nrm = sqrt(warp_sum(z0 * z0 + z1 * z1));
-            __syncwarp();
-            double a0 = 0.0, a1 = 0.0;
-            if (has0) for (int b = 0; b <= lane; ++b) a0 += r.chol[lane * d + b] * (zsw[b] / nrm);
-            if (has1) for (int b = 0; b <= lane + 32; ++b) a1 += r.chol[(lane + 32) * d + b] * (zsw[b] / nrm);
-            __syncwarp();
-            u0v = a0; u1v = a1;
+            // direction of this move (k_directions)
+            const double* dir = r.dirs + ((size_t)c * r.R + move) * d;
+            u0v = has0 ? dir[lane] : 0.0;
+            u1v = has1 ? dir[lane + 32] : 0.0;
             const double s0 = philox_uniforms(r.seed, P_STEPOUT, 0, (uint32_t)it, (uint32_t)c, (uint32_t)move).a;
             l = __dmul_rn(-w, s0);
             rr = l + w;
@@ -400,25 +426,21 @@ __device__ void advance_chain(const RunDev& r, int c, int lane, double* zsw) {
 }
 
 __global__ void __launch_bounds__(256) k_slice_advance(RunDev r) {
-    __shared__ double zs[8][64];
-    const int wib = threadIdx.x >> 5;
-    const int c = blockIdx.x * 8 + wib;
+    const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (c >= r.k) return;
-    advance_chain(r, c, threadIdx.x & 31, zs[wib]);
+    advance_chain(r, c, threadIdx.x & 31);
 }
 
 // All chains of several packed runs: global warp g -> (run, chain) through the
 // prefix offsets chain_off[0..n_runs].
 __global__ void __launch_bounds__(256) k_slice_advance_multi(const RunDev* __restrict__ runs,
                                                              const int* __restrict__ chain_off, int n_runs) {
-    __shared__ double zs[8][64];
-    const int wib = threadIdx.x >> 5;
-    const int g = blockIdx.x * 8 + wib;
+    const int g = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (g >= chain_off[n_runs]) return;
     int r = 0;
     while (r + 1 < n_runs && chain_off[r + 1] <= g) ++r;
     const RunDev rd = runs[r];
-    advance_chain(rd, g - chain_off[r], threadIdx.x & 31, zs[wib]);
+    advance_chain(rd, g - chain_off[r], threadIdx.x & 31);
 }
 
 __global__ void k_insert(RunDev r) {
@@ -584,7 +606,12 @@ static int grow_dead(ns_run* r, long long need) {
 
 static int sync_scalars(ns_run* r) {
     NS_CUDA_TRY(cudaMemcpyAsync(r->h_sc, r->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, r->st));
+    NS_TRY(workspace_err_fetch(&r->ws, r->st));
     NS_CUDA_TRY(cudaStreamSynchronize(r->st));
+    if (const int bits = workspace_err_bits(&r->ws)) {
+        r->h_sc->status |= bits;
+        return NS_ETIMEOUT;
+    }
     return NS_OK;
 }
 
@@ -659,6 +686,7 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
     RA(starts, sizeof(int) * k);
     RA(chol, sizeof(double) * d * d);
     RA(cov, sizeof(double) * d * d);
+    RA(dirs, sizeof(double) * (size_t)k * r->R * d);
     RA(ch_x, sizeof(double) * k * d);
     RA(ch_u, sizeof(double) * k * d);
     RA(ch_L, sizeof(double) * k);
@@ -713,6 +741,7 @@ static int one_iteration(ns_run* r) {
     NS_CUDA_TRY(cudaGetLastError());
     k_live_cov<<<r->d, 256, 0, st>>>(rd, r->cfg.ridge);
     k_cholesky<<<1, 128, 0, st>>>(rd);
+    k_directions<<<(unsigned)(((long long)r->k * r->R + 7) / 8), 256, 0, st>>>(rd);
     k_chains_start<<<(r->k + 127) / 128, 128, 0, st>>>(rd);
     NS_CUDA_TRY(cudaGetLastError());
     const int R = rounds_per_sync(r);
@@ -827,7 +856,7 @@ extern "C" int ns_last_iteration(const ns_run* r, double* lstar, int* deleted, i
 }
 
 extern "C" int ns_profile_stage(ns_run* r, int stage) {
-    if (!r || stage < PROBE_NONE || stage > PROBE_EMU_HIDDEN) return NS_EINVAL;
+    if (!r || stage < PROBE_NONE || stage > PROBE_WINDOWS) return NS_EINVAL;
     NS_CUDA_TRY(cudaStreamSynchronize(r->st));
     if (stage != PROBE_NONE && !r->probe.ev0) {
         NS_CUDA_TRY(cudaEventCreate(&r->probe.ev0));
@@ -1036,6 +1065,7 @@ static int multi_start_iteration(ns_multi* m, int i) {
     k_sort_delete<<<1, 1024, sm, m->st>>>(r->rd, r->n_pad, r->k, 1);
     k_live_cov<<<r->d, 256, 0, m->st>>>(r->rd, r->cfg.ridge);
     k_cholesky<<<1, 128, 0, m->st>>>(r->rd);
+    k_directions<<<(unsigned)(((long long)r->k * r->R + 7) / 8), 256, 0, m->st>>>(r->rd);
     k_chains_start<<<(r->k + 127) / 128, 128, 0, m->st>>>(r->rd);
     NS_CUDA_TRY(cudaGetLastError());
     return NS_OK;
@@ -1076,7 +1106,12 @@ extern "C" int ns_multi_step(ns_multi* m, int n_iters, ns_status* st) {
             if (m->state[i] == 1)
                 NS_CUDA_TRY(cudaMemcpyAsync(m->runs[i]->h_sc, m->runs[i]->sc, sizeof(Scalars), cudaMemcpyDeviceToHost,
                                             m->st));
+        NS_TRY(workspace_err_fetch(&m->ws, m->st));
         NS_CUDA_TRY(cudaStreamSynchronize(m->st));
+        if (const int bits = workspace_err_bits(&m->ws)) {
+            for (ns_run* r : m->runs) r->h_sc->status |= bits;
+            return NS_ETIMEOUT;
+        }
         bool finished = false;
         for (int i = 0; i < nr; ++i)
             if (m->state[i] == 1 && m->runs[i]->h_sc->n_active == 0) {

@@ -99,6 +99,11 @@ int workspace_create(const ns_problem* p, int cap, Workspace* ws) {
     void* v;
     NS_TRY(dalloc(sizeof(int), &v, ws->owned));
     ws->d_nrows = (int*)v;
+    NS_TRY(dalloc(sizeof(int), &v, ws->owned));
+    ws->d_err = (int*)v;
+    NS_CUDA_TRY(cudaMemset(ws->d_err, 0, sizeof(int)));
+    if (cudaMallocHost(&ws->h_err, sizeof(int)) != cudaSuccess) return NS_ENOMEM;
+    *ws->h_err = 0;
     NS_TRY(dalloc(sizeof(double) * (size_t)cap * p->P, &v, ws->owned));
     ws->theta_full = (double*)v;
     NS_TRY(dalloc(sizeof(double) * (size_t)cap, &v, ws->owned));
@@ -121,6 +126,11 @@ int workspace_create(const ns_problem* p, int cap, Workspace* ws) {
     }
     NS_TRY(dalloc((size_t)tab_elt * cap * p->sp.D, &v, ws->owned));
     ws->resid = v;
+    NS_TRY(dalloc((size_t)tab_elt * cap * (p->sp.nb + 1) * ((p->sp.N + 3) & ~3), &v, ws->owned));
+    ws->win = v;
+    NS_CUDA_TRY(cudaStreamCreateWithFlags(&ws->side, cudaStreamNonBlocking));
+    NS_CUDA_TRY(cudaEventCreateWithFlags(&ws->ev_fork, cudaEventDisableTiming));
+    NS_CUDA_TRY(cudaEventCreateWithFlags(&ws->ev_join, cudaEventDisableTiming));
     NS_TRY(dalloc(sizeof(double) * (size_t)cap * ((p->sp.D + 63) / 64), &v, ws->owned));
     ws->chi2_part = v;
 
@@ -135,9 +145,21 @@ int workspace_create(const ns_problem* p, int cap, Workspace* ws) {
     return NS_OK;
 }
 
+int workspace_err_fetch(Workspace* ws, cudaStream_t st) {
+    NS_CUDA_TRY(cudaMemcpyAsync(ws->h_err, ws->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return NS_OK;
+}
+
 void workspace_free(Workspace* ws) {
     for (void* q : ws->owned) cudaFree(q);
     ws->owned.clear();
+    if (ws->h_err) cudaFreeHost(ws->h_err);
+    ws->h_err = nullptr;
+    if (ws->ev_fork) cudaEventDestroy(ws->ev_fork);
+    if (ws->ev_join) cudaEventDestroy(ws->ev_join);
+    if (ws->side) cudaStreamDestroy(ws->side);
+    ws->ev_fork = ws->ev_join = nullptr;
+    ws->side = nullptr;
 }
 
 static int validate_desc(const ns_problem_desc* d) {
@@ -296,8 +318,10 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
         for (int l = 1; l < e.n_layers; ++l) {
             const int N = p->dims[l + 1];
             const bool last = (l == e.n_layers - 1);
-            int tn = last ? 128 : 64;
-            if (N < tn) tn = 64;
+            // hidden layers have few M tiles (rows = active chains): narrow N
+            // tiles give more CTAs; the output layer is wide enough for 128
+            int tn = last ? 128 : 32;
+            if (N < tn) tn = (N >= 64) ? 64 : 32;
             p->tile_n[l] = tn;
             int s = make_tensor_map_bf16(&p->tmB[l], p->d_W[l], N, p->dims[l], tn);
             if (s) return fail(s);
@@ -316,6 +340,7 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
     sp.N = sd.n_chi;
     sp.D = desc->n_data;
     sp.n_tmpl = sd.n_tmpl;
+    if (!projection_fits(sp, p->precision == NS_PREC_FP64 ? 8 : 4)) return fail(NS_ENOTSUP);
     sp.lnk_min = sd.lnk_min;
     sp.lnk_max = sd.lnk_max;
     sp.dlnk = (sd.lnk_max - sd.lnk_min) / (sd.n_k - 1);
@@ -470,6 +495,14 @@ extern "C" int ns_model_batch(const ns_problem* p, const double* theta_dev, int 
     cudaStream_t st = (cudaStream_t)stream;
     NS_TRY(batch_common(p, theta_dev, B, st));
     return run_likelihood(p, const_cast<Workspace*>(&p->ws), B, nullptr, model_dev, st);
+}
+
+extern "C" int ns_problem_status(ns_problem* p, int* bits, int clear) {
+    if (!p || !bits) return NS_EINVAL;
+    NS_CUDA_TRY(cudaDeviceSynchronize());
+    NS_CUDA_TRY(cudaMemcpy(bits, p->ws.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (clear) NS_CUDA_TRY(cudaMemset(p->ws.d_err, 0, sizeof(int)));
+    return NS_OK;
 }
 
 extern "C" int ns_emulator_batch(const ns_problem* p, const double* theta_dev, int B, double* out_dev,

@@ -19,7 +19,10 @@
 // k_whiten / k_chi2_finish: Y = R L^-T in tiles of 16 rows x 64 columns
 //   (b <= a), per-tile row sums of y^2, then a fixed-order sum and
 //   log L = c0 - chi^2 / 2 added in FP64.
+#include <algorithm>
+
 #include "likelihood.cuh"
+#include "async_copy.cuh"
 
 namespace gpuns {
 
@@ -95,37 +98,27 @@ __device__ __forceinline__ T warp_transpose_sum16(T (&v)[16]) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
-template <typename T>
-struct ProjArgs {
-    ShearParams sp;
-    const double* theta_full;
-    const T* table;
-    T* resid;             // rows x D residuals (unused when model_out is set)
-    double* model_out;
-    const int* nrows;
-};
+
+// Stage A (per evaluation): distances, growth and windows.  Writes, per row,
+// ln chi and V_i = sqrt(w / chi^2) W^eps_i, (NB + 1) vectors of pitch
+// win_pitch(N) (16-byte multiples, for the Limber stage's bulk copy), to `win`.
+__host__ __device__ inline int win_pitch(int N) { return (N + 3) & ~3; }
 
 template <typename T, int NB, bool FAST>
-__global__ void __launch_bounds__(kProjThreads, sizeof(T) == 8 ? 1 : 3)
-k_projection(const ProjArgs<T> args) {
+__global__ void __launch_bounds__(kProjThreads)
+k_windows(const ShearParams sp, const double* __restrict__ theta_full, T* __restrict__ win,
+          const int* __restrict__ nrows) {
     using M = Math<T, FAST>;
-    constexpr int NP = NB * (NB + 1) / 2;
-    static_assert(NP <= 16, "pair sums per item must fit one 16-value warp transpose");
-    const ShearParams& sp = args.sp;
     const int row = blockIdx.x;
-    if (row >= *args.nrows) return;
+    if (row >= *nrows) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = sp.N, nzk = sp.n_z * sp.n_k;
-    const int PK = sp.n_k + 2;                        // padded table row length
-    const int usz = max(6 * N, (sp.n_z + 2) * PK);
-    const int n_items = sp.n_ell * 2;                 // (multipole, half of the nodes)
+    const int N = sp.N;
     T* chi = reinterpret_cast<T*>(smem_raw);
     T* lnchi = chi + N;
     T* V = lnchi + N;                          // NB x N
-    T* U = chi + (((2 + NB) * N + 3) & ~3);    // union (16-byte aligned): scratch, P table, residual
-    T* part = U + ((usz + 3) & ~3);            // max(warps x 32, items x 16)
-    T* Cl = part + max(kProjWarps * 32, n_items * 16);   // NP x n_ell
-    T* th = Cl + NP * sp.n_ell;
+    T* U = V + NB * N;                         // 6 N scratch
+    T* part = U + 6 * N;                       // warps x 32
+    T* th = part + kProjWarps * 32;
     T* red = th + sp.n_params;                 // 96
     T* Ez = U;
     T* Dg = U + N;
@@ -138,8 +131,9 @@ k_projection(const ProjArgs<T> args) {
     const T* wa_ = pick<T>(sp.wa, sp.wa_f);
     const int tid = threadIdx.x, nt = kProjThreads;
     const int lane = tid & 31, wid = tid >> 5;
+    (void)lane;
 
-    for (int i = tid; i < sp.n_params; i += nt) th[i] = (T)args.theta_full[(size_t)row * sp.n_params + i];
+    for (int i = tid; i < sp.n_params; i += nt) th[i] = (T)theta_full[(size_t)row * sp.n_params + i];
     __syncthreads();
     const T h = th[2];
     const T om = (th[0] + th[1]) / (h * h);
@@ -275,152 +269,318 @@ k_projection(const ProjArgs<T> args) {
     }
     __syncthreads();
 
-    // 3. stage the log10 P table in shared memory with one ghost row/column on
-    //    each side (linear extrapolation, rows first, then columns), so every
-    //    Catmull-Rom tap is an in-range read.
-    {
-        const T* src = args.table + (size_t)row * nzk;
-        const int n_k = sp.n_k, n_z = sp.n_z;
-        if (sizeof(T) == 4 && (nzk % 4) == 0 && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
-            const float4* s4 = reinterpret_cast<const float4*>(src);
-            for (int i = tid; i < nzk / 4; i += nt) {
-                const float4 q = __ldg(s4 + i);
-                const int e = 4 * i;
-                const T vals[4] = {(T)q.x, (T)q.y, (T)q.z, (T)q.w};
+    // write ln chi and V for the Limber stage
+    const int Np = win_pitch(N);
+    T* out = win + (size_t)row * (NB + 1) * Np;
+    for (int n = tid; n < N; n += nt) out[n] = lnchi[n];
+    for (int i = 0; i < NB; ++i)
+        for (int n = tid; n < N; n += nt) out[(i + 1) * Np + n] = V[i * N + n];
+}
+
+// Stage B: Limber sums for (evaluation, group of 4 multipoles) work items.
+// The CTA stages the evaluation's log10 P table in shared memory with bulk
+// (TMA) row copies, then adds ghost rows/columns by linear extrapolation.
+// Padded layout: row r + 1 holds z row r, data column k sits at padded column
+// k + 4 (16-byte aligned rows for the copies), ghosts at columns 3 and n_k + 4;
+// the row pitch PK is a multiple of 4 chosen so that the 4-word tap windows
+// of up to 8 consecutive rows fall in distinct banks.  Warps 0-3 take the
+// group's first two multipoles and warps 4-7 the other two, each lane walking
+// chi nodes (node z-taps, ln chi and the windows from the stage-A output),
+// doing the Catmull-Rom lookup and the pair sums; a transposed warp reduction,
+// then a fixed-order sum over the four warps of each half.  The same threads
+// then form the data-vector entries of their (pair, multipole) and write the
+// residual d - m (or the model).
+constexpr int kLGroup = 4;
+
+__host__ __device__ inline int limber_pitch(int n_k) {
+    int pk = (n_k + 5 + 3) & ~3;
+    if ((pk & 31) == 0 || (pk & 31) == 16) pk += 4;
+    return pk;
+}
+
+// FP32 Limber inner loop for the multipole pair (ell0, ell1) of a warp: the two
+// lookups and their pair sums run as packed f32x2 arithmetic (one FFMA2 per
+// two FMAs).  Nodes n0, n0 + 128, ...; acc[p] / acc[NP + p] receive the pair
+// sums of ell0 / ell1.  With a single multipole left, ell1 = ell0 and the
+// second half is discarded by the caller.
+template <int NB, bool FAST>
+__device__ __forceinline__ void limber_pair_f32(const float* __restrict__ U, int PK, int N, int n_k,
+                                                const int* __restrict__ zrp, const float* __restrict__ zwp,
+                                                const float* __restrict__ lnchi, const float* __restrict__ V,
+                                                int Np, float lne0, float lne1, float lkmin, float lkmax,
+                                                float inv_dk, int n0, float* acc) {
+    using M = Math<float, FAST>;
+    constexpr int NP = NB * (NB + 1) / 2;
+    const float2 one = make_float2(1.f, 1.f), m1 = make_float2(-1.f, -1.f), two = make_float2(2.f, 2.f);
+    const float2 three = make_float2(3.f, 3.f), m3 = make_float2(-3.f, -3.f), four = make_float2(4.f, 4.f);
+    const float2 m5 = make_float2(-5.f, -5.f);
+    const float nk2 = (float)(n_k - 2);
+    float2 a2[NP];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int r = (e + c) / n_k, k = (e + c) % n_k;
-                    U[(r + 1) * PK + k + 1] = vals[c];
+    for (int p = 0; p < NP; ++p) a2[p] = make_float2(0.f, 0.f);
+    for (int n = n0; n < N; n += 128) {
+        const float* rz = U + zrp[n] * PK + 3;
+        const float4 wz = *reinterpret_cast<const float4*>(zwp + 4 * n);
+        const float lc = lnchi[n];
+        float2 vv[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) { const float x = V[i * Np + n]; vv[i] = make_float2(x, x); }
+        const float u0 = (fminf(fmaxf(lne0 - lc, lkmin), lkmax) - lkmin) * inv_dk;
+        const float u1 = (fminf(fmaxf(lne1 - lc, lkmin), lkmax) - lkmin) * inv_dk;
+        // cell index without conversion instructions: adding 2^23 rounds a
+        // value in [0, 2^22) to an integer held in the low mantissa bits.
+        // (u - 1/2) rounds to floor(u) except at exact integers, where the
+        // cell below with t = 1 gives the same interpolant.
+        const float f0 = fminf(fmaxf(__fadd_rn(__fadd_rn(u0 - 0.5f, 8388608.f), -8388608.f), 0.f), nk2);
+        const float f1 = fminf(fmaxf(__fadd_rn(__fadd_rn(u1 - 0.5f, 8388608.f), -8388608.f), 0.f), nk2);
+        const int ik0 = __float_as_int(__fadd_rn(f0, 8388608.f)) - 0x4B000000;
+        const int ik1 = __float_as_int(__fadd_rn(f1, 8388608.f)) - 0x4B000000;
+        const float2 t = make_float2(u0 - f0, u1 - f1);
+        const float2 t2 = __fmul2_rn(t, t);
+        // doubled Catmull-Rom weights (the z-taps are doubled too)
+        const float2 k0 = __fmul2_rn(t, __ffma2_rn(t, __ffma2_rn(t, m1, two), m1));
+        const float2 k1 = __ffma2_rn(t2, __ffma2_rn(three, t, m5), two);
+        const float2 k2 = __fmul2_rn(t, __ffma2_rn(t, __ffma2_rn(m3, t, four), one));
+        const float2 k3 = __fmul2_rn(t2, __fadd2_rn(t, m1));
+        const float* c0 = rz + ik0;
+        const float* c1 = rz + ik1;
+        const float wzr[4] = {wz.x, wz.y, wz.z, wz.w};
+        float2 v;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int o = r * PK;
+            float2 sr = __fmul2_rn(k0, make_float2(c0[o], c1[o]));
+            sr = __ffma2_rn(k1, make_float2(c0[o + 1], c1[o + 1]), sr);
+            sr = __ffma2_rn(k2, make_float2(c0[o + 2], c1[o + 2]), sr);
+            sr = __ffma2_rn(k3, make_float2(c0[o + 3], c1[o + 3]), sr);
+            const float2 w = make_float2(wzr[r], wzr[r]);
+            v = (r == 0) ? __fmul2_rn(w, sr) : __ffma2_rn(w, sr, v);
+        }
+        const float2 P = make_float2(M::p10(0.25f * v.x), M::p10(0.25f * v.y));
+        float2 tv[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) tv[i] = __fmul2_rn(vv[i], P);
+        int p = 0;
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+            for (int j = i; j < NB; ++j) { a2[p] = __ffma2_rn(tv[i], vv[j], a2[p]); ++p; }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) { acc[p] = a2[p].x; acc[NP + p] = a2[p].y; }
+}
+
+template <typename T, int NB, bool FAST>
+__global__ void __launch_bounds__(kProjThreads, sizeof(T) == 8 ? 1 : 3)
+k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* __restrict__ table,
+         const T* __restrict__ win, T* __restrict__ resid, double* __restrict__ model_out,
+         const int* __restrict__ nrows, int* __restrict__ err) {
+    using M = Math<T, FAST>;
+    constexpr int NP = NB * (NB + 1) / 2;
+    static_assert(2 * NP <= 32, "two multipoles of pair sums must fit one warp transpose");
+    const int row = blockIdx.y;
+    if (row >= *nrows) return;
+    const int l_base = blockIdx.x * kLGroup;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar;
+    const int N = sp.N, n_k = sp.n_k, n_z = sp.n_z;
+    const int PK = limber_pitch(n_k);
+    const int Np = win_pitch(N);
+    T* U = reinterpret_cast<T*>(smem_raw);          // padded table
+    T* W = U + (n_z + 2) * PK;                      // ln chi, V_1..V_NB (pitch Np)
+    T* part = W + (NB + 1) * Np;                    // 8 warps x 32
+    const int tid = threadIdx.x, nt = kProjThreads;
+    const int lane = tid & 31, wid = tid >> 5;
+    const T* src = table + (size_t)row * n_z * n_k;
+    const T* wsrc = win + (size_t)row * (NB + 1) * Np;
+    const uint32_t row_bytes = (uint32_t)(n_k * sizeof(T));
+    const uint32_t win_bytes = (uint32_t)((NB + 1) * Np * sizeof(T));
+    const bool bulk = (row_bytes % 16) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0 &&
+                      (reinterpret_cast<uintptr_t>(wsrc) & 15) == 0;
+    int fail = 0;
+    if (bulk) {
+        const uint32_t bar = smem_u32(&s_bar);
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+        if (tid == 0) {
+            mbar_expect_tx(bar, row_bytes * n_z + win_bytes);
+            bulk_g2s(smem_u32(W), wsrc, win_bytes, bar);
+            for (int r = 0; r < n_z; ++r)
+                bulk_g2s(smem_u32(U + (r + 1) * PK + 4), src + (size_t)r * n_k, row_bytes, bar);
+        }
+        // one warp polls the barrier while the others sleep at the CTA barrier;
+        // afterwards every thread observes the completed phase (acquire).
+        if (wid == 0) fail = !mbar_wait(bar, 0);
+        if (!__syncthreads_or(fail)) mbar_try_wait(bar, 0);
+        else {
+            // give copies still in flight a second bounded wait before leaving
+            if (wid == 0) mbar_wait(bar, 0);
+            __syncthreads();
+            if (tid == 0 && err) atomicOr(err, NS_BIT_TIMEOUT);
+            if (tid < 2 * 2 * NP) {
+                const int hf = tid / (2 * NP), q = tid % (2 * NP);
+                const int l = l_base + 2 * hf + q / NP, p = q % NP;
+                if (l < sp.n_ell) {
+                    const int a = p * sp.n_ell + l;
+                    if (model_out) model_out[(size_t)row * sp.D + a] = NAN;
+                    else resid[(size_t)row * sp.D + a] = (T)NAN;
                 }
             }
-        } else {
-            for (int i = tid; i < nzk; i += nt) U[(i / n_k + 1) * PK + i % n_k + 1] = src[i];
+            return;
         }
+    } else {
+        for (int r = wid; r < n_z; r += kProjWarps)
+            for (int k = lane; k < n_k; k += 32) U[(r + 1) * PK + 4 + k] = src[(size_t)r * n_k + k];
+        for (int i = tid; i < (NB + 1) * Np; i += nt) W[i] = wsrc[i];
         __syncthreads();
-        for (int k = 1 + tid; k <= n_k; k += nt) {
-            U[k] = T(2) * U[PK + k] - U[2 * PK + k];
-            U[(n_z + 1) * PK + k] = T(2) * U[n_z * PK + k] - U[(n_z - 1) * PK + k];
-        }
-        __syncthreads();
-        for (int r = tid; r < n_z + 2; r += nt) {
-            U[r * PK] = T(2) * U[r * PK + 1] - U[r * PK + 2];
-            U[r * PK + n_k + 1] = T(2) * U[r * PK + n_k] - U[r * PK + n_k - 1];
-        }
+    }
+    for (int k = 4 + tid; k < 4 + n_k; k += nt) {
+        U[k] = T(2) * U[PK + k] - U[2 * PK + k];
+        U[(n_z + 1) * PK + k] = T(2) * U[n_z * PK + k] - U[(n_z - 1) * PK + k];
     }
     __syncthreads();
-
-    // 4. Limber with the Catmull-Rom lookup.  Work items are (multipole, half
-    //    of the chi nodes), spread over the warps; each lane walks nodes of its
-    //    item, reads the node's precomputed z-taps (doubled weights), forms the
-    //    k-taps (doubled) and the pair sums V_i V_j P; one transposed warp
-    //    reduction per item, then the two halves are added in fixed order.
+    for (int r = tid; r < n_z + 2; r += nt) {
+        U[r * PK + 3] = T(2) * U[r * PK + 4] - U[r * PK + 5];
+        U[r * PK + n_k + 4] = T(2) * U[r * PK + n_k + 3] - U[r * PK + n_k + 2];
+    }
+    __syncthreads();
     const T lkmin = (T)sp.lnk_min, lkmax = (T)sp.lnk_max, inv_dk = T(1) / (T)sp.dlnk;
-    const int n_k = sp.n_k;
     const int* zrp = sp.zrp;
     const T* zwp = pick<T>(sp.zw4d, sp.zw4f);
-    const int half_len = (N - 1 + 1) / 2;
-#pragma unroll 1
-    for (int item = wid; item < n_items; item += kProjWarps) {
-        const int l = item >> 1;
-        const int nb0 = 1 + (item & 1) * half_len, nb1 = min(N, nb0 + half_len);
-        T acc[16];
+    const T* lnchi = W;
+    const T* V = W + Np;
+    const int half = wid >> 2;                 // which two multipoles of the group
+    const int l0 = l_base + 2 * half;
+    const bool has0 = l0 < sp.n_ell, has1 = l0 + 1 < sp.n_ell;
+    const T lne0 = has0 ? (T)sp.lnell[l0] : T(0), lne1 = has1 ? (T)sp.lnell[l0 + 1] : T(0);
+    T acc[32];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc[q] = T(0);
-        const T lne = (T)sp.lnell[l];
-        for (int n = nb0 + lane; n < nb1; n += 32) {
-            const T* rz = U + zrp[n] * PK;
+    for (int q = 0; q < 32; ++q) acc[q] = T(0);
+    if constexpr (sizeof(T) == 4) {
+        if (has0) limber_pair_f32<NB, FAST>(U, PK, N, n_k, zrp, reinterpret_cast<const float*>(zwp),
+                                            reinterpret_cast<const float*>(lnchi), reinterpret_cast<const float*>(V),
+                                            Np, (float)lne0, (float)(has1 ? lne1 : lne0), (float)lkmin, (float)lkmax,
+                                            (float)inv_dk, 1 + lane + 32 * (wid & 3), reinterpret_cast<float*>(acc));
+    } else if (has0) {
+        for (int n = 1 + lane + 32 * (wid & 3); n < N; n += 128) {
+            const T* rz = U + zrp[n] * PK + 3;
             const T wz0 = zwp[4 * n], wz1 = zwp[4 * n + 1], wz2 = zwp[4 * n + 2], wz3 = zwp[4 * n + 3];
-            T sk = lne - lnchi[n];
-            sk = fmin(fmax(sk, lkmin), lkmax);
-            const T uk = (sk - lkmin) * inv_dk;
-            int ik = (int)floor(uk);
-            ik = min(max(ik, 0), n_k - 2);
-            const T t = uk - (T)ik, t2 = t * t;
-            // doubled Catmull-Rom weights
-            const T k0 = t * (t * (T(2) - t) - T(1));
-            const T k1 = T(2) + t2 * (T(3) * t - T(5));
-            const T k2 = t * (T(1) + t * (T(4) - T(3) * t));
-            const T k3 = t2 * (t - T(1));
-            const T* c = rz + ik;
-            const T v = wz0 * (k0 * c[0] + k1 * c[1] + k2 * c[2] + k3 * c[3]) +
-                        wz1 * (k0 * c[PK] + k1 * c[PK + 1] + k2 * c[PK + 2] + k3 * c[PK + 3]) +
-                        wz2 * (k0 * c[2 * PK] + k1 * c[2 * PK + 1] + k2 * c[2 * PK + 2] + k3 * c[2 * PK + 3]) +
-                        wz3 * (k0 * c[3 * PK] + k1 * c[3 * PK + 1] + k2 * c[3 * PK + 2] + k3 * c[3 * PK + 3]);
-            const T P = M::p10(T(0.25) * v);
-            T vv[NB], tv[NB];
+            const T lc = lnchi[n];
+            T vv[NB];
 #pragma unroll
-            for (int i = 0; i < NB; ++i) { vv[i] = V[i * N + n]; tv[i] = vv[i] * P; }
-            int p = 0;
+            for (int i = 0; i < NB; ++i) vv[i] = V[i * Np + n];
 #pragma unroll
-            for (int i = 0; i < NB; ++i)
+            for (int j = 0; j < 2; ++j) {
+                if (j == 1 && !has1) break;
+                T sk = (j == 0 ? lne0 : lne1) - lc;
+                sk = fmin(fmax(sk, lkmin), lkmax);
+                const T uk = (sk - lkmin) * inv_dk;
+                int ik = (int)floor(uk);
+                ik = min(max(ik, 0), n_k - 2);
+                const T t = uk - (T)ik, t2 = t * t;
+                // doubled Catmull-Rom weights (the z-taps are doubled too)
+                const T k0 = t * (t * (T(2) - t) - T(1));
+                const T k1 = T(2) + t2 * (T(3) * t - T(5));
+                const T k2 = t * (T(1) + t * (T(4) - T(3) * t));
+                const T k3 = t2 * (t - T(1));
+                const T* c = rz + ik;
+                const T v = wz0 * (k0 * c[0] + k1 * c[1] + k2 * c[2] + k3 * c[3]) +
+                            wz1 * (k0 * c[PK] + k1 * c[PK + 1] + k2 * c[PK + 2] + k3 * c[PK + 3]) +
+                            wz2 * (k0 * c[2 * PK] + k1 * c[2 * PK + 1] + k2 * c[2 * PK + 2] + k3 * c[2 * PK + 3]) +
+                            wz3 * (k0 * c[3 * PK] + k1 * c[3 * PK + 1] + k2 * c[3 * PK + 2] + k3 * c[3 * PK + 3]);
+                const T P = M::p10(T(0.25) * v);
+                T tv[NB];
 #pragma unroll
-                for (int jj = i; jj < NB; ++jj) { acc[p] += tv[i] * vv[jj]; ++p; }
+                for (int i = 0; i < NB; ++i) tv[i] = vv[i] * P;
+                int p = 0;
+#pragma unroll
+                for (int i = 0; i < NB; ++i)
+#pragma unroll
+                    for (int jj = i; jj < NB; ++jj) { acc[j * NP + p] += tv[i] * vv[jj]; ++p; }
+            }
         }
-        const T mine = warp_transpose_sum16(acc);
-        if (lane < NP) part[item * 16 + lane] = mine;
     }
+    const T mine = warp_transpose_sum(acc);
+    part[wid * 32 + lane] = mine;
     __syncthreads();
-    for (int t = tid; t < NP * sp.n_ell; t += nt) {
-        const int p = t / sp.n_ell, l = t % sp.n_ell;
-        Cl[t] = part[(2 * l) * 16 + p] + part[(2 * l + 1) * 16 + p];
-    }
-    __syncthreads();
-
-    // 5. data vector (1 + m_i)(1 + m_j) C_ij(ell) + T b; residual d - m
-    for (int a = tid; a < sp.D; a += nt) {
-        const int p = a / sp.n_ell, e = a % sp.n_ell;
-        const int i = sp.pi[p], j = sp.pj[p];
-        T m = (T(1) + th[11 + NB + i]) * (T(1) + th[11 + NB + j]) * Cl[p * sp.n_ell + e];
-        for (int t = 0; t < sp.n_tmpl; ++t) m += (T)sp.tmpl[(size_t)a * sp.n_tmpl + t] * th[11 + 2 * NB + t];
-        if (args.model_out) args.model_out[(size_t)row * sp.D + a] = (double)m;
-        else args.resid[(size_t)row * sp.D + a] = (T)sp.data[a] - m;
+    if (tid < 2 * 2 * NP) {
+        const int hf = tid / (2 * NP), q = tid % (2 * NP);
+        const int j = q / NP, p = q % NP;
+        const int l = l_base + 2 * hf + j;
+        if (l < sp.n_ell) {
+            T cl = T(0);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) cl += part[(4 * hf + w) * 32 + q];
+            // data vector (1 + m_i)(1 + m_j) C_ij(ell) + T b; residual d - m
+            const double* th = theta_full + (size_t)row * sp.n_params;
+            const int a = p * sp.n_ell + l;
+            T m = (T(1) + (T)th[11 + NB + sp.pi[p]]) * (T(1) + (T)th[11 + NB + sp.pj[p]]) * cl;
+            for (int t = 0; t < sp.n_tmpl; ++t) m += (T)sp.tmpl[(size_t)a * sp.n_tmpl + t] * (T)th[11 + 2 * NB + t];
+            if (model_out) model_out[(size_t)row * sp.D + a] = (double)m;
+            else resid[(size_t)row * sp.D + a] = (T)sp.data[a] - m;
+        }
     }
 }
 
-// Whitening Y = R L^-T over tiles of 16 rows x 64 columns (b <= a), the next
-// 32-deep chunk of R and L^-T prefetched into registers while the current one
-// is multiplied from shared memory; per-tile row sums of y^2.
-constexpr int kWR = 16, kWC = 64, kWK = 32;
+// Whitening Y = R L^-T over tiles of 16 rows x 64 columns (b <= a).  The
+// reduction range is staged into shared memory in chunks of kc with
+// cp.async (every element of a chunk in flight at once), then multiplied;
+// per-tile row sums of y^2 go to `partial`.
+constexpr int kWR = 16, kWC = 64;
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <typename TR, typename TA>
 __global__ void __launch_bounds__(256)
 k_whiten(const TR* __restrict__ resid, int D, const TA* __restrict__ LinvT, TA* __restrict__ partial,
-         int ntile, const int* __restrict__ nrows) {
+         int ntile, int kc, const int* __restrict__ nrows) {
     const int M = *nrows;
     const int row0 = blockIdx.y * kWR;
     if (row0 >= M) return;
     const int a0 = blockIdx.x * kWC;
-    __shared__ TA Rs[kWR][kWK + 1];
-    __shared__ TA Ls[kWK][kWC + 1];
-    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;   // ty: 8 row pairs
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TR* Rs = reinterpret_cast<TR*>(smem_raw);                                  // kWR x kc
+    TA* Ls = reinterpret_cast<TA*>(smem_raw + (((size_t)kWR * kc * sizeof(TR) + 15) & ~(size_t)15));  // kc x kWC
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     const int b_end = min(D, a0 + kWC);
-    // per-thread share of a chunk: R 16 x 32 = 512 (2 each), L 32 x 64 = 2048 (8 each)
-    TA pr[2], pl[8];
-    auto fetch = [&](int b0) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int idx = tid + 256 * q, r = idx / kWK, c = idx % kWK;
-            pr[q] = (row0 + r < M && b0 + c < D) ? (TA)resid[(size_t)(row0 + r) * D + b0 + c] : TA(0);
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int idx = tid + 256 * q, bb = idx / kWC, aa = idx % kWC;
-            pl[q] = (b0 + bb < D && a0 + aa < D) ? LinvT[(size_t)(b0 + bb) * D + a0 + aa] : TA(0);
-        }
-    };
     TA acc[2][2] = {{TA(0), TA(0)}, {TA(0), TA(0)}};
-    fetch(0);
-    for (int b0 = 0; b0 < b_end; b0 += kWK) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) { const int idx = tid + 256 * q; Rs[idx / kWK][idx % kWK] = pr[q]; }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) { const int idx = tid + 256 * q; Ls[idx / kWC][idx % kWC] = pl[q]; }
+    for (int b0 = 0; b0 < b_end; b0 += kc) {
+        const int len = min(kc, b_end - b0);
+        for (int q = tid; q < kWR * len; q += 256) {
+            const int rr = q / len, c = q % len;
+            TR* dst = Rs + rr * kc + c;
+            if (row0 + rr < M) {
+                const TR* src = resid + (size_t)(row0 + rr) * D + b0 + c;
+                if (sizeof(TR) == 4) cp_async4(dst, src); else cp_async8(dst, src);
+            } else {
+                *dst = TR(0);
+            }
+        }
+        for (int q = tid; q < len * kWC; q += 256) {
+            const int bb = q / kWC, aa = q % kWC;
+            TA* dst = Ls + bb * kWC + aa;
+            if (a0 + aa < D) {
+                const TA* src = LinvT + (size_t)(b0 + bb) * D + a0 + aa;
+                if (sizeof(TA) == 4) cp_async4(dst, src); else cp_async8(dst, src);
+            } else {
+                *dst = TA(0);
+            }
+        }
+        cp_async_wait_all();
         __syncthreads();
-        if (b0 + kWK < b_end) fetch(b0 + kWK);
-#pragma unroll 8
-        for (int kk = 0; kk < kWK; ++kk) {
-            const TA l0 = Ls[kk][tx], l1 = Ls[kk][tx + 32];
-            const TA r0 = Rs[ty][kk], r1 = Rs[ty + 8][kk];
+#pragma unroll 4
+        for (int kk = 0; kk < len; ++kk) {
+            const TA l0 = Ls[kk * kWC + tx], l1 = Ls[kk * kWC + tx + 32];
+            const TA r0 = (TA)Rs[ty * kc + kk], r1 = (TA)Rs[(ty + 8) * kc + kk];
             acc[0][0] += r0 * l0; acc[0][1] += r0 * l1;
             acc[1][0] += r1 * l0; acc[1][1] += r1 * l1;
         }
@@ -451,8 +611,18 @@ template <typename TR, typename TA>
 int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL, void* partial, const int* nrows,
                 int grid_rows, cudaStream_t st) {
     const int ntile = (D + kWC - 1) / kWC;
+    // one chunk when it fits in ~200 KB of shared memory
+    const size_t per_b = (size_t)kWR * sizeof(TR) + (size_t)kWC * sizeof(TA);
+    int kc = (int)std::min<size_t>((size_t)D, (200 * 1024 - 32) / per_b);
+    kc = std::max(kc, 16);
+    const size_t smem = (((size_t)kWR * kc * sizeof(TR) + 15) & ~(size_t)15) + (size_t)kc * kWC * sizeof(TA);
+    static bool attr = false;
+    if (!attr) {
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_whiten<TR, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr = true;
+    }
     dim3 g(ntile, (grid_rows + kWR - 1) / kWR);
-    k_whiten<TR, TA><<<g, 256, 0, st>>>(resid, D, LinvT, (TA*)partial, ntile, nrows);
+    k_whiten<TR, TA><<<g, 256, smem, st>>>(resid, D, LinvT, (TA*)partial, ntile, kc, nrows);
     k_chi2_finish<TA><<<(grid_rows + 127) / 128, 128, 0, st>>>((const TA*)partial, ntile, c0, logL, nrows);
     NS_CUDA_TRY(cudaGetLastError());
     return NS_OK;
@@ -464,48 +634,92 @@ template int launch_chi2<float, double>(const float*, int, const double*, double
 template int launch_chi2<double, double>(const double*, int, const double*, double, double*, void*, const int*, int,
                                          cudaStream_t);
 
-size_t projection_smem_bytes(const ShearParams& sp, int elt, int elt_acc) {
-    const int NP = sp.nb * (sp.nb + 1) / 2;
-    const int usz = std::max(6 * sp.N, (sp.n_z + 2) * (sp.n_k + 2));
-    (void)elt_acc;
-    const size_t n = (size_t)(((2 + sp.nb) * sp.N + 3) & ~3) + ((usz + 3) & ~3) +
-                     (size_t)std::max(kProjWarps * 32, sp.n_ell * 2 * 16) + (size_t)NP * sp.n_ell + sp.n_params + 96;
-    return n * elt;
+template <typename T>
+static size_t windows_smem(const ShearParams& sp) {
+    return ((size_t)(2 + sp.nb) * sp.N + 6 * (size_t)sp.N + kProjWarps * 32 + sp.n_params + 96) * sizeof(T);
+}
+// dynamic shared memory left beside the Limber kernel's static barrier
+constexpr size_t kLimberSmemMax = 227 * 1024 - 64;
+template <typename T>
+static size_t limber_smem(const ShearParams& sp) {
+    return ((size_t)(sp.n_z + 2) * limber_pitch(sp.n_k) + (size_t)(sp.nb + 1) * win_pitch(sp.N) + kProjWarps * 32) *
+           sizeof(T);
+}
+
+bool projection_fits(const ShearParams& sp, int elt) {
+    const size_t lim = 227 * 1024;
+    return elt == 8 ? (windows_smem<double>(sp) <= lim && limber_smem<double>(sp) <= kLimberSmemMax)
+                    : (windows_smem<float>(sp) <= lim && limber_smem<float>(sp) <= kLimberSmemMax);
 }
 
 template <typename T, int NB, bool FAST>
-static int launch_nb(const ProjArgs<T>& a, int grid_rows, cudaStream_t st) {
-    const size_t smem = projection_smem_bytes(a.sp, sizeof(T), sizeof(T));
+static int windows_nb(const ShearParams& sp, const double* theta_full, T* win, const int* nrows, int grid_rows,
+                      cudaStream_t st) {
+    const size_t smem = windows_smem<T>(sp);
     if (smem > 227 * 1024) return NS_ENOTSUP;
     static bool attr_done = false;
     if (!attr_done) {
-        NS_CUDA_TRY(cudaFuncSetAttribute(k_projection<T, NB, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024));
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_windows<T, NB, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr_done = true;
     }
-    k_projection<T, NB, FAST><<<grid_rows, kProjThreads, smem, st>>>(a);
+    k_windows<T, NB, FAST><<<grid_rows, kProjThreads, smem, st>>>(sp, theta_full, win, nrows);
+    NS_CUDA_TRY(cudaGetLastError());
+    return NS_OK;
+}
+
+template <typename T, int NB, bool FAST>
+static int limber_nb(const ShearParams& sp, const double* theta_full, const T* table, const T* win, T* resid,
+                     double* model_out, const int* nrows, int grid_rows, int* err, cudaStream_t st) {
+    const size_t smem = limber_smem<T>(sp);
+    if (smem > kLimberSmemMax) return NS_ENOTSUP;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncAttributes fa;
+        NS_CUDA_TRY(cudaFuncGetAttributes(&fa, k_limber<T, NB, FAST>));
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_limber<T, NB, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(227 * 1024 - fa.sharedSizeBytes)));
+        attr_done = true;
+    }
+    dim3 g((sp.n_ell + kLGroup - 1) / kLGroup, grid_rows);
+    k_limber<T, NB, FAST><<<g, kProjThreads, smem, st>>>(sp, theta_full, table, win, resid, model_out, nrows, err);
     NS_CUDA_TRY(cudaGetLastError());
     return NS_OK;
 }
 
 template <typename T, bool FAST>
-int launch_projection(const ShearParams& sp, const double* theta_full, const T* table, T* resid, double* model_out,
-                      const int* nrows, int grid_rows, cudaStream_t st) {
-    ProjArgs<T> a{sp, theta_full, table, resid, model_out, nrows};
+int launch_windows(const ShearParams& sp, const double* theta_full, T* win, const int* nrows, int grid_rows,
+                   cudaStream_t st) {
     switch (sp.nb) {
-        case 1: return launch_nb<T, 1, FAST>(a, grid_rows, st);
-        case 2: return launch_nb<T, 2, FAST>(a, grid_rows, st);
-        case 3: return launch_nb<T, 3, FAST>(a, grid_rows, st);
-        case 4: return launch_nb<T, 4, FAST>(a, grid_rows, st);
-        case 5: return launch_nb<T, 5, FAST>(a, grid_rows, st);
+        case 1: return windows_nb<T, 1, FAST>(sp, theta_full, win, nrows, grid_rows, st);
+        case 2: return windows_nb<T, 2, FAST>(sp, theta_full, win, nrows, grid_rows, st);
+        case 3: return windows_nb<T, 3, FAST>(sp, theta_full, win, nrows, grid_rows, st);
+        case 4: return windows_nb<T, 4, FAST>(sp, theta_full, win, nrows, grid_rows, st);
+        case 5: return windows_nb<T, 5, FAST>(sp, theta_full, win, nrows, grid_rows, st);
         default: return NS_ENOTSUP;
     }
 }
-template int launch_projection<double, false>(const ShearParams&, const double*, const double*, double*, double*,
-                                              const int*, int, cudaStream_t);
-template int launch_projection<float, false>(const ShearParams&, const double*, const float*, float*, double*,
-                                             const int*, int, cudaStream_t);
-template int launch_projection<float, true>(const ShearParams&, const double*, const float*, float*, double*,
-                                            const int*, int, cudaStream_t);
+
+template <typename T, bool FAST>
+int launch_limber(const ShearParams& sp, const double* theta_full, const T* table, const T* win, T* resid,
+                  double* model_out, const int* nrows, int grid_rows, int* err, cudaStream_t st) {
+    switch (sp.nb) {
+        case 1: return limber_nb<T, 1, FAST>(sp, theta_full, table, win, resid, model_out, nrows, grid_rows, err, st);
+        case 2: return limber_nb<T, 2, FAST>(sp, theta_full, table, win, resid, model_out, nrows, grid_rows, err, st);
+        case 3: return limber_nb<T, 3, FAST>(sp, theta_full, table, win, resid, model_out, nrows, grid_rows, err, st);
+        case 4: return limber_nb<T, 4, FAST>(sp, theta_full, table, win, resid, model_out, nrows, grid_rows, err, st);
+        case 5: return limber_nb<T, 5, FAST>(sp, theta_full, table, win, resid, model_out, nrows, grid_rows, err, st);
+        default: return NS_ENOTSUP;
+    }
+}
+
+template int launch_windows<double, false>(const ShearParams&, const double*, double*, const int*, int, cudaStream_t);
+template int launch_windows<float, false>(const ShearParams&, const double*, float*, const int*, int, cudaStream_t);
+template int launch_windows<float, true>(const ShearParams&, const double*, float*, const int*, int, cudaStream_t);
+template int launch_limber<double, false>(const ShearParams&, const double*, const double*, const double*, double*,
+                                          double*, const int*, int, int*, cudaStream_t);
+template int launch_limber<float, false>(const ShearParams&, const double*, const float*, const float*, float*,
+                                         double*, const int*, int, int*, cudaStream_t);
+template int launch_limber<float, true>(const ShearParams&, const double*, const float*, const float*, float*,
+                                        double*, const int*, int, int*, cudaStream_t);
 
 }  // namespace gpuns
