@@ -133,6 +133,9 @@ int workspace_create(const ns_problem* p, int cap, Workspace* ws) {
     NS_CUDA_TRY(cudaEventCreateWithFlags(&ws->ev_join, cudaEventDisableTiming));
     NS_TRY(dalloc(sizeof(double) * (size_t)cap * ((p->sp.D + 63) / 64), &v, ws->owned));
     ws->chi2_part = v;
+    NS_TRY(dalloc(sizeof(int) * (size_t)((cap + 15) / 16), &v, ws->owned));
+    ws->chi2_done = (int*)v;
+    NS_CUDA_TRY(cudaMemset(v, 0, sizeof(int) * (size_t)((cap + 15) / 16)));
 
     if (p->precision == NS_PREC_BF16 || p->precision == NS_PREC_BF16_F64CHI2) {
         ws->tmA.resize(p->n_layers);

@@ -1,6 +1,7 @@
 // The shear projection (App. A, rows A8-A12) and the whitened chi^2 (A13).
 //
-// k_projection: one CTA (8 warps) per likelihood evaluation.
+// k_windows: one CTA (8 warps) per likelihood evaluation; needs only theta,
+// so it runs on a second stream beside the emulator.
 //   1. background: E(a) at the nodes; chi increments over each a-interval by a
 //      4-point Gauss-Legendre rule and a block prefix sum (chi_0 = 0 at a = 1);
 //      growth ln D = -sum trapezoid(Omega_m(a)^gamma) dln a by a second scan.
@@ -8,17 +9,19 @@
 //      grid; W^gamma (Eq. 5) = A (chi/a) [S0 - chi S1] with exclusive suffix
 //      sums S0 = sum_{m>n} w n, S1 = sum_{m>n} w n / chi (the m = n term of the
 //      direct double sum is zero); W^I (Eq. 6); V_i = sqrt(w/chi^2) W^eps_i.
-//   3. the emulator's log10 P table (n_z x n_k) is staged in shared memory
-//      (over the background scratch) so the 16 taps of every lookup hit smem.
-//   4. Limber (Eq. 3-4): multipoles in groups of G; each lane owns chi nodes,
-//      forms the node's z-taps and window values once per group, then for the
-//      group's multipoles the Catmull-Rom lookup at ln k = ln(ell + 1/2) -
-//      ln chi and the pair sums V_i V_j P.  A transposed warp reduction, then
-//      a fixed-order sum over warps (deterministic).
+//      ln chi and V go to a per-evaluation buffer.
+// k_limber: one CTA per (evaluation, group of 4 multipoles).
+//   3. the emulator's log10 P table (n_z x n_k) and the evaluation's windows
+//      are staged in shared memory by bulk (TMA) copies, so the 16 taps of
+//      every lookup and the node data hit shared memory.
+//   4. Limber (Eq. 3-4): lanes own chi nodes; per node the Catmull-Rom lookup
+//      at ln k = ln(ell + 1/2) - ln chi for two multipoles at once (packed
+//      FP32x2 arithmetic) and the pair sums V_i V_j P.  A transposed warp
+//      reduction, then a fixed-order sum over warps (deterministic).
 //   5. data vector (1 + m_i)(1 + m_j) C_ij(ell) + T b and residual d - m.
-// k_whiten / k_chi2_finish: Y = R L^-T in tiles of 16 rows x 64 columns
-//   (b <= a), per-tile row sums of y^2, then a fixed-order sum and
-//   log L = c0 - chi^2 / 2 added in FP64.
+// k_whiten: Y = R L^-T in tiles of 16 rows x 64 columns (b <= a), per-tile
+//   row sums of y^2; the last tile of a row block adds them in fixed order
+//   and writes log L = c0 - chi^2 / 2 in FP64.
 #include <algorithm>
 
 #include "likelihood.cuh"
@@ -526,11 +529,19 @@ k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* _
 }
 
 // Whitening Y = R L^-T over tiles of 16 rows x 64 columns (b <= a).  The
-// reduction range is staged into shared memory in chunks of kc with
-// cp.async (every element of a chunk in flight at once), then multiplied;
-// per-tile row sums of y^2 go to `partial`.
-constexpr int kWR = 16, kWC = 64;
+// reduction range (rounded up to 32, zero-filled) is staged in shared memory
+// with 16-byte cp.async copies, in as few chunks as fit; the 8 warps split it
+// (warp w takes the w-th eighth), each lane accumulating 16 rows x 2 columns,
+// with the four R values of a row read as one vector.  The eight partial
+// tiles are added in fixed order; per-tile row sums of y^2 go to `partial`;
+// the last tile CTA of a row block (arrival counter) adds them in fixed order
+// and writes log L = c0 - chi^2 / 2.
+constexpr int kWR = 16, kWC = 64, kWarps = 8;
 
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
 }
@@ -539,100 +550,168 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+template <typename T>
+__device__ __forceinline__ void cp_async_elt(T* dst, const T* src) {
+    if (sizeof(T) == 4) cp_async4(dst, src); else cp_async8(dst, src);
+}
+
+// four consecutive values (16-byte aligned for float, 16-byte aligned pairs for double)
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+    const double2 q0 = *reinterpret_cast<const double2*>(p), q1 = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+
 template <typename TR, typename TA>
 __global__ void __launch_bounds__(256)
-k_whiten(const TR* __restrict__ resid, int D, const TA* __restrict__ LinvT, TA* __restrict__ partial,
-         int ntile, int kc, const int* __restrict__ nrows) {
+k_whiten(const TR* __restrict__ resid, int D, const TA* __restrict__ LinvT, TA* __restrict__ partial, int ntile,
+         int KC, int* __restrict__ done, double c0, double* __restrict__ logL, const int* __restrict__ nrows) {
     const int M = *nrows;
     const int row0 = blockIdx.y * kWR;
     if (row0 >= M) return;
     const int a0 = blockIdx.x * kWC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TR* Rs = reinterpret_cast<TR*>(smem_raw);                                  // kWR x kc
-    TA* Ls = reinterpret_cast<TA*>(smem_raw + (((size_t)kWR * kc * sizeof(TR) + 15) & ~(size_t)15));  // kc x kWC
-    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    TA* Ls = reinterpret_cast<TA*>(smem_raw);                 // KC x kWC
+    TR* Rs = reinterpret_cast<TR*>(Ls + (size_t)KC * kWC);    // kWR x KC
+    TA* red = Ls;                                             // kWarps x kWR x kWC, after the last chunk
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int b_end = min(D, a0 + kWC);
-    TA acc[2][2] = {{TA(0), TA(0)}, {TA(0), TA(0)}};
-    for (int b0 = 0; b0 < b_end; b0 += kc) {
-        const int len = min(kc, b_end - b0);
-        for (int q = tid; q < kWR * len; q += 256) {
-            const int rr = q / len, c = q % len;
-            TR* dst = Rs + rr * kc + c;
-            if (row0 + rr < M) {
-                const TR* src = resid + (size_t)(row0 + rr) * D + b0 + c;
-                if (sizeof(TR) == 4) cp_async4(dst, src); else cp_async8(dst, src);
-            } else {
-                *dst = TR(0);
+    const int Kp = (b_end + 31) & ~31;
+    const bool vecL = (D * sizeof(TA)) % 16 == 0 && (reinterpret_cast<uintptr_t>(LinvT) & 15) == 0;
+    const bool vecR = (D * sizeof(TR)) % 16 == 0 && (reinterpret_cast<uintptr_t>(resid) & 15) == 0;
+    TA acc[kWR][2];
+#pragma unroll
+    for (int r = 0; r < kWR; ++r) { acc[r][0] = TA(0); acc[r][1] = TA(0); }
+    for (int k0 = 0; k0 < Kp; k0 += KC) {
+        const int len = min(KC, Kp - k0);          // multiple of 32
+        const int lv = max(0, min(len, b_end - k0)); // rows holding data
+        if (k0 > 0) __syncthreads();
+        // L^-T rows k0 .. k0 + len (zero beyond b_end and beyond column D)
+        if (vecL) {
+            constexpr int per = 16 / sizeof(TA), vpr = kWC / per;
+            for (int q = tid; q < len * vpr; q += 256) {
+                const int bb = q / vpr, v = q % vpr;
+                TA* dst = Ls + bb * kWC + v * per;
+                if (bb < lv && a0 + v * per < D) cp_async16(dst, LinvT + (size_t)(k0 + bb) * D + a0 + v * per);
+                else for (int e = 0; e < per; ++e) dst[e] = TA(0);
+            }
+        } else {
+            for (int q = tid; q < len * kWC; q += 256) {
+                const int bb = q / kWC, aa = q % kWC;
+                if (bb < lv && a0 + aa < D) cp_async_elt(Ls + bb * kWC + aa, LinvT + (size_t)(k0 + bb) * D + a0 + aa);
+                else Ls[bb * kWC + aa] = TA(0);
             }
         }
-        for (int q = tid; q < len * kWC; q += 256) {
-            const int bb = q / kWC, aa = q % kWC;
-            TA* dst = Ls + bb * kWC + aa;
-            if (a0 + aa < D) {
-                const TA* src = LinvT + (size_t)(b0 + bb) * D + a0 + aa;
-                if (sizeof(TA) == 4) cp_async4(dst, src); else cp_async8(dst, src);
-            } else {
-                *dst = TA(0);
+        // R rows row0 .. row0 + 16, columns k0 .. k0 + len (zero beyond b_end / M)
+        if (vecR) {
+            constexpr int per = 16 / sizeof(TR);
+            const int vpr = len / per;
+            for (int q = tid; q < kWR * vpr; q += 256) {
+                const int rr = q / vpr, v = q % vpr;
+                TR* dst = Rs + rr * KC + v * per;
+                if (row0 + rr < M && v * per < lv) cp_async16(dst, resid + (size_t)(row0 + rr) * D + k0 + v * per);
+                else for (int e = 0; e < per; ++e) dst[e] = TR(0);
+            }
+        } else {
+            for (int q = tid; q < kWR * len; q += 256) {
+                const int rr = q / len, cc = q % len;
+                if (row0 + rr < M && cc < lv) cp_async_elt(Rs + rr * KC + cc, resid + (size_t)(row0 + rr) * D + k0 + cc);
+                else Rs[rr * KC + cc] = TR(0);
             }
         }
         cp_async_wait_all();
         __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < len; ++kk) {
-            const TA l0 = Ls[kk * kWC + tx], l1 = Ls[kk * kWC + tx + 32];
-            const TA r0 = (TA)Rs[ty * kc + kk], r1 = (TA)Rs[(ty + 8) * kc + kk];
-            acc[0][0] += r0 * l0; acc[0][1] += r0 * l1;
-            acc[1][0] += r1 * l0; acc[1][1] += r1 * l1;
-        }
-        __syncthreads();
-    }
+        const int kw = len / kWarps;               // multiple of 4
+        const int kb = wid * kw;
+        for (int k = kb; k < kb + kw; k += 4) {
+            TA l0[4], l1[4];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        TA s = TA(0);
-        if (a0 + tx < D) s += acc[i][0] * acc[i][0];
-        if (a0 + tx + 32 < D) s += acc[i][1] * acc[i][1];
-        s = warp_sum(s);
-        const int r = row0 + ty + 8 * i;
-        if (tx == 0 && r < M) partial[(size_t)r * ntile + blockIdx.x] = s;
+            for (int j = 0; j < 4; ++j) { l0[j] = Ls[(k + j) * kWC + lane]; l1[j] = Ls[(k + j) * kWC + lane + 32]; }
+#pragma unroll
+            for (int r = 0; r < kWR; ++r) {
+                TR rv[4];
+                ld4(Rs + r * KC + k, rv);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[r][0] += (TA)rv[j] * l0[j];
+                    acc[r][1] += (TA)rv[j] * l1[j];
+                }
+            }
+        }
     }
-}
-
-template <typename TA>
-__global__ void k_chi2_finish(const TA* __restrict__ partial, int ntile, double c0, double* __restrict__ logL,
-                              const int* __restrict__ nrows) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= *nrows) return;
-    TA s = TA(0);
-    for (int t = 0; t < ntile; ++t) s += partial[(size_t)r * ntile + t];
-    logL[r] = c0 - 0.5 * (double)s;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kWR; ++r) {
+        red[(wid * kWR + r) * kWC + lane] = acc[r][0];
+        red[(wid * kWR + r) * kWC + lane + 32] = acc[r][1];
+    }
+    __syncthreads();
+    // thread t: row t / 16, columns 4 (t % 16) .. + 3
+    {
+        const int r = tid >> 4, cb = (tid & 15) * 4;
+        TA sq = TA(0);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            TA y = TA(0);
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) y += red[(w * kWR + r) * kWC + cb + e];
+            if (a0 + cb + e < D) sq += y * y;
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o, 16);
+        if ((tid & 15) == 0 && row0 + r < M) partial[(size_t)(row0 + r) * ntile + blockIdx.x] = sq;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&done[blockIdx.y], 1) == ntile - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (tid < kWR && row0 + tid < M) {
+        const int r = row0 + tid;
+        TA s2 = TA(0);
+        for (int t = 0; t < ntile; ++t) s2 += __ldcg(partial + (size_t)r * ntile + t);
+        logL[r] = c0 - 0.5 * (double)s2;
+    }
+    if (tid == 0) done[blockIdx.y] = 0;
 }
 
 template <typename TR, typename TA>
-int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL, void* partial, const int* nrows,
-                int grid_rows, cudaStream_t st) {
+static size_t whiten_smem(int KC) {
+    return std::max((size_t)KC * kWC * sizeof(TA) + (size_t)kWR * KC * sizeof(TR),
+                    (size_t)kWarps * kWR * kWC * sizeof(TA));
+}
+
+template <typename TR, typename TA>
+int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL, void* partial, int* done,
+                const int* nrows, int grid_rows, cudaStream_t st) {
     const int ntile = (D + kWC - 1) / kWC;
-    // one chunk when it fits in ~200 KB of shared memory
-    const size_t per_b = (size_t)kWR * sizeof(TR) + (size_t)kWC * sizeof(TA);
-    int kc = (int)std::min<size_t>((size_t)D, (200 * 1024 - 32) / per_b);
-    kc = std::max(kc, 16);
-    const size_t smem = (((size_t)kWR * kc * sizeof(TR) + 15) & ~(size_t)15) + (size_t)kc * kWC * sizeof(TA);
+    // the whole (padded) reduction range in one chunk when it fits ~200 KB
+    const int Kp = (D + 31) & ~31;
+    const size_t per_k = (size_t)kWC * sizeof(TA) + (size_t)kWR * sizeof(TR);
+    int KC = (int)std::min<size_t>((size_t)Kp, ((200 * 1024) / per_k) & ~(size_t)31);
+    KC = std::max(KC, 32);
+    const size_t smem = whiten_smem<TR, TA>(KC);
     static bool attr = false;
     if (!attr) {
-        NS_CUDA_TRY(cudaFuncSetAttribute(k_whiten<TR, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_whiten<TR, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 64));
         attr = true;
     }
     dim3 g(ntile, (grid_rows + kWR - 1) / kWR);
-    k_whiten<TR, TA><<<g, 256, smem, st>>>(resid, D, LinvT, (TA*)partial, ntile, kc, nrows);
-    k_chi2_finish<TA><<<(grid_rows + 127) / 128, 128, 0, st>>>((const TA*)partial, ntile, c0, logL, nrows);
+    k_whiten<TR, TA><<<g, 256, smem, st>>>(resid, D, LinvT, (TA*)partial, ntile, KC, done, c0, logL, nrows);
     NS_CUDA_TRY(cudaGetLastError());
     return NS_OK;
 }
-template int launch_chi2<float, float>(const float*, int, const float*, double, double*, void*, const int*, int,
-                                       cudaStream_t);
-template int launch_chi2<float, double>(const float*, int, const double*, double, double*, void*, const int*, int,
-                                        cudaStream_t);
-template int launch_chi2<double, double>(const double*, int, const double*, double, double*, void*, const int*, int,
-                                         cudaStream_t);
+template int launch_chi2<float, float>(const float*, int, const float*, double, double*, void*, int*, const int*,
+                                       int, cudaStream_t);
+template int launch_chi2<float, double>(const float*, int, const double*, double, double*, void*, int*, const int*,
+                                        int, cudaStream_t);
+template int launch_chi2<double, double>(const double*, int, const double*, double, double*, void*, int*, const int*,
+                                         int, cudaStream_t);
 
 template <typename T>
 static size_t windows_smem(const ShearParams& sp) {
