@@ -132,18 +132,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def projection_flops_per_eval(cfg) -> float:
-    """Algorithmic FLOPs of the fused projection kernel per evaluation (the
-    count stated in the design notes): per (ell, chi-node) a 16-tap bicubic
-    lookup (32) + bracket/weights (10) + nb window products + 2 n_pairs Limber
-    FMAs; per node interval the 4-point distance quadrature (4 x 12); per node
-    and bin the n(z) / window work (25); per data element bias + templates."""
+def limber_flops_per_eval(cfg) -> float:
+    """Algorithmic FLOPs of the Limber stage (k_limber) per evaluation, the
+    count stated in the design notes: per (ell, chi-node) a 16-tap bicubic
+    lookup (32) + bracket and Catmull-Rom weights (10) + nb window products +
+    2 n_pairs pair-sum FLOPs (one FMA each); per data element the bias
+    product and the template sum (3 + 2 n_tmpl)."""
     N = cfg.n_chi
     nb = cfg.n_bins
     npairs = nb * (nb + 1) // 2
     D = cfg.n_data
-    return (cfg.n_ell * (N - 1) * (32 + 10 + nb + 2 * npairs) + (N - 1) * 48 + N * nb * 25
-            + D * (3 + 2 * cfg.n_tmpl))
+    return cfg.n_ell * (N - 1) * (32 + 10 + nb + 2 * npairs) + D * (3 + 2 * cfg.n_tmpl)
+
+
+def windows_flops_per_eval(cfg) -> float:
+    """Algorithmic FLOPs of the windows stage (k_windows) per evaluation: per
+    node interval the 4-point distance quadrature (4 x 12), per node the
+    growth and weights (12), per node and bin the n(z) and window work (25)."""
+    N = cfg.n_chi
+    return (N - 1) * 48 + N * 12 + N * cfg.n_bins * 25
 
 
 def replace_seed(sc, rank):
@@ -282,21 +289,23 @@ def ours(args):
     value = ev_job / t_job
 
     # kernels launched per round: slice state machine, prior transform, emulator input
-    # layer, one GEMM per further layer, projection, chi^2; per iteration 5 more.
+    # per round: slice, prior transform, windows, emulator input layer, one
+    # GEMM per further layer, Limber, whitening; per iteration 6 more (sort and
+    # delete, covariance, Cholesky, directions, chain starts, insert).
     n_layers = len(inp["emu_W"])
-    per_round = 3 + (n_layers - 1) + 2
-    gpu_launches = res["rounds"] * per_round + 5 * res["iters"]
+    per_round = 5 + (n_layers - 1) + 1
+    gpu_launches = res["rounds"] * per_round + 6 * res["iters"]
 
-    # ---------------- roofline of the dominant kernel (projection), timed live
+    # ---------------- roofline of the dominant kernel (Limber stage), timed live
     prof = res["prof"]
-    flops = projection_flops_per_eval(cfg)
+    flops = limber_flops_per_eval(cfg)
     peak = fp32_alu_peak_tflops(2070.0)
     roofline = None
     if prof and prof["launches"] > 0 and prof["ms"] > 0:
         achieved = prof["rows"] * flops / (prof["ms"] * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
-                    "kernel": "k_projection<float,5,fast> (A8-A12: distances, windows, P lookup, Limber, data vector)",
+                    "kernel": "k_limber<float,5,fast> (A10-A12: P lookup, Limber sums, data vector)",
                     "flop_per_eval": flops, "avg_launch_ms": prof["ms"] / prof["launches"],
                     "avg_rows_per_launch": prof["rows"] / prof["launches"],
                     "peak_basis": "FP32 ALU 152 SM x 128 lanes x 2 x 2070 MHz (no measured FP32 peak in MEASURED_PEAKS.json)"}

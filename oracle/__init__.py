@@ -13,7 +13,8 @@ Modules
   philox    counter-based generator (pinned by published known-answer vectors)
   special   log-sum-exp and inverse normal CDF (scipy's ndtri)
   priors    cube -> physical prior transform (Table 1)
-  shear     cosmic-shear likelihood (App. A: Eq. 3-6, chi-grid of L287)
+  shear     cosmic-shear likelihood (App. A: Eq. 3-6, the chi grid of App. A)
+  cmb       CMB-like Gaussian likelihood with a dense covariance (Sec. 3.1)
   gauss     isotropic Gaussian test likelihood + closed-form evidence
   ns        nested slice sampler with batched deletion (Sec. 2.1-2.2)
   evidence  log Z / log X / H accumulation and the simulated-shrinkage error

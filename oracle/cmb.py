@@ -1,0 +1,96 @@
+"""CMB-like Gaussian likelihood (the paper's CMB test problem, Sec. 3.1, in the
+dense-covariance form of the 6-parameter LCDM configuration), in plain FP64
+NumPy.  Test infrastructure only.
+
+Steps, each following the cited passage:
+  emulator    MLP stand-in for the CosmoPower C_ell emulator (Sec. 2.5): hidden
+              layers h <- f(W h + b) with CosmoPower's activation
+              f(x) = [gamma + (1 - gamma) sigmoid(beta x)] x (one gamma, beta per
+              unit), a linear head, outputs de-standardised as mu + sigma * y.
+              Inputs are the 6 parameters standardised over the prior box.
+  model       m(theta) = the emulator output (TT, TE, EE stacked).
+  loglike     Gaussian: -1/2 |L^-1 (d - m)|^2 - sum ln L_aa - D/2 ln 2 pi, the
+              whitening by explicit forward substitution (no fast algebra).
+
+Mock data and covariance: C = s W with W the seeded Wishart-style base of the
+workload inputs and s setting the mean variance to (cov_rel * rms m_fid)^2;
+data = m_fid + L eps.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .priors import cube_to_theta, theta_free_to_full
+
+
+def sigmoid_linear(x, g, beta):
+    """CosmoPower's activation [g + (1 - g) / (1 + exp(-beta x))] x."""
+    return (g + (1.0 - g) / (1.0 + np.exp(-beta * x))) * x
+
+
+class CMBOracle:
+    def __init__(self, inp: dict, data=None, cov=None, wishart=None):
+        self.inp = inp
+        self.priors = inp["priors"]
+        self.D = int(inp["n_data"])
+        if data is None or cov is None:
+            data, cov = self.make_mock(wishart)
+        self.set_data(data, cov)
+
+    # ----------------------------------------------------------- emulator
+    def emulator(self, theta):
+        """De-standardised emulator output mu + sigma * y, shape (D,)."""
+        inp = self.inp
+        x = (np.asarray(theta)[inp["emu_inputs"]] - inp["emu_in_center"]) / inp["emu_in_scale"]
+        Ws, bs = inp["emu_W"], inp["emu_b"]
+        h = x
+        for l in range(len(Ws) - 1):
+            h = sigmoid_linear(Ws[l] @ h + bs[l], inp["act_g"][l], inp["act_beta"][l])
+        y = Ws[-1] @ h + bs[-1]
+        return inp["emu_out_mu"] + inp["emu_out_sig"] * y
+
+    def model(self, theta):
+        return self.emulator(theta)
+
+    # ----------------------------------------------------------- data
+    def make_mock(self, wishart=None):
+        inp = self.inp
+        mfid = self.model(np.asarray(inp["fiducial"], float))
+        if wishart is None:
+            from workloads import wishart_base
+            wishart = wishart_base(self.D, int(inp["wishart_nu"]), int(inp["seed_cov"]))
+        s = (inp["cov_rel"] * math.sqrt(np.mean(mfid * mfid))) ** 2 / np.mean(np.diag(wishart))
+        cov = s * wishart
+        data = mfid + np.linalg.cholesky(cov) @ inp["noise_eps"]
+        return data, cov
+
+    def set_data(self, data, cov):
+        self.data = np.asarray(data, float)
+        self.cov = np.asarray(cov, float)
+        self.L = np.linalg.cholesky(self.cov)
+        self.c0 = -np.sum(np.log(np.diag(self.L))) - 0.5 * self.D * math.log(2.0 * math.pi)
+
+    # ----------------------------------------------------------- likelihood
+    def forward_subst(self, r):
+        """Solve L y = r by explicit forward substitution."""
+        L = self.L
+        y = np.zeros(self.D, dtype=np.result_type(r, L))
+        for a in range(self.D):
+            y[a] = (r[a] - L[a, :a] @ y[:a]) / L[a, a]
+        return y
+
+    def chi2(self, theta):
+        y = self.forward_subst(self.data - self.model(theta))
+        return float(np.sum(y * y))
+
+    def loglike_full(self, theta):
+        return -0.5 * self.chi2(theta) + self.c0
+
+    def loglike(self, theta_free):
+        return self.loglike_full(theta_free_to_full(self.priors, np.asarray(theta_free)))
+
+    def loglike_cube(self, cube):
+        return self.loglike_full(cube_to_theta(self.priors, cube))

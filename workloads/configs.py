@@ -290,6 +290,14 @@ def cmb6(n_ell: int = 2507, **sampler_kw) -> CMBConfig:
                      sampler=SamplerConfig(**kw))
 
 
+def cmb_tiny(**sampler_kw) -> CMBConfig:
+    """A small CMB-like problem for parity tests: 40 multipoles (D = 120),
+    emulator 6 -> 96 -> 80 -> 120, spanning several tiles with ragged tails."""
+    kw = dict(n_live=60, n_delete=30)
+    kw.update(sampler_kw)
+    return CMBConfig(name="cmb_tiny", n_ell=40, emu_hidden=(96, 80), sampler=SamplerConfig(**kw))
+
+
 def shear39_interp(**sampler_kw) -> ShearConfig:
     """shear39 with the emulator evaluated on 10 coarse z nodes, Catmull-Rom
     interpolated to the 50-node table (output 200 k x 10 z = 2000)."""

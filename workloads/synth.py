@@ -139,6 +139,32 @@ def make_cmb_inputs(cfg: CMBConfig) -> dict:
     return dict(kind="cmb", name=cfg.name, n_params=6, priors=priors,
                 fiducial=np.array(cfg.fiducial), emu_W=Ws, emu_b=bs,
                 emu_act="sigmoid_linear", act_g=act_g, act_beta=act_beta,
-                emu_in_center=centers, emu_in_scale=scales,
-                emu_out_mu=mu, emu_out_sig=sig, ell=ell,
-                noise_eps=noise_eps, wishart_nu=nu, seed_cov=cfg.seed_cov)
+                emu_inputs=np.arange(6), emu_in_center=centers, emu_in_scale=scales,
+                emu_out_mu=mu, emu_out_sig=sig, ell=ell, n_data=D,
+                noise_eps=noise_eps, wishart_nu=nu, seed_cov=cfg.seed_cov,
+                cov_rel=0.1)
+
+
+_WISHART_CACHE: dict = {}
+
+
+def wishart_base(D: int, nu: int, seed: int) -> np.ndarray:
+    """W = A A^T / nu with A ~ N(0, 1) of size D x nu (seeded), accumulated in
+    column blocks of A: a dense SPD matrix with E[W] = I whose spectrum follows
+    the Marchenko-Pastur law (condition number near ((1 + r)/(1 - r))^2,
+    r = sqrt(D / nu)).  The CMB covariance is this matrix times a scale set
+    from the fiducial model by each side.  Cached per process (the D = 7521
+    case takes seconds)."""
+    key = (int(D), int(nu), int(seed))
+    if key not in _WISHART_CACHE:
+        rng = np.random.default_rng(seed)
+        W = np.zeros((D, D))
+        blk = 1024
+        for c0 in range(0, nu, blk):
+            A = rng.standard_normal((D, min(blk, nu - c0)))
+            W += A @ A.T
+        W /= nu
+        W = 0.5 * (W + W.T)
+        _WISHART_CACHE.clear()
+        _WISHART_CACHE[key] = W
+    return _WISHART_CACHE[key]
