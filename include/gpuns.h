@@ -53,7 +53,7 @@ extern "C" {
 #define NS_BIT_TIMEOUT    4   /* a device wait hit its bound */
 
 /* ---- enums -------------------------------------------------------------- */
-enum ns_kind { NS_KIND_GAUSS = 0, NS_KIND_SHEAR = 1 };
+enum ns_kind { NS_KIND_GAUSS = 0, NS_KIND_SHEAR = 1, NS_KIND_CMB = 2 };
 /* Arithmetic of the likelihood.  FP64: every stage in double.  FP32: every
  * stage in float (emulator on CUDA cores), the constant and the final log L in
  * double.  BF16: emulator hidden/output GEMMs as tcgen05 BF16 x BF16 -> FP32
@@ -61,7 +61,15 @@ enum ns_kind { NS_KIND_GAUSS = 0, NS_KIND_SHEAR = 1 };
  * whitening solve and chi^2 in FP64. */
 enum ns_precision { NS_PREC_FP64 = 0, NS_PREC_FP32 = 1, NS_PREC_BF16 = 2, NS_PREC_BF16_F64CHI2 = 3 };
 enum ns_prior_kind { NS_PRIOR_UNIFORM = 0, NS_PRIOR_GAUSS = 1, NS_PRIOR_FIXED = 2 };
-enum ns_activation { NS_ACT_TANH = 0 };
+/* Hidden-layer activation: tanh, or CosmoPower's "sigmoid-linear"
+ * f(x) = [g + (1 - g) sigmoid(beta x)] x with one (g, beta) per unit. */
+enum ns_activation { NS_ACT_TANH = 0, NS_ACT_SIGMOID_LINEAR = 1 };
+/* CMB chi^2 form (all exact in exact arithmetic; C = L L^T factorised in FP64 at
+ * create):  FOLD: the linear output head is folded into the whitening,
+ * W' = L^-1 diag(out_sigma) W_out and c' = L^-1 (d - out_mu - out_sigma b_out),
+ * so y = c' - W' h and no per-evaluation solve remains.  LITERAL: the model
+ * vector m is formed and y = L^-1 (d - m) per evaluation (FP64 only). */
+enum ns_cmb_solve { NS_SOLVE_FOLD = 0, NS_SOLVE_LITERAL = 1 };
 
 /* One prior per full parameter (Table 1).  UNIFORM: theta = a + (b - a) c;
  * GAUSS: theta = a + b Phi^-1(c) (mean a, sd b); FIXED: theta = a and the
@@ -83,7 +91,10 @@ typedef struct {
     const double* in_center;      /* dims[0] */
     const double* in_scale;       /* dims[0] */
     const double* out_mu;         /* dims[n_layers] */
-    double out_sigma;
+    double out_sigma;             /* scalar output scale (used when out_sigma_vec is NULL) */
+    const double* out_sigma_vec;  /* dims[n_layers] per-output scales, or NULL */
+    const double* const* act_g;   /* SIGMOID_LINEAR: act_g[l], l < n_layers - 1: dims[l+1] values */
+    const double* const* act_beta;/* SIGMOID_LINEAR: act_beta[l] likewise */
 } ns_emulator_desc;
 
 /* Cosmic-shear model (App. A).  Full parameter layout:
@@ -112,6 +123,14 @@ typedef struct {
     const double* tmpl;           /* n_data x n_tmpl noise templates (may be NULL if n_tmpl = 0) */
 } ns_shear_desc;
 
+/* CMB-like Gaussian likelihood (Sec. 3.1 test problem, dense-covariance form):
+ * the model is the emulator output itself (TT, TE, EE stacked, D = dims[n_layers]),
+ * inputs = the full parameter vector; log L = -1/2 |L^-1 (d - m)|^2 + c0.
+ * The emulator's last layer must be linear (it always is: the head has no
+ * activation).  Precisions FP64, FP32 and BF16 (hidden layers on tensor cores,
+ * head and chi^2 in FP32); LITERAL needs FP64. */
+typedef struct { int solve; } ns_cmb_desc;
+
 /* Isotropic Gaussian test likelihood on the cube: log L = -1/2 |(x - mu)/sigma|^2 - d ln(sigma sqrt(2 pi)). */
 typedef struct { double mu; double sigma; } ns_gauss_desc;
 
@@ -120,13 +139,16 @@ typedef struct {
     int precision;                /* ns_precision */
     int n_params;                 /* length of the full parameter vector */
     const ns_prior* priors;       /* n_params */
-    int n_data;                   /* D (shear); ignored for GAUSS */
+    int n_data;                   /* D (shear, CMB); ignored for GAUSS */
     const double* data;           /* D */
-    const double* cov;            /* D x D symmetric positive definite; factorised in FP64 */
+    const double* cov;            /* D x D symmetric positive definite; factorised in FP64.
+                                     data and cov may both be NULL: a model-only problem whose
+                                     loglike calls fail with NS_EINVAL */
     ns_emulator_desc emu;
     ns_shear_desc shear;
     ns_gauss_desc gauss;
     int max_batch;                /* largest batch B any call will pass (>= 1) */
+    ns_cmb_desc cmb;
 } ns_problem_desc;
 
 typedef struct ns_problem ns_problem;
@@ -164,8 +186,9 @@ typedef struct {
 const char* ns_strerror(int code);
 
 /* Build a problem on the current CUDA device: copies every host array, converts
- * weights to the problem precision, factorises cov = L L^T in FP64 (host),
- * forms L^-1 and the constant c0 = -sum ln L_aa - D/2 ln 2 pi.
+ * weights to the problem precision, factorises cov = L L^T in FP64 (on the host
+ * for D <= 1024, else by blocked FP64 kernels on the device), forms L^-1 (and,
+ * for the CMB fold, W' and c') and the constant c0 = -sum ln L_aa - D/2 ln 2 pi.
  * Errors: NS_EINVAL (bad sizes, non-SPD covariance, unknown enums),
  * NS_ENOMEM, NS_ECUDA, NS_ENOTSUP (e.g. BF16 with shapes the tensor-core
  * path cannot tile). */
@@ -186,14 +209,16 @@ int ns_prior_transform(const ns_problem* p, const double* cube_dev, int B,
 int loglike_batch(const ns_problem* p, const double* theta_dev, int B,
                   double* logL_dev, void* stream);
 
-/* Shear model data vector m(theta) (B x D, FP64 out), before the residual.
- * Used to build mock data.  NS_EINVAL for the GAUSS kind. */
+/* Model data vector m(theta) (B x D, FP64 out), before the residual: the shear
+ * spectra with biases and templates, or the CMB emulator output.  Used to
+ * build mock data.  NS_EINVAL for the GAUSS kind. */
 int ns_model_batch(const ns_problem* p, const double* theta_dev, int B,
                    double* model_dev, void* stream);
 
 /* Emulator output (B x dims[n_layers], FP64 out) at physical free parameters:
- * for the shear kind log10 P on the emulator's (z, k) grid, z-major, computed
- * in the problem precision (BF16: tcgen05 GEMMs with FP32 accumulation).
+ * for the shear kind log10 P on the emulator's (z, k) grid, z-major, for the
+ * CMB kind the spectra; computed in the problem precision (BF16: tcgen05 GEMMs
+ * with FP32 accumulation).
  * NS_EINVAL for the GAUSS kind. */
 int ns_emulator_batch(const ns_problem* p, const double* theta_dev, int B,
                       double* out_dev, void* stream);

@@ -41,15 +41,36 @@ class CMBOracle:
         self.set_data(data, cov)
 
     # ----------------------------------------------------------- emulator
-    def emulator(self, theta):
-        """De-standardised emulator output mu + sigma * y, shape (D,)."""
+    @staticmethod
+    def to_bf16(a):
+        """Round to the nearest bfloat16 (ties to even) through float32, returned as float64."""
+        f = np.asarray(a, dtype=np.float32).copy()
+        u = f.view(np.uint32)
+        u += np.uint32(0x7FFF) + ((u >> np.uint32(16)) & np.uint32(1))
+        u &= np.uint32(0xFFFF0000)
+        return u.view(np.float32).astype(np.float64)
+
+    def hidden(self, theta, bf16=False):
+        """Last hidden activation h.  With bf16=True the weights of the hidden
+        layers >= 1 and every hidden activation are rounded to bfloat16 (the
+        arithmetic stays FP64): the model the tensor-core path computes, up to
+        its FP32 accumulation order."""
         inp = self.inp
         x = (np.asarray(theta)[inp["emu_inputs"]] - inp["emu_in_center"]) / inp["emu_in_scale"]
         Ws, bs = inp["emu_W"], inp["emu_b"]
         h = x
         for l in range(len(Ws) - 1):
-            h = sigmoid_linear(Ws[l] @ h + bs[l], inp["act_g"][l], inp["act_beta"][l])
-        y = Ws[-1] @ h + bs[-1]
+            W = self.to_bf16(Ws[l]) if (bf16 and l >= 1) else Ws[l]
+            h = sigmoid_linear(W @ h + bs[l], inp["act_g"][l], inp["act_beta"][l])
+            if bf16:
+                h = self.to_bf16(h)
+        return h
+
+    def emulator(self, theta, bf16=False):
+        """De-standardised emulator output mu + sigma * y, shape (D,); the
+        linear head in FP64 (FP32 on the tensor-core path)."""
+        inp = self.inp
+        y = inp["emu_W"][-1] @ self.hidden(theta, bf16) + inp["emu_b"][-1]
         return inp["emu_out_mu"] + inp["emu_out_sig"] * y
 
     def model(self, theta):
@@ -82,8 +103,11 @@ class CMBOracle:
             y[a] = (r[a] - L[a, :a] @ y[:a]) / L[a, a]
         return y
 
+    def whitened(self, theta, bf16=False):
+        return self.forward_subst(self.data - self.emulator(theta, bf16))
+
     def chi2(self, theta):
-        y = self.forward_subst(self.data - self.model(theta))
+        y = self.whitened(theta)
         return float(np.sum(y * y))
 
     def loglike_full(self, theta):

@@ -11,7 +11,9 @@ LIB_PATH = os.path.join(_PKG, "libgpuns.so")
 
 NS_OK, NS_EINVAL, NS_ECUDA, NS_ENOMEM, NS_ETIMEOUT, NS_ESLICE, NS_ENONFINITE, NS_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
 NS_BIT_SLICE_CAP, NS_BIT_NONFINITE, NS_BIT_TIMEOUT = 1, 2, 4
-NS_KIND_GAUSS, NS_KIND_SHEAR = 0, 1
+NS_KIND_GAUSS, NS_KIND_SHEAR, NS_KIND_CMB = 0, 1, 2
+NS_ACT = {"tanh": 0, "sigmoid_linear": 1}
+NS_SOLVE = {"fold": 0, "literal": 1}
 NS_PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16_f64chi2": 3}
 NS_PRIOR = {"U": 0, "N": 1, "F": 2}
 
@@ -31,7 +33,9 @@ class EmulatorDesc(C.Structure):
                 ("W", C.POINTER(C.POINTER(C.c_double))), ("b", C.POINTER(C.POINTER(C.c_double))),
                 ("activation", C.c_int), ("inputs", C.POINTER(C.c_int)),
                 ("in_center", C.POINTER(C.c_double)), ("in_scale", C.POINTER(C.c_double)),
-                ("out_mu", C.POINTER(C.c_double)), ("out_sigma", C.c_double)]
+                ("out_mu", C.POINTER(C.c_double)), ("out_sigma", C.c_double),
+                ("out_sigma_vec", C.POINTER(C.c_double)),
+                ("act_g", C.POINTER(C.POINTER(C.c_double))), ("act_beta", C.POINTER(C.POINTER(C.c_double)))]
 
 
 class ShearDesc(C.Structure):
@@ -47,11 +51,16 @@ class GaussDesc(C.Structure):
     _fields_ = [("mu", C.c_double), ("sigma", C.c_double)]
 
 
+class CmbDesc(C.Structure):
+    _fields_ = [("solve", C.c_int)]
+
+
 class ProblemDesc(C.Structure):
     _fields_ = [("kind", C.c_int), ("precision", C.c_int), ("n_params", C.c_int),
                 ("priors", C.POINTER(Prior)), ("n_data", C.c_int),
                 ("data", C.POINTER(C.c_double)), ("cov", C.POINTER(C.c_double)),
-                ("emu", EmulatorDesc), ("shear", ShearDesc), ("gauss", GaussDesc), ("max_batch", C.c_int)]
+                ("emu", EmulatorDesc), ("shear", ShearDesc), ("gauss", GaussDesc), ("max_batch", C.c_int),
+                ("cmb", CmbDesc)]
 
 
 class Config(C.Structure):

@@ -36,15 +36,19 @@ def _require_cuda(t: torch.Tensor, name: str, dtype=torch.float64):
 class Problem:
     """A likelihood problem resident on the current CUDA device."""
 
-    def __init__(self, inp: dict, precision: str = "fp64", max_batch: int = 1024, data=None, cov=None):
+    def __init__(self, inp: dict, precision: str = "fp64", max_batch: int = 1024, data=None, cov=None,
+                 solve: str = "fold"):
         self.lib = L.load()
         self.inp = inp
         self.kind = inp["kind"]
         self.precision = precision
         self.max_batch = int(max_batch)
+        self.solve = solve
         self._h = C.c_void_p()
         if self.kind == "shear" and (data is None or cov is None):
             data, cov = self._make_mock()
+        elif self.kind == "cmb" and (data is None or cov is None):
+            data, cov = self._make_mock_cmb()
         self.data = None if data is None else np.ascontiguousarray(data, dtype=np.float64)
         self.cov = None if cov is None else np.ascontiguousarray(cov, dtype=np.float64)
         self._create(precision, self.max_batch, self.data, self.cov, self._templates(self.cov))
@@ -81,11 +85,26 @@ class Problem:
         data = mfid + np.linalg.cholesky(cov) @ inp["noise_eps"]
         return data, cov
 
+    def _make_mock_cmb(self):
+        """C = s W (seeded Wishart base, s from the library's FP64 fiducial
+        model: mean variance (cov_rel * rms m_fid)^2) and data = m_fid + L eps."""
+        from workloads import wishart_base
+        inp = self.inp
+        self._create("fp64", 1, None, None, None)
+        th = torch.tensor(np.asarray(inp["fiducial"], float)[None, :], dtype=torch.float64, device="cuda")
+        mfid = self.model(th)[0].cpu().numpy()
+        self._free()
+        W = wishart_base(int(inp["n_data"]), int(inp["wishart_nu"]), int(inp["seed_cov"]))
+        s = (inp["cov_rel"] * np.sqrt(np.mean(mfid * mfid))) ** 2 / np.mean(np.diag(W))
+        cov = s * W
+        data = mfid + np.linalg.cholesky(cov) @ inp["noise_eps"]
+        return data, cov
+
     def _create(self, precision, max_batch, data, cov, tmpl):
         inp = self.inp
         keep = []   # arrays that must stay alive during ns_problem_create
         desc = L.ProblemDesc()
-        desc.kind = L.NS_KIND_SHEAR if self.kind == "shear" else L.NS_KIND_GAUSS
+        desc.kind = {"shear": L.NS_KIND_SHEAR, "cmb": L.NS_KIND_CMB}.get(self.kind, L.NS_KIND_GAUSS)
         desc.precision = L.NS_PREC[precision]
         pri = inp["priors"]
         desc.n_params = len(pri)
@@ -99,6 +118,8 @@ class Problem:
             D = len(inp["noise_eps"])
             desc.n_data = D
             for arr, field in ((data, "data"), (cov, "cov")):
+                if arr is None:
+                    continue
                 a = np.ascontiguousarray(arr, dtype=np.float64)
                 keep.append(a)
                 setattr(desc, field, _dptr(a))
@@ -119,11 +140,29 @@ class Problem:
             e.dims = _iptr(dims)
             e.W = C.cast(Wp, C.POINTER(C.POINTER(C.c_double)))
             e.b = C.cast(bp, C.POINTER(C.POINTER(C.c_double)))
-            e.activation = 0
             e.inputs = _iptr(ins)
             e.in_center = _dptr(cen)
             e.in_scale = _dptr(scl)
             e.out_mu = _dptr(mu)
+            e.activation = L.NS_ACT[inp.get("emu_act", "tanh")]
+            if e.activation == L.NS_ACT["sigmoid_linear"]:
+                gs = [np.ascontiguousarray(g, dtype=np.float64) for g in inp["act_g"]]
+                bs_ = [np.ascontiguousarray(b, dtype=np.float64) for b in inp["act_beta"]]
+                gp = (C.POINTER(C.c_double) * len(gs))(*[_dptr(g) for g in gs])
+                bp2 = (C.POINTER(C.c_double) * len(bs_))(*[_dptr(b) for b in bs_])
+                keep += gs + bs_ + [gp, bp2]
+                e.act_g = C.cast(gp, C.POINTER(C.POINTER(C.c_double)))
+                e.act_beta = C.cast(bp2, C.POINTER(C.POINTER(C.c_double)))
+            if self.kind == "cmb":
+                sv = np.ascontiguousarray(inp["emu_out_sig"], dtype=np.float64)
+                keep.append(sv)
+                e.out_sigma = 1.0
+                e.out_sigma_vec = _dptr(sv)
+                desc.cmb.solve = L.NS_SOLVE[self.solve]
+                h = C.c_void_p()
+                L.check(self.lib.ns_problem_create(C.byref(desc), C.byref(h)), "ns_problem_create")
+                self._h = h
+                return
             e.out_sigma = float(inp["emu_out_sigma"])
             s = desc.shear
             nzm = np.ascontiguousarray(inp["nz_mean"], dtype=np.float64)

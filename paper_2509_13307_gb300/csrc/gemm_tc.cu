@@ -104,7 +104,8 @@ template <int BN, int EPI>
 __global__ void __launch_bounds__(128, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           const float* __restrict__ bias, const float* __restrict__ out_mu, float out_sigma,
-          void* __restrict__ Cout, const int* __restrict__ nrows, int N, int K, int* __restrict__ err) {
+          void* __restrict__ Cout, const int* __restrict__ nrows, int N, int K, const float* __restrict__ act_beta,
+          int* __restrict__ err) {
     using C = Cfg<BN>;
     const int M = *nrows;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -180,14 +181,21 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             tmem_ld32(lane_addr + c * 32, v);
             const int col0 = n0 + c * 32;
             if (row >= M || col0 >= N) continue;
-            if (EPI == 0) {
+            if (EPI == 0 || EPI == 2) {
+                // hidden layer: tanh (EPI 0) or sigmoid-linear with per-unit
+                // (g, beta) = (out_mu, act_beta) (EPI 2); stored bf16
+                auto act = [&](float x, int col) {
+                    if (EPI == 0) return tanh_fast(x);
+                    const float g = __ldg(out_mu + col);
+                    return (g + (1.f - g) / (1.f + __expf(-__ldg(act_beta + col) * x))) * x;
+                };
                 __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(Cout) + (size_t)row * N + col0;
                 if (col0 + 32 <= N && (N % 8) == 0) {
                     uint32_t pk[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const float a0 = tanh_fast(v[2 * j] + __ldg(bias + col0 + 2 * j));
-                        const float a1 = tanh_fast(v[2 * j + 1] + __ldg(bias + col0 + 2 * j + 1));
+                        const float a0 = act(v[2 * j] + __ldg(bias + col0 + 2 * j), col0 + 2 * j);
+                        const float a1 = act(v[2 * j + 1] + __ldg(bias + col0 + 2 * j + 1), col0 + 2 * j + 1);
                         __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, a1);
                         pk[j] = *reinterpret_cast<uint32_t*>(&h2);
                     }
@@ -196,7 +204,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     for (int q = 0; q < 4; ++q) o4[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
                 } else {
                     for (int j = 0; j < 32 && col0 + j < N; ++j)
-                        out[j] = __float2bfloat16_rn(tanh_fast(v[j] + bias[col0 + j]));
+                        out[j] = __float2bfloat16_rn(act(v[j] + bias[col0 + j], col0 + j));
                 }
             } else {
                 float* out = reinterpret_cast<float*>(Cout) + (size_t)row * N + col0;
@@ -229,18 +237,23 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
 template <int BN>
 static int launch_bn(const CUtensorMap* tmA, const CUtensorMap* tmB, const float* bias, const float* mu,
-                     float sigma, void* Cout, const int* nrows, int grid_rows, int N, int K, int epi, int* err,
-                     cudaStream_t st) {
+                     float sigma, void* Cout, const int* nrows, int grid_rows, int N, int K, int epi,
+                     const float* beta, int* err, cudaStream_t st) {
     using C = Cfg<BN>;
     static bool attr = false;
     if (!attr) {
         NS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<BN, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
         NS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<BN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<BN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
         attr = true;
     }
     dim3 grid((N + BN - 1) / BN, (grid_rows + BM - 1) / BM);
-    if (epi == 0) k_gemm_tc<BN, 0><<<grid, 128, C::SMEM, st>>>(*tmA, *tmB, bias, mu, sigma, Cout, nrows, N, K, err);
-    else k_gemm_tc<BN, 1><<<grid, 128, C::SMEM, st>>>(*tmA, *tmB, bias, mu, sigma, Cout, nrows, N, K, err);
+    if (epi == TC_EPI_TANH)
+        k_gemm_tc<BN, 0><<<grid, 128, C::SMEM, st>>>(*tmA, *tmB, bias, mu, sigma, Cout, nrows, N, K, beta, err);
+    else if (epi == TC_EPI_OUT)
+        k_gemm_tc<BN, 1><<<grid, 128, C::SMEM, st>>>(*tmA, *tmB, bias, mu, sigma, Cout, nrows, N, K, beta, err);
+    else
+        k_gemm_tc<BN, 2><<<grid, 128, C::SMEM, st>>>(*tmA, *tmB, bias, mu, sigma, Cout, nrows, N, K, beta, err);
     NS_CUDA_TRY(cudaGetLastError());
     return NS_OK;
 }
@@ -249,13 +262,13 @@ static int launch_bn(const CUtensorMap* tmA, const CUtensorMap* tmB, const float
 
 int launch_gemm_tc(const CUtensorMap* tmA, const CUtensorMap* tmB, int tile_n, const float* bias,
                    const float* out_mu, float out_sigma, void* C, const int* d_nrows, int grid_rows, int N, int K,
-                   int epi, int* d_err, cudaStream_t st) {
+                   int epi, const float* act_beta, int* d_err, cudaStream_t st) {
     if (grid_rows <= 0) return NS_OK;
     switch (tile_n) {
-        case 32: return tc::launch_bn<32>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, d_err, st);
-        case 64: return tc::launch_bn<64>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, d_err, st);
-        case 128: return tc::launch_bn<128>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, d_err, st);
-        case 256: return tc::launch_bn<256>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, d_err, st);
+        case 32: return tc::launch_bn<32>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, act_beta, d_err, st);
+        case 64: return tc::launch_bn<64>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, act_beta, d_err, st);
+        case 128: return tc::launch_bn<128>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, act_beta, d_err, st);
+        case 256: return tc::launch_bn<256>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, act_beta, d_err, st);
         default: return NS_EINVAL;
     }
 }

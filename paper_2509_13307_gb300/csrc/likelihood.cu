@@ -80,19 +80,40 @@ __global__ void k_gauss_loglike(const double* __restrict__ theta_full, int P, do
 }
 
 // ------------------------------------------------------------ emulator
+// Hidden-layer activation: tanh, or CosmoPower's sigmoid-linear
+// f(x) = [g + (1 - g) sigmoid(beta x)] x with one (g, beta) per unit.
 template <typename T> __device__ inline T act_tanh(T x);
 template <> __device__ inline double act_tanh<double>(double x) { return tanh(x); }
 template <> __device__ inline float act_tanh<float>(float x) { return tanhf(x); }
+template <typename T> __device__ inline T ex_acc(T x);
+template <> __device__ inline double ex_acc<double>(double x) { return exp(x); }
+template <> __device__ inline float ex_acc<float>(float x) { return expf(x); }
 
-template <typename TO> __device__ inline TO to_out(float v);
-template <> __device__ inline float to_out<float>(float v) { return v; }
-template <> __device__ inline __nv_bfloat16 to_out<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <typename T>
+struct ActDev {
+    int kind;
+    const T* g;
+    const T* beta;
+};
 
-// Input layer: h = tanh(W0 x + b0), x = (theta[inputs] - center) / scale.
+template <typename T>
+__device__ __forceinline__ T act_apply(const ActDev<T>& a, int n, T x) {
+    if (a.kind == NS_ACT_TANH) return act_tanh<T>(x);
+    const T g = a.g[n];
+    return (g + (T(1) - g) / (T(1) + ex_acc<T>(-a.beta[n] * x))) * x;
+}
+
+template <typename TO, typename T> __device__ inline TO cvt_out(T v) { return (TO)v; }
+template <> __device__ inline __nv_bfloat16 cvt_out<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+
+template <typename T> __device__ inline T cvt_in(T v) { return v; }
+__device__ inline float cvt_in(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Input layer: h = act(W0 x + b0), x = (theta[inputs] - center) / scale.
 template <typename T, typename TO>
 __global__ void k_emu_input(const double* __restrict__ theta_full, int P, const int* __restrict__ inputs,
                             const double* __restrict__ center, const double* __restrict__ scale, int K0,
-                            const T* __restrict__ W0, const T* __restrict__ b0, int N,
+                            const T* __restrict__ W0, const T* __restrict__ b0, ActDev<T> act, int N,
                             TO* __restrict__ out, const int* __restrict__ nrows) {
     const int row = blockIdx.y;
     if (row >= *nrows) return;
@@ -105,38 +126,21 @@ __global__ void k_emu_input(const double* __restrict__ theta_full, int P, const 
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     T acc = b0[n];
-    for (int j = 0; j < K0; ++j) acc += W0[(size_t)n * K0 + j] * x[j];
-    out[(size_t)row * N + n] = (TO)act_tanh<T>(acc);
+    for (int j = 0; j < K0; ++j) acc = fma(W0[(size_t)n * K0 + j], x[j], acc);
+    out[(size_t)row * N + n] = cvt_out<TO, T>(act_apply<T>(act, n, acc));
 }
-template <>
-__global__ void k_emu_input<float, __nv_bfloat16>(const double* __restrict__ theta_full, int P,
-        const int* __restrict__ inputs, const double* __restrict__ center, const double* __restrict__ scale,
-        int K0, const float* __restrict__ W0, const float* __restrict__ b0, int N,
-        __nv_bfloat16* __restrict__ out, const int* __restrict__ nrows) {
-    const int row = blockIdx.y;
-    if (row >= *nrows) return;
-    __shared__ float x[32];
-    if (threadIdx.x < K0) {
-        const int j = threadIdx.x;
-        x[j] = (float)((theta_full[(size_t)row * P + inputs[j]] - center[j]) / scale[j]);
-    }
-    __syncthreads();
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    float acc = b0[n];
-    for (int j = 0; j < K0; ++j) acc = fmaf(W0[(size_t)n * K0 + j], x[j], acc);
-    out[(size_t)row * N + n] = __float2bfloat16_rn(tanhf(acc));
-}
-
-enum { EPI_TANH = 0, EPI_OUT = 1 };
 
 // C[M x N] = epi(A[M x K] W[N x K]^T + b).  Threads own an interleaved
 // TM x TN sub-tile (rows ty + i*BM/TM, cols tx + j*BN/TN) so shared-memory
-// reads and global stores are conflict-free / coalesced.
-template <typename T, int BM, int BN, int BK, int TM, int TN, int EPI>
+// reads and global stores are conflict-free / coalesced.  A may be stored in
+// a narrower type (bf16 activations) and is widened on load.
+//   EPI_ACT: act(acc + b);  EPI_OUT: mu + s (acc + b), s = sig_vec[n] or sigma.
+enum { EPI_ACT = 0, EPI_OUT = 1 };
+
+template <typename T, typename TA, int BM, int BN, int BK, int TM, int TN, int EPI>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
-k_gemm_simt(const T* __restrict__ A, const T* __restrict__ W, const T* __restrict__ bias,
-            const T* __restrict__ out_mu, T out_sigma, T* __restrict__ C,
+k_gemm_simt(const TA* __restrict__ A, const T* __restrict__ W, const T* __restrict__ bias, ActDev<T> act,
+            const T* __restrict__ out_mu, const T* __restrict__ sig_vec, T out_sigma, T* __restrict__ C,
             const int* __restrict__ nrows, int N, int K) {
     constexpr int TX = BN / TN, TY = BM / TM, NT = TX * TY;
     const int M = *nrows;
@@ -154,7 +158,7 @@ k_gemm_simt(const T* __restrict__ A, const T* __restrict__ W, const T* __restric
         for (int i = tid; i < BM * BK; i += NT) {
             const int r = i / BK, c = i % BK;
             const int gm = m0 + r, gk = k0 + c;
-            As[c][r] = (gm < M && gk < K) ? A[(size_t)gm * K + gk] : T(0);
+            As[c][r] = (gm < M && gk < K) ? (T)cvt_in(A[(size_t)gm * K + gk]) : T(0);
         }
         for (int i = tid; i < BN * BK; i += NT) {
             const int r = i / BK, c = i % BK;
@@ -184,9 +188,9 @@ k_gemm_simt(const T* __restrict__ A, const T* __restrict__ W, const T* __restric
         for (int j = 0; j < TN; ++j) {
             const int gn = n0 + tx + j * TX;
             if (gn >= N) continue;
-            T v = acc[i][j] + bias[gn];
-            if (EPI == EPI_TANH) v = act_tanh<T>(v);
-            else v = out_mu[gn] + out_sigma * v;
+            T v = acc[i][j] + (bias ? bias[gn] : T(0));
+            if (EPI == EPI_ACT) v = act_apply<T>(act, gn, v);
+            else v = out_mu[gn] + (sig_vec ? sig_vec[gn] : out_sigma) * v;
             C[(size_t)gm * N + gn] = v;
         }
     }
@@ -211,36 +215,33 @@ __global__ void k_zinterp(const T* __restrict__ coarse, int nzc, const int* __re
     }
 }
 
-template <typename T>
-static int launch_gemm_simt(const T* A, const T* W, const T* bias, const T* mu, T sigma, T* C,
-                            const int* nrows, int grid_rows, int N, int K, int epi, cudaStream_t st);
+template <typename T, typename TA>
+struct SimtTile;
+template <typename TA> struct SimtTile<double, TA> { static constexpr int BM = 64, BN = 64, BK = 8, TM = 4, TN = 4; };
+template <typename TA> struct SimtTile<float, TA> { static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8; };
 
-template <>
-int launch_gemm_simt<double>(const double* A, const double* W, const double* bias, const double* mu,
-                             double sigma, double* C, const int* nrows, int grid_rows, int N, int K,
-                             int epi, cudaStream_t st) {
-    constexpr int BM = 64, BN = 64, BK = 8, TM = 4, TN = 4;
-    dim3 grid((N + BN - 1) / BN, (grid_rows + BM - 1) / BM);
-    if (epi == EPI_TANH)
-        k_gemm_simt<double, BM, BN, BK, TM, TN, EPI_TANH><<<grid, 256, 0, st>>>(A, W, bias, mu, sigma, C, nrows, N, K);
+template <typename T, typename TA>
+int launch_gemm_simt(const TA* A, const T* W, const T* bias, ActDev<T> act, const T* mu, const T* sig_vec, T sigma,
+                     T* C, const int* nrows, int grid_rows, int N, int K, int epi, cudaStream_t st) {
+    using S = SimtTile<T, TA>;
+    constexpr int NT = (S::BM / S::TM) * (S::BN / S::TN);
+    dim3 grid((N + S::BN - 1) / S::BN, (grid_rows + S::BM - 1) / S::BM);
+    if (epi == EPI_ACT)
+        k_gemm_simt<T, TA, S::BM, S::BN, S::BK, S::TM, S::TN, EPI_ACT><<<grid, NT, 0, st>>>(
+            A, W, bias, act, mu, sig_vec, sigma, C, nrows, N, K);
     else
-        k_gemm_simt<double, BM, BN, BK, TM, TN, EPI_OUT><<<grid, 256, 0, st>>>(A, W, bias, mu, sigma, C, nrows, N, K);
+        k_gemm_simt<T, TA, S::BM, S::BN, S::BK, S::TM, S::TN, EPI_OUT><<<grid, NT, 0, st>>>(
+            A, W, bias, act, mu, sig_vec, sigma, C, nrows, N, K);
     NS_CUDA_TRY(cudaGetLastError());
     return NS_OK;
 }
 
-template <>
-int launch_gemm_simt<float>(const float* A, const float* W, const float* bias, const float* mu, float sigma,
-                            float* C, const int* nrows, int grid_rows, int N, int K, int epi,
-                            cudaStream_t st) {
-    constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
-    dim3 grid((N + BN - 1) / BN, (grid_rows + BM - 1) / BM);
-    if (epi == EPI_TANH)
-        k_gemm_simt<float, BM, BN, BK, TM, TN, EPI_TANH><<<grid, 256, 0, st>>>(A, W, bias, mu, sigma, C, nrows, N, K);
-    else
-        k_gemm_simt<float, BM, BN, BK, TM, TN, EPI_OUT><<<grid, 256, 0, st>>>(A, W, bias, mu, sigma, C, nrows, N, K);
-    NS_CUDA_TRY(cudaGetLastError());
-    return NS_OK;
+// Plain FP64 GEMM C = A W^T (M x N, K inner) on the device, for set-up work
+// (the CMB whitening fold); nrows_dev holds M.
+int gemm_f64_plain(const double* A, const double* W, double* C, const int* nrows_dev, int M, int N, int K,
+                   const double* zeros_n, cudaStream_t st) {
+    return launch_gemm_simt<double, double>(A, W, zeros_n, ActDev<double>{0, nullptr, nullptr}, zeros_n, nullptr,
+                                            1.0, C, nrows_dev, M, N, K, EPI_OUT, st);
 }
 
 int launch_cube_to_theta(const ns_problem* p, Workspace* ws, const double* cube, int grid_rows,
@@ -253,22 +254,51 @@ int launch_cube_to_theta(const ns_problem* p, Workspace* ws, const double* cube,
 }
 
 template <typename T>
-static int run_emulator_simt(const ns_problem* p, Workspace* ws, int grid_rows, cudaStream_t st) {
+static ActDev<T> layer_act(const ns_problem* p, int l) {
+    ActDev<T> a{p->act, nullptr, nullptr};
+    if (p->act == NS_ACT_SIGMOID_LINEAR) {
+        a.g = (const T*)p->d_act_g[l];
+        a.beta = (const T*)p->d_act_beta[l];
+    }
+    return a;
+}
+
+// The emulator's last layer: W h + b, de-standardised as mu + s * (.), written to out.
+struct Head {
+    const void* W;
+    const void* bias;
+    const void* mu;
+    const void* sig_vec;
+    double sigma;
+    void* out;
+};
+
+static Head model_head(const ns_problem* p, void* out) {
+    const int L = p->n_layers;
+    return Head{p->d_W[L - 1], p->d_b[L - 1], p->d_out_mu, p->d_out_sig, p->out_sigma, out};
+}
+
+template <typename T>
+static int run_emulator_simt(const ns_problem* p, Workspace* ws, int grid_rows, cudaStream_t st, const Head& hd) {
     const int L = p->n_layers;
     const int K0 = p->dims[0], H1 = p->dims[1];
     dim3 g0((H1 + 255) / 256, grid_rows);
     k_emu_input<T, T><<<g0, 256, 0, st>>>(ws->theta_full, p->P, p->d_inputs, p->d_in_center, p->d_in_scale,
-                                          K0, (const T*)p->d_W[0], (const T*)p->d_b[0], H1, (T*)ws->act[0],
-                                          ws->d_nrows);
+                                          K0, (const T*)p->d_W[0], (const T*)p->d_b[0], layer_act<T>(p, 0), H1,
+                                          (T*)ws->act[0], ws->d_nrows);
     NS_CUDA_TRY(cudaGetLastError());
     int cur = 0;
     for (int l = 1; l < L; ++l) {
         const int K = p->dims[l], N = p->dims[l + 1];
-        const bool last = (l == L - 1);
-        T* out = last ? (T*)ws->table : (T*)ws->act[cur ^ 1];
-        NS_TRY(launch_gemm_simt<T>((const T*)ws->act[cur], (const T*)p->d_W[l], (const T*)p->d_b[l],
-                                   (const T*)p->d_out_mu, (T)p->out_sigma, out, ws->d_nrows, grid_rows, N, K,
-                                   last ? EPI_OUT : EPI_TANH, st));
+        if (l == L - 1) {
+            NS_TRY((launch_gemm_simt<T, T>((const T*)ws->act[cur], (const T*)hd.W, (const T*)hd.bias, ActDev<T>{0, nullptr, nullptr},
+                                           (const T*)hd.mu, (const T*)hd.sig_vec, (T)hd.sigma, (T*)hd.out,
+                                           ws->d_nrows, grid_rows, N, K, EPI_OUT, st)));
+        } else {
+            NS_TRY((launch_gemm_simt<T, T>((const T*)ws->act[cur], (const T*)p->d_W[l], (const T*)p->d_b[l],
+                                           layer_act<T>(p, l), nullptr, nullptr, T(0), (T*)ws->act[cur ^ 1],
+                                           ws->d_nrows, grid_rows, N, K, EPI_ACT, st)));
+        }
         cur ^= 1;
     }
     return NS_OK;
@@ -286,25 +316,38 @@ static int probe_end(const StageProbe* pr, int stage, cudaStream_t st) {
     return NS_OK;
 }
 
+// BF16: input layer on CUDA cores, hidden layers as tcgen05 GEMMs with the
+// activation in the epilogue.  The last layer: for the shear kind a tcgen05
+// GEMM with the de-standardising epilogue into the FP32 table; for the CMB
+// kind `hd` on CUDA cores in FP32 (the folded head needs FP32 weights).
 static int run_emulator_bf16(const ns_problem* p, Workspace* ws, int grid_rows, cudaStream_t st,
-                             const StageProbe* probe = nullptr) {
+                             const StageProbe* probe, const Head* hd) {
     const int L = p->n_layers;
     const int K0 = p->dims[0], H1 = p->dims[1];
     dim3 g0((H1 + 255) / 256, grid_rows);
     k_emu_input<float, __nv_bfloat16><<<g0, 256, 0, st>>>(
         ws->theta_full, p->P, p->d_inputs, p->d_in_center, p->d_in_scale, K0, (const float*)p->d_W[0],
-        (const float*)p->d_b[0], H1, (__nv_bfloat16*)ws->act[0], ws->d_nrows);
+        (const float*)p->d_b[0], layer_act<float>(p, 0), H1, (__nv_bfloat16*)ws->act[0], ws->d_nrows);
     NS_CUDA_TRY(cudaGetLastError());
     int cur = 0;
     for (int l = 1; l < L; ++l) {
         const int K = p->dims[l], N = p->dims[l + 1];
         const bool last = (l == L - 1);
-        void* out = last ? ws->table : ws->act[cur ^ 1];
         const int stage = last ? PROBE_EMU_OUT : (l == 1 ? PROBE_EMU_HIDDEN : PROBE_NONE);
         NS_TRY(probe_begin(probe, stage, ws, st));
-        NS_TRY(launch_gemm_tc(&ws->tmA[l], &p->tmB[l], p->tile_n[l], (const float*)p->d_b[l],
-                              (const float*)p->d_out_mu, (float)p->out_sigma, out, ws->d_nrows, grid_rows,
-                              N, K, last ? 1 : 0, ws->d_err, st));
+        if (last && hd) {
+            NS_TRY((launch_gemm_simt<float, __nv_bfloat16>(
+                (const __nv_bfloat16*)ws->act[cur], (const float*)hd->W, (const float*)hd->bias,
+                ActDev<float>{0, nullptr, nullptr}, (const float*)hd->mu, (const float*)hd->sig_vec,
+                (float)hd->sigma, (float*)hd->out, ws->d_nrows, grid_rows, N, K, EPI_OUT, st)));
+        } else {
+            const ActDev<float> a = layer_act<float>(p, l);
+            const int epi = last ? TC_EPI_OUT : (p->act == NS_ACT_SIGMOID_LINEAR ? TC_EPI_SIGLIN : TC_EPI_TANH);
+            NS_TRY(launch_gemm_tc(&ws->tmA[l], &p->tmB[l], p->tile_n[l], (const float*)p->d_b[l],
+                                  last ? (const float*)p->d_out_mu : a.g, last ? (float)p->out_sigma : 0.f,
+                                  last ? ws->table : ws->act[cur ^ 1], ws->d_nrows, grid_rows, N, K, epi,
+                                  last ? nullptr : a.beta, ws->d_err, st));
+        }
         NS_TRY(probe_end(probe, stage, st));
         cur ^= 1;
     }
@@ -320,20 +363,70 @@ __global__ void k_to_double(const T* __restrict__ in, double* __restrict__ out, 
         out[(size_t)row * n_per_row + i] = (double)in[(size_t)row * n_per_row + i];
 }
 
+// chi^2 = sum_a y_a^2 per row (fixed-order block tree, partials widened to
+// FP64), log L = c0 - chi^2 / 2 in FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rowsq(const T* __restrict__ y, int D, double c0, double* __restrict__ logL,
+                                               const int* __restrict__ nrows) {
+    const int row = blockIdx.x;
+    if (row >= *nrows) return;
+    __shared__ double part[256];
+    const T* yr = y + (size_t)row * D;
+    T s = T(0);
+    for (int a = threadIdx.x; a < D; a += 256) s = fma(yr[a], yr[a], s);
+    part[threadIdx.x] = (double)s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) logL[row] = c0 - 0.5 * part[0];
+}
+
 int run_emulator_only(const ns_problem* p, Workspace* ws, int grid_rows, double* out, cudaStream_t st) {
     if (grid_rows <= 0) return NS_OK;
     const int n_out = p->dims.back();
     dim3 g((n_out + 255) / 256, grid_rows);
+    const Head hd = model_head(p, ws->table);
     if (p->precision == NS_PREC_FP64) {
-        NS_TRY(run_emulator_simt<double>(p, ws, grid_rows, st));
+        NS_TRY(run_emulator_simt<double>(p, ws, grid_rows, st, hd));
         k_to_double<double><<<g, 256, 0, st>>>((const double*)ws->table, out, n_out, ws->d_nrows);
     } else {
-        if (p->precision == NS_PREC_FP32) NS_TRY(run_emulator_simt<float>(p, ws, grid_rows, st));
-        else NS_TRY(run_emulator_bf16(p, ws, grid_rows, st));
+        if (p->precision == NS_PREC_FP32) NS_TRY(run_emulator_simt<float>(p, ws, grid_rows, st, hd));
+        else NS_TRY(run_emulator_bf16(p, ws, grid_rows, st, nullptr, p->kind == NS_KIND_CMB ? &hd : nullptr));
         k_to_double<float><<<g, 256, 0, st>>>((const float*)ws->table, out, n_out, ws->d_nrows);
     }
     NS_CUDA_TRY(cudaGetLastError());
     return NS_OK;
+}
+
+// CMB kind (Sec. 3.1 problem, dense covariance): FOLD runs the hidden layers
+// and the folded head y = c' - W' h, then chi^2 = |y|^2; LITERAL (FP64) forms
+// r = (d - mu) - sigma (W h + b) with the same head kernel and whitens it by
+// L^-1; model_out gets the de-standardised emulator output.
+static int run_cmb(const ns_problem* p, Workspace* ws, int grid_rows, double* logL_out, double* model_out,
+                   cudaStream_t st, const StageProbe* probe) {
+    const int D = p->D;
+    if (model_out) return run_emulator_only(p, ws, grid_rows, model_out, st);
+    const bool f64 = p->precision == NS_PREC_FP64;
+    if (p->cmb_solve == NS_SOLVE_LITERAL) {
+        const int L = p->n_layers;
+        const Head hd{p->d_W[L - 1], p->d_b[L - 1], p->d_lit_mu, p->d_lit_sig, 0.0, ws->resid};
+        NS_TRY(run_emulator_simt<double>(p, ws, grid_rows, st, hd));
+        NS_TRY(probe_begin(probe, PROBE_CHI2, ws, st));
+        NS_TRY((launch_chi2<double, double>((const double*)ws->resid, D, p->d_LinvT64, p->c0, logL_out,
+                                            ws->chi2_part, ws->chi2_done, ws->d_nrows, grid_rows, st)));
+        return probe_end(probe, PROBE_CHI2, st);
+    }
+    const Head hd{p->d_Wfold, p->d_zeroD, p->d_cfold, nullptr, -1.0, ws->table};
+    if (f64) NS_TRY(run_emulator_simt<double>(p, ws, grid_rows, st, hd));
+    else if (p->precision == NS_PREC_FP32) NS_TRY(run_emulator_simt<float>(p, ws, grid_rows, st, hd));
+    else NS_TRY(run_emulator_bf16(p, ws, grid_rows, st, probe, &hd));
+    NS_TRY(probe_begin(probe, PROBE_CHI2, ws, st));
+    if (f64) k_rowsq<double><<<grid_rows, 256, 0, st>>>((const double*)ws->table, D, p->c0, logL_out, ws->d_nrows);
+    else k_rowsq<float><<<grid_rows, 256, 0, st>>>((const float*)ws->table, D, p->c0, logL_out, ws->d_nrows);
+    NS_CUDA_TRY(cudaGetLastError());
+    return probe_end(probe, PROBE_CHI2, st);
 }
 
 int run_likelihood(const ns_problem* p, Workspace* ws, int grid_rows, double* logL_out, double* model_out,
@@ -345,6 +438,7 @@ int run_likelihood(const ns_problem* p, Workspace* ws, int grid_rows, double* lo
         NS_CUDA_TRY(cudaGetLastError());
         return NS_OK;
     }
+    if (p->kind == NS_KIND_CMB) return run_cmb(p, ws, grid_rows, logL_out, model_out, st, probe);
     const ShearParams& sp = p->sp;
     const bool coarse = p->n_z_emu != sp.n_z;
     const bool f64 = p->precision == NS_PREC_FP64;
@@ -360,7 +454,7 @@ int run_likelihood(const ns_problem* p, Workspace* ws, int grid_rows, double* lo
     NS_TRY(probe_end(probe, PROBE_WINDOWS, ws->side));
     NS_CUDA_TRY(cudaEventRecord(ws->ev_join, ws->side));
     if (f64) {
-        NS_TRY(run_emulator_simt<double>(p, ws, grid_rows, st));
+        NS_TRY(run_emulator_simt<double>(p, ws, grid_rows, st, model_head(p, ws->table)));
         const double* tab = (const double*)ws->table;
         if (coarse) {
             dim3 g((sp.n_z * sp.n_k + 255) / 256, grid_rows);
@@ -377,8 +471,8 @@ int run_likelihood(const ns_problem* p, Workspace* ws, int grid_rows, double* lo
                                            ws->chi2_part, ws->chi2_done, ws->d_nrows, grid_rows, st);
     }
     // FP32 stages (FP32 / BF16 / BF16_F64CHI2)
-    if (p->precision == NS_PREC_FP32) NS_TRY(run_emulator_simt<float>(p, ws, grid_rows, st));
-    else NS_TRY(run_emulator_bf16(p, ws, grid_rows, st, probe));
+    if (p->precision == NS_PREC_FP32) NS_TRY(run_emulator_simt<float>(p, ws, grid_rows, st, model_head(p, ws->table)));
+    else NS_TRY(run_emulator_bf16(p, ws, grid_rows, st, probe, nullptr));
     const float* tab = (const float*)ws->table;
     if (coarse) {
         dim3 g((sp.n_z * sp.n_k + 255) / 256, grid_rows);

@@ -90,6 +90,18 @@ struct ns_problem {
     double c0 = 0.0;
     double* d_LinvT64 = nullptr;     // D x D: LinvT[b*D + a] = (L^-1)[a][b]
     float* d_LinvT32 = nullptr;
+    bool has_lik = true;             // false for a model-only problem (no data / covariance)
+    // activations (per hidden layer l < n_layers - 1, compute dtype; FP32 for BF16)
+    int act = 0;
+    std::vector<void*> d_act_g, d_act_beta;
+    void* d_out_sig = nullptr;       // per-output scales (compute dtype) or null: scalar out_sigma
+    // CMB
+    int cmb_solve = 0;
+    void* d_Wfold = nullptr;         // D x H: W' = L^-1 diag(sigma) W_out (compute dtype)
+    void* d_cfold = nullptr;         // D: c' = L^-1 (d - mu - sigma b_out)
+    void* d_zeroD = nullptr;         // D zeros: bias of the folded head
+    double* d_lit_mu = nullptr;      // LITERAL: d - mu
+    double* d_lit_sig = nullptr;     // LITERAL: -sigma
     std::vector<void*> owned;
     gpuns::Workspace ws;             // scratch of loglike_batch / ns_model_batch
 };
@@ -158,11 +170,22 @@ int launch_free_to_full_ext(const ns_problem* p, const double* theta, int B, dou
 
 // BF16 tcgen05 GEMM: C[M x N] = epi(A[M x K] * W[N x K]^T + bias), M = *d_nrows.
 // epi 0: tanh -> bf16 C (ldc = N); epi 1: mu + sigma * v -> fp32 C.
+// Epilogues of the tensor-core GEMM: hidden tanh -> bf16; output
+// mu + sigma (acc + b) -> FP32; hidden sigmoid-linear -> bf16 with per-unit
+// g (passed as out_mu) and beta (act_beta).
+enum { TC_EPI_TANH = 0, TC_EPI_OUT = 1, TC_EPI_SIGLIN = 2 };
 int launch_gemm_tc(const CUtensorMap* tmA, const CUtensorMap* tmB, int tile_n,
                    const float* bias, const float* out_mu, float out_sigma,
                    void* C, const int* d_nrows, int grid_rows, int N, int K, int epi,
-                   int* d_err, cudaStream_t st);
+                   const float* act_beta, int* d_err, cudaStream_t st);
 int make_tensor_map_bf16(CUtensorMap* tm, const void* base, int rows, int K, int box_rows);
+// Dense FP64 set-up kernels (dense_linalg.cu): C (device, overwritten by L) ->
+// L^-1 (new device buffer) and sum ln L_aa; NS_EINVAL if C is not SPD.
+int device_cholesky_inverse(double* dC, int D, double** Xout, double* sum_log_diag, cudaStream_t st);
+int device_transpose(const double* dA, double* dT, int D, cudaStream_t st);
+// C = A W^T on the device in FP64 (likelihood.cu); nrows_dev holds M; zeros_n: N zeros.
+int gemm_f64_plain(const double* A, const double* W, double* C, const int* nrows_dev, int M, int N, int K,
+                   const double* zeros_n, cudaStream_t st);
 int gemm_tc_supported(int N, int K);
 
 }  // namespace gpuns

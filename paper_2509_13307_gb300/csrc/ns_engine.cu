@@ -656,7 +656,7 @@ static void run_release(ns_run* r) {
 }
 
 extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, ns_run** out) {
-    if (!p || !cfg || !out) return NS_EINVAL;
+    if (!p || !cfg || !out || !p->has_lik) return NS_EINVAL;
     *out = nullptr;
     const int n = cfg->n_live, k = cfg->n_delete, d = p->d;
     if (n < 2 || n > 4096 || k < 1 || k >= n || d < 1 || d > 64) return NS_EINVAL;

@@ -108,8 +108,37 @@ int workspace_create(const ns_problem* p, int cap, Workspace* ws) {
     ws->theta_full = (double*)v;
     NS_TRY(dalloc(sizeof(double) * (size_t)cap, &v, ws->owned));
     ws->logL = (double*)v;
-    if (p->kind != NS_KIND_SHEAR) return NS_OK;
+    if (p->kind == NS_KIND_GAUSS) return NS_OK;
     const int elt = (p->precision == NS_PREC_FP64) ? 8 : (p->precision == NS_PREC_FP32 ? 4 : 2);
+    if (p->kind == NS_KIND_CMB) {
+        const int tab_elt = (p->precision == NS_PREC_FP64) ? 8 : 4;
+        const int rows_pad = ((cap + 127) / 128) * 128;
+        for (int i = 0; i < 2; ++i) {
+            NS_TRY(dalloc((size_t)elt * rows_pad * p->hidden_max, &v, ws->owned));
+            ws->act[i] = v;
+            NS_CUDA_TRY(cudaMemset(v, 0, (size_t)elt * rows_pad * p->hidden_max));
+        }
+        NS_TRY(dalloc((size_t)tab_elt * cap * p->D, &v, ws->owned));
+        ws->table = v;
+        if (p->cmb_solve == NS_SOLVE_LITERAL) {
+            NS_TRY(dalloc(sizeof(double) * (size_t)cap * p->D, &v, ws->owned));
+            ws->resid = v;
+            NS_TRY(dalloc(sizeof(double) * (size_t)cap * ((p->D + 63) / 64), &v, ws->owned));
+            ws->chi2_part = v;
+            NS_TRY(dalloc(sizeof(int) * (size_t)((cap + 15) / 16), &v, ws->owned));
+            ws->chi2_done = (int*)v;
+            NS_CUDA_TRY(cudaMemset(v, 0, sizeof(int) * (size_t)((cap + 15) / 16)));
+        }
+        if (p->precision == NS_PREC_BF16) {
+            ws->tmA.resize(p->n_layers);
+            int cur = 0;
+            for (int l = 1; l + 1 < p->n_layers; ++l) {
+                NS_TRY(make_tensor_map_bf16(&ws->tmA[l], ws->act[cur], rows_pad, p->dims[l], 128));
+                cur ^= 1;
+            }
+        }
+        return NS_OK;
+    }
     const int tab_elt = (p->precision == NS_PREC_FP64) ? 8 : 4;
     const int rows_pad = ((cap + 127) / 128) * 128;
     for (int i = 0; i < 2; ++i) {
@@ -165,6 +194,121 @@ void workspace_free(Workspace* ws) {
     ws->side = nullptr;
 }
 
+// Upload a host FP64 vector in the problem's compute dtype (FP64, else FP32).
+static int upload_compute(const ns_problem* p, const double* h, size_t n, void** out, std::vector<void*>& owned) {
+    if (p->precision == NS_PREC_FP64) {
+        double* v;
+        NS_TRY(upload(h, n, &v, owned));
+        *out = v;
+    } else {
+        std::vector<float> f(h, h + n);
+        float* v;
+        NS_TRY(upload(f.data(), n, &v, owned));
+        *out = v;
+    }
+    return NS_OK;
+}
+
+// CMB set-up: FP64 factorisation of the covariance (host for D <= 256, else
+// blocked kernels on the device), the constant c0, and either L^-T for the
+// literal per-evaluation whitening or the fold of the linear head:
+// W' = L^-1 diag(sigma) W_out, c' = L^-1 (d - mu - sigma b_out).
+static int cmb_setup(ns_problem* p, const ns_problem_desc* desc) {
+    p->cmb_solve = desc->cmb.solve;
+    if (!p->has_lik) return NS_OK;
+    const ns_emulator_desc& e = desc->emu;
+    const int L = e.n_layers, D = p->D, H = e.dims[L - 1];
+    const double* Wout = e.W[L - 1];
+    const double* bout = e.b[L - 1];
+    std::vector<double> sig(D), v(D);
+    for (int a = 0; a < D; ++a) {
+        sig[a] = e.out_sigma_vec ? e.out_sigma_vec[a] : e.out_sigma;
+        v[a] = desc->data[a] - e.out_mu[a] - sig[a] * bout[a];
+    }
+    const bool literal = p->cmb_solve == NS_SOLVE_LITERAL;
+    if (literal) {
+        std::vector<double> lm(D), ls(D);
+        for (int a = 0; a < D; ++a) { lm[a] = desc->data[a] - e.out_mu[a]; ls[a] = -sig[a]; }
+        NS_TRY(upload(lm.data(), D, &p->d_lit_mu, p->owned));
+        NS_TRY(upload(ls.data(), D, &p->d_lit_sig, p->owned));
+    }
+    std::vector<double> zeros(std::max(D, H), 0.0);
+    NS_TRY(upload_compute(p, zeros.data(), D, &p->d_zeroD, p->owned));
+    std::vector<double> Wf((size_t)D * H), cf(D);
+    if (D <= 256) {
+        std::vector<double> Lh, Linv;
+        if (!cholesky_inverse(desc->cov, D, Lh, Linv)) return NS_EINVAL;
+        double c0 = -0.5 * D * std::log(2.0 * M_PI);
+        for (int a = 0; a < D; ++a) c0 -= std::log(Lh[(size_t)a * D + a]);
+        p->c0 = c0;
+        if (literal) {
+            std::vector<double> LT((size_t)D * D);
+            for (int a = 0; a < D; ++a)
+                for (int b = 0; b < D; ++b) LT[(size_t)b * D + a] = Linv[(size_t)a * D + b];
+            return upload(LT.data(), LT.size(), &p->d_LinvT64, p->owned);
+        }
+        for (int a = 0; a < D; ++a) {
+            double c = 0.0;
+            for (int b = 0; b <= a; ++b) c += Linv[(size_t)a * D + b] * v[b];
+            cf[a] = c;
+            for (int h = 0; h < H; ++h) {
+                double w = 0.0;
+                for (int b = 0; b <= a; ++b) w += Linv[(size_t)a * D + b] * sig[b] * Wout[(size_t)b * H + h];
+                Wf[(size_t)a * H + h] = w;
+            }
+        }
+    } else {
+        cudaStream_t st = nullptr;
+        double* dC = nullptr;
+        double* X = nullptr;
+        std::vector<void*> tmp;
+        auto done = [&](int code) {
+            for (void* q : tmp) cudaFree(q);
+            cudaFree(dC);
+            cudaFree(X);
+            return code;
+        };
+        if (upload(desc->cov, (size_t)D * D, &dC, tmp)) return done(NS_ENOMEM);
+        tmp.clear();
+        double sum_log = 0.0;
+        int s = device_cholesky_inverse(dC, D, &X, &sum_log, st);
+        if (s) return done(s);
+        p->c0 = -0.5 * D * std::log(2.0 * M_PI) - sum_log;
+        if (literal) {
+            double* LT = nullptr;
+            if (cudaMalloc(&LT, sizeof(double) * (size_t)D * D) != cudaSuccess) return done(NS_ENOMEM);
+            p->owned.push_back(LT);
+            if ((s = device_transpose(X, LT, D, st))) return done(s);
+            if (cudaStreamSynchronize(st) != cudaSuccess) return done(NS_ECUDA);
+            p->d_LinvT64 = LT;
+            return done(NS_OK);
+        }
+        // W' = X (sigma W_out) and c' = X v as FP64 GEMMs on the device
+        std::vector<double> Wt((size_t)H * D);
+        for (int b = 0; b < D; ++b)
+            for (int h = 0; h < H; ++h) Wt[(size_t)h * D + b] = sig[b] * Wout[(size_t)b * H + h];
+        double *dWt, *dv, *dz, *dWf, *dcf;
+        int* dn;
+        if (upload(Wt.data(), Wt.size(), &dWt, tmp) || upload(v.data(), D, &dv, tmp) ||
+            upload(zeros.data(), zeros.size(), &dz, tmp) || upload(&D, 1, &dn, tmp))
+            return done(NS_ENOMEM);
+        if (cudaMalloc(&dWf, sizeof(double) * (size_t)D * H) != cudaSuccess) return done(NS_ENOMEM);
+        tmp.push_back(dWf);
+        if (cudaMalloc(&dcf, sizeof(double) * (size_t)D) != cudaSuccess) return done(NS_ENOMEM);
+        tmp.push_back(dcf);
+        if ((s = gemm_f64_plain(X, dWt, dWf, dn, D, H, D, dz, st))) return done(s);
+        if ((s = gemm_f64_plain(X, dv, dcf, dn, D, 1, D, dz, st))) return done(s);
+        if (cudaMemcpyAsync(Wf.data(), dWf, sizeof(double) * Wf.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(cf.data(), dcf, sizeof(double) * D, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return done(NS_ECUDA);
+        done(NS_OK);
+    }
+    NS_TRY(upload_compute(p, Wf.data(), Wf.size(), &p->d_Wfold, p->owned));
+    NS_TRY(upload_compute(p, cf.data(), cf.size(), &p->d_cfold, p->owned));
+    return NS_OK;
+}
+
 static int validate_desc(const ns_problem_desc* d) {
     if (!d || !d->priors || d->n_params < 1 || d->n_params > 256 || d->max_batch < 1) return NS_EINVAL;
     if (d->precision < 0 || d->precision > NS_PREC_BF16_F64CHI2) return NS_EINVAL;
@@ -179,18 +323,31 @@ static int validate_desc(const ns_problem_desc* d) {
     }
     if (nfree < 1 || nfree > 64) return NS_EINVAL;
     if (d->kind == NS_KIND_GAUSS) return (d->gauss.sigma > 0) ? NS_OK : NS_EINVAL;
-    if (d->kind != NS_KIND_SHEAR) return NS_EINVAL;
-    const ns_shear_desc& s = d->shear;
+    if (d->kind != NS_KIND_SHEAR && d->kind != NS_KIND_CMB) return NS_EINVAL;
     const ns_emulator_desc& e = d->emu;
+    if (e.n_layers < 2 || !e.dims || !e.W || !e.b || !e.inputs || !e.in_center || !e.in_scale || !e.out_mu)
+        return NS_EINVAL;
+    if (e.activation != NS_ACT_TANH && e.activation != NS_ACT_SIGMOID_LINEAR) return NS_EINVAL;
+    if (e.activation == NS_ACT_SIGMOID_LINEAR && (!e.act_g || !e.act_beta)) return NS_EINVAL;
+    if ((d->data == nullptr) != (d->cov == nullptr)) return NS_EINVAL;
+    if (d->kind == NS_KIND_CMB) {
+        if (e.dims[0] < 1 || e.dims[0] > 32) return NS_EINVAL;
+        if (d->n_data != e.dims[e.n_layers] || d->n_data < 1) return NS_EINVAL;
+        for (int j = 0; j < e.dims[0]; ++j)
+            if (e.inputs[j] < 0 || e.inputs[j] >= d->n_params || !(e.in_scale[j] != 0)) return NS_EINVAL;
+        if (d->cmb.solve != NS_SOLVE_FOLD && d->cmb.solve != NS_SOLVE_LITERAL) return NS_EINVAL;
+        if (d->cmb.solve == NS_SOLVE_LITERAL && d->precision != NS_PREC_FP64) return NS_ENOTSUP;
+        if (d->precision == NS_PREC_BF16_F64CHI2) return NS_ENOTSUP;
+        return NS_OK;
+    }
+    const ns_shear_desc& s = d->shear;
     if (s.n_bins < 1 || s.n_bins > 5 || s.n_ell < 1 || s.n_k < 4 || s.n_z < 4 || s.n_chi < 3 || !(s.a_min > 0 && s.a_min < 1))
         return NS_EINVAL;
     if (s.n_z_emu < 4 || s.n_z_emu > s.n_z) return NS_EINVAL;
     if (d->n_params != 11 + 2 * s.n_bins + s.n_tmpl) return NS_EINVAL;
     const int D = s.n_bins * (s.n_bins + 1) / 2 * s.n_ell;
-    if (d->n_data != D || !d->data || !d->cov) return NS_EINVAL;
+    if (d->n_data != D) return NS_EINVAL;
     if (s.n_tmpl > 0 && !s.tmpl) return NS_EINVAL;
-    if (e.n_layers < 2 || !e.dims || !e.W || !e.b || !e.inputs || !e.in_center || !e.in_scale || !e.out_mu)
-        return NS_EINVAL;
     if (e.dims[0] < 1 || e.dims[0] > 32) return NS_EINVAL;
     if (e.dims[e.n_layers] != s.n_k * s.n_z_emu) return NS_EINVAL;
     for (int j = 0; j < e.dims[0]; ++j)
@@ -258,10 +415,14 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
     p->dims.assign(e.dims, e.dims + e.n_layers + 1);
     p->hidden_max = 0;
     for (int l = 1; l < e.n_layers; ++l) p->hidden_max = std::max(p->hidden_max, p->dims[l]);
+    const bool cmb = p->kind == NS_KIND_CMB;
+    // BF16 layers on tensor cores: every layer >= 1 for shear; the hidden
+    // layers only for CMB (its head runs on CUDA cores in FP32)
+    auto tc_layer = [&](int l) { return bf16 && l >= 1 && !(cmb && l == e.n_layers - 1); };
     if (bf16) {
         for (int l = 1; l < e.n_layers; ++l)
-            if (!gemm_tc_supported(p->dims[l + 1], p->dims[l]) && !(l == e.n_layers - 1 && p->dims[l + 1] % 4 == 0 &&
-                                                                   p->dims[l] % 8 == 0))
+            if (tc_layer(l) && !gemm_tc_supported(p->dims[l + 1], p->dims[l]) &&
+                !(l == e.n_layers - 1 && p->dims[l + 1] % 4 == 0 && p->dims[l] % 8 == 0))
                 return fail(NS_ENOTSUP);
     }
     p->d_W.assign(e.n_layers, nullptr);
@@ -281,7 +442,7 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
             float* b;
             if ((s = upload(bf.data(), nb, &b, p->owned))) return fail(s);
             p->d_b[l] = b;
-            if (bf16 && l >= 1) {
+            if (tc_layer(l)) {
                 std::vector<uint16_t> wb(nw);
                 for (size_t i = 0; i < nw; ++i) wb[i] = f32_to_bf16_rne((float)e.W[l][i]);
                 uint16_t* w;
@@ -314,11 +475,48 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
             p->d_out_mu = m;
         }
         p->out_sigma = e.out_sigma;
+        if (e.out_sigma_vec) {
+            if (f64) {
+                double* v;
+                if ((s = upload(e.out_sigma_vec, no, &v, p->owned))) return fail(s);
+                p->d_out_sig = v;
+            } else {
+                std::vector<float> vf(no);
+                for (size_t i = 0; i < no; ++i) vf[i] = (float)e.out_sigma_vec[i];
+                float* v;
+                if ((s = upload(vf.data(), no, &v, p->owned))) return fail(s);
+                p->d_out_sig = v;
+            }
+        }
+        p->act = e.activation;
+        if (p->act == NS_ACT_SIGMOID_LINEAR) {
+            p->d_act_g.assign(e.n_layers - 1, nullptr);
+            p->d_act_beta.assign(e.n_layers - 1, nullptr);
+            for (int l = 0; l + 1 < e.n_layers; ++l) {
+                const size_t n = p->dims[l + 1];
+                for (int w = 0; w < 2; ++w) {
+                    const double* src = w ? e.act_beta[l] : e.act_g[l];
+                    void* dst = nullptr;
+                    if (f64) {
+                        double* v;
+                        if ((s = upload(src, n, &v, p->owned))) return fail(s);
+                        dst = v;
+                    } else {
+                        std::vector<float> vf(src, src + n);
+                        float* v;
+                        if ((s = upload(vf.data(), n, &v, p->owned))) return fail(s);
+                        dst = v;
+                    }
+                    (w ? p->d_act_beta[l] : p->d_act_g[l]) = dst;
+                }
+            }
+        }
     }
     if (bf16) {
         p->tmB.resize(e.n_layers);
         p->tile_n.assign(e.n_layers, 128);
         for (int l = 1; l < e.n_layers; ++l) {
+            if (!tc_layer(l)) continue;
             const int N = p->dims[l + 1];
             const bool last = (l == e.n_layers - 1);
             // hidden layers have few M tiles (rows = active chains): narrow N
@@ -329,6 +527,16 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
             int s = make_tensor_map_bf16(&p->tmB[l], p->d_W[l], N, p->dims[l], tn);
             if (s) return fail(s);
         }
+    }
+
+    p->D = desc->n_data;
+    p->has_lik = desc->cov != nullptr;
+    if (cmb) {
+        int s = cmb_setup(p, desc);
+        if (!s) s = workspace_create(p, p->max_batch, &p->ws);
+        if (s) return fail(s);
+        *out = p;
+        return NS_OK;
     }
 
     // ---------------- shear grids and constants
@@ -379,7 +587,7 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
             (s = upload(lnell.data(), sd.n_ell, &dlnell, p->owned)) ||
             (s = upload(sd.nz_mean, sd.n_bins, &dmu, p->owned)) || (s = upload(sd.nz_sigma, sd.n_bins, &dsg, p->owned)) ||
             (s = upload(pi.data(), pi.size(), &dpi, p->owned)) || (s = upload(pj.data(), pj.size(), &dpj, p->owned)) ||
-            (s = upload(desc->data, sp.D, &ddata, p->owned)))
+            (s = upload(desc->data ? desc->data : std::vector<double>(sp.D, 0.0).data(), sp.D, &ddata, p->owned)))
             return fail(s);
         if (sd.n_tmpl > 0 && (s = upload(sd.tmpl, (size_t)sp.D * sd.n_tmpl, &dtm, p->owned))) return fail(s);
         sp.a = da_; sp.lna = dlna; sp.z = dz_; sp.wa = dwa; sp.zw = dzw; sp.zrow = dzrow; sp.lnell = dlnell;
@@ -426,7 +634,7 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
         }
     }
     // ---------------- Gaussian likelihood: FP64 Cholesky, L^-1, constant
-    {
+    if (p->has_lik) {
         const int D = sp.D;
         std::vector<double> L, Linv;
         if (!cholesky_inverse(desc->cov, D, L, Linv)) return fail(NS_EINVAL);
@@ -484,7 +692,7 @@ static int batch_common(const ns_problem* p, const double* theta_dev, int B, cud
 }
 
 extern "C" int loglike_batch(const ns_problem* p, const double* theta_dev, int B, double* logL_dev, void* stream) {
-    if (!p || B < 0 || B > p->max_batch || (B > 0 && (!theta_dev || !logL_dev))) return NS_EINVAL;
+    if (!p || !p->has_lik || B < 0 || B > p->max_batch || (B > 0 && (!theta_dev || !logL_dev))) return NS_EINVAL;
     if (B == 0) return NS_OK;
     cudaStream_t st = (cudaStream_t)stream;
     NS_TRY(batch_common(p, theta_dev, B, st));
@@ -492,7 +700,7 @@ extern "C" int loglike_batch(const ns_problem* p, const double* theta_dev, int B
 }
 
 extern "C" int ns_model_batch(const ns_problem* p, const double* theta_dev, int B, double* model_dev, void* stream) {
-    if (!p || p->kind != NS_KIND_SHEAR || B < 0 || B > p->max_batch || (B > 0 && (!theta_dev || !model_dev)))
+    if (!p || p->kind == NS_KIND_GAUSS || B < 0 || B > p->max_batch || (B > 0 && (!theta_dev || !model_dev)))
         return NS_EINVAL;
     if (B == 0) return NS_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -510,7 +718,7 @@ extern "C" int ns_problem_status(ns_problem* p, int* bits, int clear) {
 
 extern "C" int ns_emulator_batch(const ns_problem* p, const double* theta_dev, int B, double* out_dev,
                                  void* stream) {
-    if (!p || p->kind != NS_KIND_SHEAR || B < 0 || B > p->max_batch || (B > 0 && (!theta_dev || !out_dev)))
+    if (!p || p->kind == NS_KIND_GAUSS || B < 0 || B > p->max_batch || (B > 0 && (!theta_dev || !out_dev)))
         return NS_EINVAL;
     if (B == 0) return NS_OK;
     cudaStream_t st = (cudaStream_t)stream;

@@ -94,3 +94,10 @@ def test_wishart_base_spectrum():
     r = math.sqrt(D / nu)
     assert e.min() > 0.8 * (1 - r) ** 2 and e.max() < 1.15 * (1 + r) ** 2
     assert np.mean(np.diag(W)) == pytest.approx(1.0, abs=0.02)
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    x = np.random.default_rng(8).standard_normal(4096) * 10.0 ** np.random.default_rng(9).uniform(-3, 3, 4096)
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(CMBOracle.to_bf16(x), ref)
