@@ -173,6 +173,7 @@ def main():
     ap.add_argument("--no-full-run", action="store_true", help="skip the time-to-converged-logZ run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-multi", action="store_true", help="skip the packed-runs measurement")
+    ap.add_argument("--no-cmb", action="store_true", help="skip the CMB (D = 7521) measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -387,6 +388,45 @@ def ours(args):
         extra.update(time_to_logZ_s=t1 - t0, logZ=ev["logZ"], logZ_err=ev["logZ_err"], logZ_iters=st.iterations,
                      logZ_evals=st.evaluations, logZ_converged=st.converged)
         run.close()
+
+    # ---------------- the 6-parameter CMB configuration (D = 7521, dense
+    # covariance, whitening fold, FP32 emulator): NS evaluations/s and the wall
+    # time to a converged log Z
+    if not args.no_cmb:
+        try:
+            ccfg = w.cmb6()
+            cinp = w.make_cmb_inputs(ccfg)
+            csc = replace_seed(ccfg.sampler, rank)
+            t_setup = time.time()
+            pc = Problem(cinp, "fp32", max_batch=csc.n_live)
+            torch.cuda.synchronize()
+            t_setup = time.time() - t_setup
+            crun = NestedRun.from_config(pc, csc)
+            crun.step(1)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            s0 = crun.step(0)
+            e0.record(stream)
+            s1 = crun.step(3)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            extra["cmb_evals_per_s"] = (s1.evaluations - s0.evaluations) / (e0.elapsed_time(e1) / 1e3)
+            crun.close()
+            t0 = time.time()
+            crun = NestedRun.from_config(pc, csc)
+            cst = crun.run(max_iters=5000)
+            cev = crun.evidence()
+            extra.update(cmb_time_to_logZ_s=time.time() - t0, cmb_logZ=cev["logZ"], cmb_logZ_err=cev["logZ_err"],
+                         cmb_iters=cst.iterations, cmb_evals=cst.evaluations, cmb_converged=cst.converged,
+                         cmb_setup_s=t_setup,
+                         cmb_workload="cmb6: 6-parameter LCDM CMB-like, emulator 6->4x512->3x2507 sigmoid-linear "
+                                      "(FP32), dense 7521 x 7521 Wishart-style covariance, whitening fold, "
+                                      "n_live = 500, k = 250")
+            crun.close()
+            pc.close()
+        except Exception as exc:
+            extra["cmb_error"] = repr(exc)[:200]
 
     # ---------------- end to end through the public API with host buffers
     B = sc.n_delete
