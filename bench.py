@@ -153,6 +153,21 @@ def windows_flops_per_eval(cfg) -> float:
     return (N - 1) * 48 + N * 12 + N * cfg.n_bins * 25
 
 
+def job_totals(t_local: float, ev_local, world: int, device):
+    """Whole-job totals over the ranks of one node: the timed region is the
+    slowest rank's (max) and the evaluations are every rank's (sum); each rank
+    runs an independent sampler (weak scaling, no data-path collective)."""
+    if world == 1:
+        return t_local, float(ev_local)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    e = torch.tensor([float(ev_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return t.item(), e.item()
+
+
 def replace_seed(sc, rank):
     from dataclasses import replace
     return replace(sc, seed=sc.seed + 100 * rank)
@@ -277,19 +292,9 @@ def ours(args):
     res = timed_steps(prob, args.warmup, args.steps, profile="projection")
     clk = clocks.stop()
 
-    t_local = res["ms"] / 1e3
-    ev_local = res["evals"]
-    if world > 1:
-        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        e = torch.tensor([float(ev_local)], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        t_job, ev_job = t.item(), e.item()
-    else:
-        t_job, ev_job = t_local, float(ev_local)
+    t_job, ev_job = job_totals(res["ms"] / 1e3, res["evals"], world, dev)
     value = ev_job / t_job
 
-    # kernels launched per round: slice state machine, prior transform, emulator input
     # per round: slice, prior transform, windows, emulator input layer, one
     # GEMM per further layer, Limber, whitening; per iteration 6 more (sort and
     # delete, covariance, Cholesky, directions, chain starts, insert).
