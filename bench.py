@@ -189,10 +189,53 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-multi", action="store_true", help="skip the packed-runs measurement")
     ap.add_argument("--no-cmb", action="store_true", help="skip the CMB (D = 7521) measurement")
+    ap.add_argument("--profile", choices=["loglike", "round", "cmb"], default=None,
+                    help="run a short fixed workload for a profiler and exit (no timing line): "
+                         "'loglike' = 4 loglike_batch calls of --batch rows on the 39-d shear problem, "
+                         "'round' = two warm NS iterations then one more inside an NVTX range 'prof', "
+                         "'cmb' = 4 loglike_batch calls on the D = 7521 CMB problem")
+    ap.add_argument("--batch", type=int, default=500)
     args = ap.parse_args()
+    if args.profile:
+        return profile_workload(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours(args)
+
+
+def profile_workload(args):
+    """Short fixed workloads to run under ncu (the launch list and single-kernel
+    captures of profiles/); prints nothing but a completion line."""
+    import numpy as np
+    import torch
+    from paper_2509_13307_gb300.build import build
+    build()
+    import workloads as w
+    from paper_2509_13307_gb300 import Problem, NestedRun
+    if args.profile == "cmb":
+        inp = w.make_cmb_inputs(w.cmb6())
+        prob = Problem(inp, args.precision if args.precision != "bf16" else "fp32", max_batch=args.batch)
+    else:
+        inp = w.make_shear_inputs(w.shear39())
+        prob = Problem(inp, args.precision, max_batch=max(args.batch, 1000))
+    if args.profile == "round":
+        sc = w.shear39().sampler
+        run = NestedRun.from_config(prob, sc)
+        run.step(2)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("prof")
+        run.step(1)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+    else:
+        free = [i for i, p in enumerate(inp["priors"]) if p[0] != "F"]
+        cube = torch.tensor(np.random.default_rng(9).uniform(0.02, 0.98, (args.batch, len(free))), device="cuda")
+        th = prob.prior_transform(cube)
+        for _ in range(4):
+            prob.loglike(th)
+        torch.cuda.synchronize()
+    print(f"profile workload {args.profile} done", flush=True)
+    return 0
 
 
 def reference_arm(args):
