@@ -3,8 +3,9 @@
 // Per iteration:
 //   k_sort_delete   sort live log L by (log L, slot) (bitonic, one block), delete
 //                   the k lowest, L* = the k-th, append them to the dead list
-//                   and update log Z / log X / H in FP64 as k sequential
-//                   deletions with n, n-1, ..., n-k+1 live points (Sec. 2.2).
+//                   and update log Z / log X / H in FP64 for k deletions
+//                   with n, n-1, ..., n-k+1 live points (Sec. 2.2): log X by
+//                   sequential subtraction, Z and H by fixed-order reductions.
 //   k_live_cov      covariance (ddof 1) of all n live cube points + ridge.
 //   k_cholesky      FP64 Cholesky of that covariance (one block).
 //   k_directions    every (chain, move) slice direction of the iteration.
@@ -81,19 +82,89 @@ __device__ inline double lse2(double a, double b) {
     return m + log(exp(a - m) + exp(b - m));
 }
 
-// Skilling's incremental update for one deletion with nl live points.
-__device__ inline void evidence_add(double& logZ, double& logX, double& H, double L, int nl) {
-    const double logw = logX + log(-expm1(-1.0 / nl));
-    const double z_new = lse2(logZ, L + logw);
-    double h = 0.0;
-    if (z_new != -INFINITY) {
-        h = (L > -INFINITY) ? exp(logw + L - z_new) * L : 0.0;
-        if (logZ > -INFINITY) h += exp(logZ - z_new) * (H + logZ);
-        h -= z_new;
+// Block-wide fixed-order reductions over per-thread partials (1024 threads max).
+__device__ double block_reduce_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = red[0];
+        for (int i = 1; i < nw; ++i) m = fmax(m, red[i]);
+        red[32] = m;
     }
-    H = h;
+    __syncthreads();
+    return red[32];
+}
+__device__ double block_reduce_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = red[0];
+        for (int i = 1; i < nw; ++i) s += red[i];
+        red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// k deletions at once, the j-th booked with n_first - j live points (Sec. 2.2),
+// keys L[0..k) ascending in shared memory, tmp: k doubles of shared scratch.
+// log X advances by sequential subtraction of 1/n_j (the same operations as one
+// deletion at a time); the weights w_j = X_{j-1} - X_j and the updates
+//   Z' = Z + sum_j w_j e^{L_j},   Z' (H' + ln Z') = Z (H + ln Z) + sum_j w_j e^{L_j} L_j
+// (Skilling's evidence and information) are fixed-order block reductions.
+// Called by every thread of the block; results valid in every thread.
+__device__ void evidence_batch(const double* L, double* tmp, int k, int n_first, double& logZ, double& logX,
+                               double& H, double* red) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int j = tid; j < k; j += nt) tmp[j] = 1.0 / (double)(n_first - j);
+    __syncthreads();
+    if (tid == 0) {
+        double lx = logX;
+        for (int j = 0; j < k; ++j) {
+            const double inv = tmp[j];
+            tmp[j] = lx;              // ln X before the j-th deletion
+            lx -= inv;
+        }
+        red[33] = lx;
+    }
+    __syncthreads();
+    const double logX_new = red[33];
+    double mloc = -INFINITY;
+    for (int j = tid; j < k; j += nt) {
+        const double logw = tmp[j] + log(-expm1(-1.0 / (double)(n_first - j)));
+        const double c = L[j] + logw;
+        tmp[j] = c;
+        mloc = fmax(mloc, c);
+    }
+    const double m = fmax(block_reduce_max(mloc, red), logZ);
+    double z_new = -INFINITY;
+    if (m > -INFINITY) {
+        double sl = 0.0;
+        for (int j = tid; j < k; j += nt) sl += exp(tmp[j] - m);
+        const double s = block_reduce_sum(sl, red) + ((logZ > -INFINITY) ? exp(logZ - m) : 0.0);
+        z_new = m + log(s);
+    } else {
+        __syncthreads();
+    }
+    double h_new = 0.0;
+    if (z_new > -INFINITY) {
+        double hl = 0.0;
+        for (int j = tid; j < k; j += nt)
+            if (L[j] > -INFINITY) hl += exp(tmp[j] - z_new) * L[j];
+        double hs = block_reduce_sum(hl, red);
+        if (logZ > -INFINITY) hs += exp(logZ - z_new) * (H + logZ);
+        h_new = hs - z_new;
+    }
+    __syncthreads();
     logZ = z_new;
-    logX -= 1.0 / nl;
+    logX = logX_new;
+    H = h_new;
 }
 
 // ------------------------------------------------------------------ init
@@ -174,9 +245,12 @@ __global__ void __launch_bounds__(1024) k_sort_delete(RunDev r, int n_pad, int d
         const int j = t / r.d, c = t % r.d;
         r.dead_x[(base + j) * r.d + c] = r.live_x[(size_t)idx[j] * r.d + c];
     }
+    __shared__ double red[34];
+    double* tmp = reinterpret_cast<double*>(idx + n_pad);
+    double logZ = r.sc->logZ, logX = r.sc->logX, H = r.sc->H;
+    __syncthreads();
+    evidence_batch(key, tmp, k, r.n, logZ, logX, H, red);
     if (tid == 0) {
-        double logZ = r.sc->logZ, logX = r.sc->logX, H = r.sc->H;
-        for (int j = 0; j < k; ++j) evidence_add(logZ, logX, H, key[j], r.n - j);
         r.sc->logZ = logZ; r.sc->logX = logX; r.sc->H = H;
         r.sc->lstar = key[k - 1];
         r.sc->n_dead = base + k;
@@ -487,11 +561,17 @@ __global__ void k_insert(RunDev r) {
 }
 
 // ------------------------------------------------------------------ evidence
-__global__ void k_final_evidence(RunDev r, double* out /* logZ, logX, H */) {
-    if (threadIdx.x != 0) return;
+// The live points added at the end in ascending order with n, n-1, ..., 1 live points.
+__global__ void __launch_bounds__(1024) k_final_evidence(RunDev r, double* out /* logZ, logX, H */) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* L = reinterpret_cast<double*>(smem_raw);
+    double* tmp = L + r.n;
+    __shared__ double red[34];
+    for (int j = threadIdx.x; j < r.n; j += blockDim.x) L[j] = r.live_L[r.order[j]];
     double logZ = r.sc->logZ, logX = r.sc->logX, H = r.sc->H;
-    for (int j = 0; j < r.n; ++j) evidence_add(logZ, logX, H, r.live_L[r.order[j]], r.n - j);
-    out[0] = logZ; out[1] = logX; out[2] = H;
+    __syncthreads();
+    evidence_batch(L, tmp, r.n, r.n, logZ, logX, H, red);
+    if (threadIdx.x == 0) { out[0] = logZ; out[1] = logX; out[2] = H; }
 }
 
 // One block per replay: ln t_i = ln(U_{s,i}) / n_i; ln Z_s = LSE_i(L_i + ln X_{i-1} + ln(1 - t_i)).
@@ -626,7 +706,13 @@ static int launch_round(ns_run* r, cudaStream_t st, const StageProbe* probe) {
 static int build_graph(ns_run* r, int rounds) {
     if (r->graph) { cudaGraphExecDestroy(r->graph); r->graph = nullptr; }
     cudaGraph_t g;
-    if (!r->cap_st) NS_CUDA_TRY(cudaStreamCreateWithFlags(&r->cap_st, cudaStreamNonBlocking));
+    if (!r->cap_st) {
+        // the round's main chain at the highest priority, so the emulator GEMMs
+        // are scheduled ahead of the windows stage running beside them
+        int lo = 0, hi = 0;
+        NS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        NS_CUDA_TRY(cudaStreamCreateWithPriority(&r->cap_st, cudaStreamNonBlocking, hi));
+    }
     NS_CUDA_TRY(cudaStreamBeginCapture(r->cap_st, cudaStreamCaptureModeThreadLocal));
     int s = NS_OK;
     for (int i = 0; i < rounds && s == NS_OK; ++i)
@@ -634,7 +720,7 @@ static int build_graph(ns_run* r, int rounds) {
     cudaError_t e = cudaStreamEndCapture(r->cap_st, &g);
     if (s != NS_OK) { if (e == cudaSuccess) cudaGraphDestroy(g); return s; }
     NS_CUDA_TRY(e);
-    e = cudaGraphInstantiate(&r->graph, g, 0);
+    e = cudaGraphInstantiate(&r->graph, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     NS_CUDA_TRY(e);
     r->graph_rounds = rounds;
@@ -655,8 +741,19 @@ static void run_release(ns_run* r) {
     delete r;
 }
 
+static int engine_kernel_attributes() {
+    static bool done = false;
+    if (done) return NS_OK;
+    // live sets up to 4096 points: keys, slots and k weights in shared memory
+    NS_CUDA_TRY(cudaFuncSetAttribute(k_sort_delete, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    NS_CUDA_TRY(cudaFuncSetAttribute(k_final_evidence, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    done = true;
+    return NS_OK;
+}
+
 extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, ns_run** out) {
     if (!p || !cfg || !out || !p->has_lik) return NS_EINVAL;
+    NS_TRY(engine_kernel_attributes());
     *out = nullptr;
     const int n = cfg->n_live, k = cfg->n_delete, d = p->d;
     if (n < 2 || n > 4096 || k < 1 || k >= n || d < 1 || d > 64) return NS_EINVAL;
@@ -736,7 +833,7 @@ static int one_iteration(ns_run* r) {
     RunDev& rd = r->rd;
     cudaStream_t st = r->st;
     NS_TRY(grow_dead(r, r->h_sc->n_dead + r->k));
-    const size_t sm = (size_t)r->n_pad * (sizeof(double) + sizeof(int));
+    const size_t sm = (size_t)r->n_pad * (sizeof(double) + sizeof(int)) + sizeof(double) * r->k;
     k_sort_delete<<<1, 1024, sm, st>>>(rd, r->n_pad, r->k, 1);
     NS_CUDA_TRY(cudaGetLastError());
     k_live_cov<<<r->d, 256, 0, st>>>(rd, r->cfg.ridge);
@@ -801,7 +898,7 @@ extern "C" int ns_evidence(const ns_run* rc, int n_replays, double* logZ, double
     NS_CUDA_TRY(cudaGetLastError());
     double* dout;
     if (cudaMalloc(&dout, sizeof(double) * (3 + n_replays)) != cudaSuccess) return NS_ENOMEM;
-    k_final_evidence<<<1, 32, 0, st>>>(r->rd, dout);
+    k_final_evidence<<<1, 1024, 2 * sizeof(double) * r->n, st>>>(r->rd, dout);
     k_err_replays<<<n_replays, 256, 128 * sizeof(double), st>>>(r->rd, r->h_sc->n_dead, dout + 3);
     std::vector<double> h(3 + n_replays);
     cudaError_t e = cudaGetLastError();
@@ -979,7 +1076,11 @@ static int multi_launch_round(ns_multi* m, cudaStream_t st) {
 
 static int multi_build_graph(ns_multi* m, int rounds) {
     if (m->graph) { cudaGraphExecDestroy(m->graph); m->graph = nullptr; }
-    if (!m->cap_st) NS_CUDA_TRY(cudaStreamCreateWithFlags(&m->cap_st, cudaStreamNonBlocking));
+    if (!m->cap_st) {
+        int lo = 0, hi = 0;
+        NS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        NS_CUDA_TRY(cudaStreamCreateWithPriority(&m->cap_st, cudaStreamNonBlocking, hi));
+    }
     cudaGraph_t g;
     NS_CUDA_TRY(cudaStreamBeginCapture(m->cap_st, cudaStreamCaptureModeThreadLocal));
     int s = NS_OK;
@@ -987,7 +1088,7 @@ static int multi_build_graph(ns_multi* m, int rounds) {
     cudaError_t e = cudaStreamEndCapture(m->cap_st, &g);
     if (s != NS_OK) { if (e == cudaSuccess) cudaGraphDestroy(g); return s; }
     NS_CUDA_TRY(e);
-    e = cudaGraphInstantiate(&m->graph, g, 0);
+    e = cudaGraphInstantiate(&m->graph, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     NS_CUDA_TRY(e);
     m->graph_rounds = rounds;
@@ -1061,7 +1162,7 @@ extern "C" int ns_multi_init(const ns_problem* const* problems, int n_runs, cons
 static int multi_start_iteration(ns_multi* m, int i) {
     ns_run* r = m->runs[i];
     NS_TRY(grow_dead(r, r->h_sc->n_dead + r->k));
-    const size_t sm = (size_t)r->n_pad * (sizeof(double) + sizeof(int));
+    const size_t sm = (size_t)r->n_pad * (sizeof(double) + sizeof(int)) + sizeof(double) * r->k;
     k_sort_delete<<<1, 1024, sm, m->st>>>(r->rd, r->n_pad, r->k, 1);
     k_live_cov<<<r->d, 256, 0, m->st>>>(r->rd, r->cfg.ridge);
     k_cholesky<<<1, 128, 0, m->st>>>(r->rd);

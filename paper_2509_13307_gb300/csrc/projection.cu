@@ -673,8 +673,14 @@ k_whiten(const TR* __restrict__ resid, int D, const TA* __restrict__ LinvT, TA* 
     __threadfence();
     if (tid < kWR && row0 + tid < M) {
         const int r = row0 + tid;
+        // issue the tile loads together, then add in tile order
+        TA v[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) v[t] = (t < ntile) ? __ldcg(partial + (size_t)r * ntile + t) : TA(0);
         TA s2 = TA(0);
-        for (int t = 0; t < ntile; ++t) s2 += __ldcg(partial + (size_t)r * ntile + t);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) s2 += v[t];
+        for (int t = 16; t < ntile; ++t) s2 += __ldcg(partial + (size_t)r * ntile + t);
         logL[r] = c0 - 0.5 * (double)s2;
     }
     if (tid == 0) done[blockIdx.y] = 0;
