@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <utility>
 #include <math.h>
 
 #include "../../include/gpuns.h"
@@ -214,5 +215,33 @@ template <> __device__ inline double dlog<double>(double x) { return log(x); }
 template <> __device__ inline float dlog<float>(float x) { return logf(x); }
 
 __global__ void k_set_int(int* p, int v);
+
+// Programmatic dependent launch.  A kernel of the round chain first lets the
+// next grid in its stream begin launching (its CTAs then fill SMs as this
+// grid's CTAs retire) and then waits until its own predecessor has completed
+// and its memory is visible.  Nothing is read or written before the wait, so
+// the overlap covers launch latency and tails only.  Both are no-ops for a
+// grid launched without the attribute.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launch with the programmatic-stream-serialization attribute (see pdl_begin).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 }  // namespace gpuns

@@ -107,6 +107,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           void* __restrict__ Cout, const int* __restrict__ nrows, int N, int K, const float* __restrict__ act_beta,
           int* __restrict__ err) {
     using C = Cfg<BN>;
+    pdl_begin();
     const int M = *nrows;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     if (m0 >= M) return;
@@ -248,13 +249,9 @@ static int launch_bn(const CUtensorMap* tmA, const CUtensorMap* tmB, const float
         attr = true;
     }
     dim3 grid((N + BN - 1) / BN, (grid_rows + BM - 1) / BM);
-    if (epi == TC_EPI_TANH)
-        k_gemm_tc<BN, 0><<<grid, 128, C::SMEM, st>>>(*tmA, *tmB, bias, mu, sigma, Cout, nrows, N, K, beta, err);
-    else if (epi == TC_EPI_OUT)
-        k_gemm_tc<BN, 1><<<grid, 128, C::SMEM, st>>>(*tmA, *tmB, bias, mu, sigma, Cout, nrows, N, K, beta, err);
-    else
-        k_gemm_tc<BN, 2><<<grid, 128, C::SMEM, st>>>(*tmA, *tmB, bias, mu, sigma, Cout, nrows, N, K, beta, err);
-    NS_CUDA_TRY(cudaGetLastError());
+    auto kern = (epi == TC_EPI_TANH) ? k_gemm_tc<BN, 0> : (epi == TC_EPI_OUT) ? k_gemm_tc<BN, 1> : k_gemm_tc<BN, 2>;
+    NS_CUDA_TRY(launch_pdl(kern, grid, dim3(128), (size_t)C::SMEM, st, *tmA, *tmB, bias, mu, sigma, Cout, nrows, N,
+                           K, beta, err));
     return NS_OK;
 }
 

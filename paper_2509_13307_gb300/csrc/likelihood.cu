@@ -12,7 +12,10 @@
 
 namespace gpuns {
 
-__global__ void k_set_int(int* p, int v) { *p = v; }
+__global__ void k_set_int(int* p, int v) {
+    pdl_begin();
+    *p = v;
+}
 
 __constant__ double c_glx[4] = {-0.86113631159405257522, -0.33998104358485626480,
                                  0.33998104358485626480, 0.86113631159405257522};
@@ -24,6 +27,7 @@ __global__ void k_cube_to_theta(const double* __restrict__ cube, int d, int P,
                                 const int* __restrict__ kind, const double* __restrict__ pa,
                                 const double* __restrict__ pb, const int* __restrict__ free_of_full,
                                 double* __restrict__ theta_full, const int* __restrict__ nrows) {
+    pdl_begin();
     const int row = blockIdx.x;
     if (row >= *nrows) return;
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
@@ -115,6 +119,7 @@ __global__ void k_emu_input(const double* __restrict__ theta_full, int P, const 
                             const double* __restrict__ center, const double* __restrict__ scale, int K0,
                             const T* __restrict__ W0, const T* __restrict__ b0, ActDev<T> act, int N,
                             TO* __restrict__ out, const int* __restrict__ nrows) {
+    pdl_begin();
     const int row = blockIdx.y;
     if (row >= *nrows) return;
     __shared__ T x[32];
@@ -247,9 +252,9 @@ int gemm_f64_plain(const double* A, const double* W, double* C, const int* nrows
 int launch_cube_to_theta(const ns_problem* p, Workspace* ws, const double* cube, int grid_rows,
                          cudaStream_t st) {
     if (grid_rows <= 0) return NS_OK;
-    k_cube_to_theta<<<grid_rows, 64, 0, st>>>(cube, p->d, p->P, p->d_pkind, p->d_pa, p->d_pb,
-                                              p->d_free_of_full, ws->theta_full, ws->d_nrows);
-    NS_CUDA_TRY(cudaGetLastError());
+    NS_CUDA_TRY(launch_pdl(k_cube_to_theta, dim3(grid_rows), dim3(64), 0, st, cube, p->d, p->P,
+                           (const int*)p->d_pkind, (const double*)p->d_pa, (const double*)p->d_pb,
+                           (const int*)p->d_free_of_full, ws->theta_full, (const int*)ws->d_nrows));
     return NS_OK;
 }
 
@@ -325,10 +330,10 @@ static int run_emulator_bf16(const ns_problem* p, Workspace* ws, int grid_rows, 
     const int L = p->n_layers;
     const int K0 = p->dims[0], H1 = p->dims[1];
     dim3 g0((H1 + 255) / 256, grid_rows);
-    k_emu_input<float, __nv_bfloat16><<<g0, 256, 0, st>>>(
-        ws->theta_full, p->P, p->d_inputs, p->d_in_center, p->d_in_scale, K0, (const float*)p->d_W[0],
-        (const float*)p->d_b[0], layer_act<float>(p, 0), H1, (__nv_bfloat16*)ws->act[0], ws->d_nrows);
-    NS_CUDA_TRY(cudaGetLastError());
+    NS_CUDA_TRY(launch_pdl(k_emu_input<float, __nv_bfloat16>, g0, dim3(256), 0, st, (const double*)ws->theta_full,
+                           p->P, (const int*)p->d_inputs, (const double*)p->d_in_center,
+                           (const double*)p->d_in_scale, K0, (const float*)p->d_W[0], (const float*)p->d_b[0],
+                           layer_act<float>(p, 0), H1, (__nv_bfloat16*)ws->act[0], (const int*)ws->d_nrows));
     int cur = 0;
     for (int l = 1; l < L; ++l) {
         const int K = p->dims[l], N = p->dims[l + 1];

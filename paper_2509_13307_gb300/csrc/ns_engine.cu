@@ -6,7 +6,8 @@
 //                   and update log Z / log X / H in FP64 for k deletions
 //                   with n, n-1, ..., n-k+1 live points (Sec. 2.2): log X by
 //                   sequential subtraction, Z and H by fixed-order reductions.
-//   k_live_cov      covariance (ddof 1) of all n live cube points + ridge.
+//   k_live_mean,    covariance (ddof 1) of all n live cube points + ridge,
+//   k_live_cov      one CTA per column mean and per entry (i, j <= i).
 //   k_cholesky      FP64 Cholesky of that covariance (one block).
 //   k_directions    every (chain, move) slice direction of the iteration.
 //   k_chains_start  chain c starts at survivor floor(u (n - k)) (Philox START).
@@ -51,6 +52,7 @@ struct RunDev {
     int* starts;
     double* chol;
     double* cov;
+    double* mean;         // d column means of the live set
     double* dirs;         // k x R x d slice directions u = L_Sigma z / |z| of the iteration
     double* ch_x;
     double* ch_u;
@@ -66,8 +68,15 @@ struct RunDev {
     double* prop;         // proposals (rows x prop_stride), cube coordinates
     int prop_stride;      // d for a single run; the largest d when runs share the batch
     int* batch_ctr;       // row counter of the round's batch (shared by packed runs)
-    int* row_run;         // row -> run index when runs share the batch (else null)
     int run_id;
+    // prior transform fused into the proposal emission (Table 1)
+    int P;                // full parameter count
+    const int* pkind;     // per full parameter: ns_prior_kind
+    const double* pa;
+    const double* pb;
+    const int* fof;       // free index of each full parameter, or -1
+    int prior_f32;        // Gaussian priors through the FP32 Phi^-1 (reduced-precision problems)
+    double* theta_full;   // rows x P, read by the likelihood
     const double* logL;   // likelihood output per proposal row
     Scalars* sc;
     double* dead_x;
@@ -258,32 +267,34 @@ __global__ void __launch_bounds__(1024) k_sort_delete(RunDev r, int n_pad, int d
 }
 
 // ------------------------------------------------------------------ covariance + Cholesky
-__global__ void k_live_cov(RunDev r, double ridge) {
-    const int i = blockIdx.x;           // row of the covariance
-    const int d = r.d, n = r.n;
-    __shared__ double mean[64];
+// Column means of the n live cube points (one CTA per dimension).
+__global__ void __launch_bounds__(256) k_live_mean(RunDev r) {
+    const int c = blockIdx.x, d = r.d, n = r.n;
     __shared__ double red[32];
-    for (int c = threadIdx.x; c < d; c += blockDim.x) mean[c] = 0.0;
-    __syncthreads();
-    // means (each block recomputes them; n x d is small)
-    for (int c = 0; c < d; ++c) {
-        double s = 0.0;
-        for (int p = threadIdx.x; p < n; p += blockDim.x) s += r.live_x[(size_t)p * d + c];
-        s = block_sum(s, red);
-        if (threadIdx.x == 0) mean[c] = s / n;
-        __syncthreads();
-    }
-    for (int j = 0; j <= i; ++j) {
-        double s = 0.0;
-        for (int p = threadIdx.x; p < n; p += blockDim.x)
-            s += (r.live_x[(size_t)p * d + i] - mean[i]) * (r.live_x[(size_t)p * d + j] - mean[j]);
-        s = block_sum(s, red);
-        if (threadIdx.x == 0) {
-            double v = s / (n - 1);
-            if (j == i) v += ridge;
-            r.cov[i * d + j] = v;
-            r.cov[j * d + i] = v;
-        }
+    double s = 0.0;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) s += r.live_x[(size_t)p * d + c];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) r.mean[c] = s / n;
+}
+
+// Covariance (ddof 1) + ridge: one CTA per pair j <= i (pairs numbered row by row).
+__global__ void __launch_bounds__(256) k_live_cov(RunDev r, double ridge) {
+    int i = (int)((sqrt(8.0 * blockIdx.x + 1.0) - 1.0) * 0.5);
+    while ((i + 1) * (i + 2) / 2 <= (int)blockIdx.x) ++i;
+    while (i * (i + 1) / 2 > (int)blockIdx.x) --i;
+    const int j = blockIdx.x - i * (i + 1) / 2;
+    const int d = r.d, n = r.n;
+    __shared__ double red[32];
+    const double mi = r.mean[i], mj = r.mean[j];
+    double s = 0.0;
+    for (int p = threadIdx.x; p < n; p += blockDim.x)
+        s += (r.live_x[(size_t)p * d + i] - mi) * (r.live_x[(size_t)p * d + j] - mj);
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) {
+        double v = s / (n - 1);
+        if (j == i) v += ridge;
+        r.cov[i * d + j] = v;
+        r.cov[j * d + i] = v;
     }
 }
 
@@ -358,24 +369,53 @@ __global__ void __launch_bounds__(256) k_directions(RunDev r) {
     if (lane < nch) {
         const Draw2 q = philox_uniforms(r.seed, P_DIR, lane, (uint32_t)it, (uint32_t)c, (uint32_t)move);
         const double rad = sqrt(-2.0 * log(q.a));
-        const double ang = 6.283185307179586 * q.b;
-        z0 = rad * cos(ang);
-        z1 = rad * sin(ang);
-        zsw[2 * lane] = z0;
-        if (2 * lane + 1 < d) zsw[2 * lane + 1] = z1; else z1 = 0.0;
+        double sn, cs;
+        sincos(6.283185307179586 * q.b, &sn, &cs);
+        z0 = rad * cs;
+        z1 = (2 * lane + 1 < d) ? rad * sn : 0.0;
     }
     const double nrm = sqrt(warp_sum(z0 * z0 + z1 * z1));
+    // z / |z| once per component (each quotient computed by one lane)
+    if (lane < nch) {
+        zsw[2 * lane] = z0 / nrm;
+        if (2 * lane + 1 < d) zsw[2 * lane + 1] = z1 / nrm;
+    }
     __syncwarp();
     double* out = r.dirs + (size_t)g * d;
     if (lane < d) {
         double a0 = 0.0;
-        for (int b = 0; b <= lane; ++b) a0 += r.chol[lane * d + b] * (zsw[b] / nrm);
+        for (int b = 0; b <= lane; ++b) a0 += r.chol[lane * d + b] * zsw[b];
         out[lane] = a0;
     }
     if (lane + 32 < d) {
         double a1 = 0.0;
-        for (int b = 0; b <= lane + 32; ++b) a1 += r.chol[(lane + 32) * d + b] * (zsw[b] / nrm);
+        for (int b = 0; b <= lane + 32; ++b) a1 += r.chol[(lane + 32) * d + b] * zsw[b];
         out[lane + 32] = a1;
+    }
+}
+
+// Physical parameters of proposal row `row` (Table 1 prior transform), written
+// by the chain's warp: lanes own full parameters lane and lane + 32 and fetch
+// their cube coordinate from the lane holding it (y0: dims < 32, y1: dims >= 32).
+__device__ __forceinline__ void emit_theta(const RunDev& r, int row, double y0, double y1, int lane) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        const int f = (i < r.P) ? r.fof[i] : -1;
+        const int src = (f >= 0) ? (f & 31) : 0;
+        const double c0 = __shfl_sync(0xffffffffu, y0, src);
+        const double c1 = __shfl_sync(0xffffffffu, y1, src);
+        if (i < r.P) {
+            double v;
+            if (f < 0) {
+                v = r.pa[i];
+            } else {
+                const double c = (f < 32) ? c0 : c1;
+                if (r.pkind[i] == NS_PRIOR_UNIFORM) v = r.pa[i] + (r.pb[i] - r.pa[i]) * c;
+                else v = r.pa[i] + r.pb[i] * (r.prior_f32 ? (double)normcdfinvf((float)c) : normcdfinv(c));
+            }
+            r.theta_full[(size_t)row * r.P + i] = v;
+        }
     }
 }
 
@@ -449,13 +489,11 @@ __device__ void advance_chain(const RunDev& r, int c, int lane) {
                 continue;
             }
             int rw = 0;
-            if (lane == 0) {
-                rw = atomicAdd(r.batch_ctr, 1);
-                if (r.row_run) r.row_run[rw] = r.run_id;
-            }
+            if (lane == 0) rw = atomicAdd(r.batch_ctr, 1);
             row = __shfl_sync(0xffffffffu, rw, 0);
             if (has0) r.prop[(size_t)row * r.prop_stride + lane] = y0;
             if (has1) r.prop[(size_t)row * r.prop_stride + lane + 32] = y1;
+            emit_theta(r, row, has0 ? y0 : 0.0, has1 ? y1 : 0.0, lane);
             ++evals;
             break;
         }
@@ -477,13 +515,11 @@ __device__ void advance_chain(const RunDev& r, int c, int lane) {
                 continue;
             }
             int rw = 0;
-            if (lane == 0) {
-                rw = atomicAdd(r.batch_ctr, 1);
-                if (r.row_run) r.row_run[rw] = r.run_id;
-            }
+            if (lane == 0) rw = atomicAdd(r.batch_ctr, 1);
             row = __shfl_sync(0xffffffffu, rw, 0);
             if (has0) r.prop[(size_t)row * r.prop_stride + lane] = y0;
             if (has1) r.prop[(size_t)row * r.prop_stride + lane + 32] = y1;
+            emit_theta(r, row, has0 ? y0 : 0.0, has1 ? y1 : 0.0, lane);
             ++evals;
             break;
         }
@@ -500,6 +536,7 @@ __device__ void advance_chain(const RunDev& r, int c, int lane) {
 }
 
 __global__ void __launch_bounds__(256) k_slice_advance(RunDev r) {
+    pdl_begin();
     const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (c >= r.k) return;
     advance_chain(r, c, threadIdx.x & 31);
@@ -696,10 +733,8 @@ static int sync_scalars(ns_run* r) {
 }
 
 static int launch_round(ns_run* r, cudaStream_t st, const StageProbe* probe) {
-    NS_CUDA_TRY(cudaMemsetAsync(&r->sc->batch, 0, sizeof(int), st));
-    k_slice_advance<<<(r->k + 7) / 8, 256, 0, st>>>(r->rd);
-    NS_CUDA_TRY(cudaGetLastError());
-    NS_TRY(launch_cube_to_theta(r->p, &r->ws, r->rd.prop, r->k, st));
+    NS_CUDA_TRY(launch_pdl(k_set_int, dim3(1), dim3(1), 0, st, &r->sc->batch, 0));
+    NS_CUDA_TRY(launch_pdl(k_slice_advance, dim3((r->k + 7) / 8), dim3(256), 0, st, r->rd));
     return run_likelihood(r->p, &r->ws, r->k, r->ws.logL, nullptr, st, probe);
 }
 
@@ -783,6 +818,7 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
     RA(starts, sizeof(int) * k);
     RA(chol, sizeof(double) * d * d);
     RA(cov, sizeof(double) * d * d);
+    RA(mean, sizeof(double) * d);
     RA(dirs, sizeof(double) * (size_t)k * r->R * d);
     RA(ch_x, sizeof(double) * k * d);
     RA(ch_u, sizeof(double) * k * d);
@@ -802,8 +838,14 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
     k_reset_chains<<<(k + 127) / 128, 128, 0, r->st>>>(rd);
     rd.prop_stride = d;
     rd.batch_ctr = &rd.sc->batch;
-    rd.row_run = nullptr;
     rd.run_id = 0;
+    rd.P = p->P;
+    rd.pkind = p->d_pkind;
+    rd.pa = p->d_pa;
+    rd.pb = p->d_pb;
+    rd.fof = p->d_free_of_full;
+    rd.prior_f32 = p->precision != NS_PREC_FP64;
+    rd.theta_full = r->ws.theta_full;
     r->sc = rd.sc;
     if (cudaMallocHost(&r->h_sc, sizeof(Scalars)) != cudaSuccess) return fail(NS_ENOMEM);
     std::memset(r->h_sc, 0, sizeof(Scalars));
@@ -836,7 +878,8 @@ static int one_iteration(ns_run* r) {
     const size_t sm = (size_t)r->n_pad * (sizeof(double) + sizeof(int)) + sizeof(double) * r->k;
     k_sort_delete<<<1, 1024, sm, st>>>(rd, r->n_pad, r->k, 1);
     NS_CUDA_TRY(cudaGetLastError());
-    k_live_cov<<<r->d, 256, 0, st>>>(rd, r->cfg.ridge);
+    k_live_mean<<<r->d, 256, 0, st>>>(rd);
+    k_live_cov<<<r->d * (r->d + 1) / 2, 256, 0, st>>>(rd, r->cfg.ridge);
     k_cholesky<<<1, 128, 0, st>>>(rd);
     k_directions<<<(unsigned)(((long long)r->k * r->R + 7) / 8), 256, 0, st>>>(rd);
     k_chains_start<<<(r->k + 127) / 128, 128, 0, st>>>(rd);
@@ -993,27 +1036,6 @@ extern "C" int ns_free(ns_run* r) {
 // ======================================================================
 namespace gpuns {
 
-__global__ void k_cube_to_theta_multi(const double* __restrict__ cube, int stride, const int* __restrict__ row_run,
-                                      int P, const int* __restrict__ kind, const double* __restrict__ pa,
-                                      const double* __restrict__ pb, const int* __restrict__ fof,
-                                      double* __restrict__ theta_full, const int* __restrict__ nrows) {
-    const int row = blockIdx.x;
-    if (row >= *nrows) return;
-    const int base = row_run[row] * P;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const int f = fof[base + i];
-        double v;
-        if (f < 0) {
-            v = pa[base + i];
-        } else {
-            const double c = cube[(size_t)row * stride + f];
-            v = (kind[base + i] == NS_PRIOR_UNIFORM) ? pa[base + i] + (pb[base + i] - pa[base + i]) * c
-                                                      : pa[base + i] + pb[base + i] * normcdfinv(c);
-        }
-        theta_full[(size_t)row * P + i] = v;
-    }
-}
-
 }  // namespace gpuns
 
 struct ns_multi {
@@ -1025,11 +1047,8 @@ struct ns_multi {
     Workspace ws;
     int stride = 0, total_chains = 0;
     double* prop = nullptr;
-    int* row_run = nullptr;
     RunDev* d_runs = nullptr;
     int* d_chain_off = nullptr;
-    int *d_kind = nullptr, *d_fof = nullptr;
-    double *d_pa = nullptr, *d_pb = nullptr;
     std::vector<void*> owned;
     cudaGraphExec_t graph = nullptr;
     int graph_rounds = 0;
@@ -1055,7 +1074,7 @@ static int multi_refresh_runs(ns_multi* m) {
         h[i].prop = m->prop;
         h[i].prop_stride = m->stride;
         h[i].batch_ctr = m->ws.d_nrows;
-        h[i].row_run = m->row_run;
+        h[i].theta_full = m->ws.theta_full;
         h[i].run_id = i;
         h[i].logL = m->ws.logL;
     }
@@ -1067,9 +1086,6 @@ static int multi_refresh_runs(ns_multi* m) {
 static int multi_launch_round(ns_multi* m, cudaStream_t st) {
     NS_CUDA_TRY(cudaMemsetAsync(m->ws.d_nrows, 0, sizeof(int), st));
     k_slice_advance_multi<<<(m->total_chains + 7) / 8, 256, 0, st>>>(m->d_runs, m->d_chain_off, m->n_runs);
-    NS_CUDA_TRY(cudaGetLastError());
-    k_cube_to_theta_multi<<<m->total_chains, 64, 0, st>>>(m->prop, m->stride, m->row_run, m->model->P, m->d_kind,
-                                                          m->d_pa, m->d_pb, m->d_fof, m->ws.theta_full, m->ws.d_nrows);
     NS_CUDA_TRY(cudaGetLastError());
     return run_likelihood(m->model, &m->ws, m->total_chains, m->ws.logL, nullptr, st);
 }
@@ -1131,26 +1147,11 @@ extern "C" int ns_multi_init(const ns_problem* const* problems, int n_runs, cons
         m->owned.push_back(q);
         return q;
     };
-    const int P = p0->P;
     m->prop = (double*)alloc(sizeof(double) * (size_t)m->total_chains * m->stride);
-    m->row_run = (int*)alloc(sizeof(int) * (size_t)m->total_chains);
     m->d_runs = (RunDev*)alloc(sizeof(RunDev) * n_runs);
     m->d_chain_off = (int*)alloc(sizeof(int) * (n_runs + 1));
-    m->d_kind = (int*)alloc(sizeof(int) * (size_t)n_runs * P);
-    m->d_fof = (int*)alloc(sizeof(int) * (size_t)n_runs * P);
-    m->d_pa = (double*)alloc(sizeof(double) * (size_t)n_runs * P);
-    m->d_pb = (double*)alloc(sizeof(double) * (size_t)n_runs * P);
-    if (!m->prop || !m->row_run || !m->d_runs || !m->d_chain_off || !m->d_kind || !m->d_fof || !m->d_pa || !m->d_pb)
-        return fail(NS_ENOMEM);
+    if (!m->prop || !m->d_runs || !m->d_chain_off) return fail(NS_ENOMEM);
     (void)v;
-    for (int i = 0; i < n_runs; ++i) {
-        const ns_problem* p = problems[i];
-        if (cudaMemcpy(m->d_kind + i * P, p->d_pkind, sizeof(int) * P, cudaMemcpyDeviceToDevice) != cudaSuccess ||
-            cudaMemcpy(m->d_fof + i * P, p->d_free_of_full, sizeof(int) * P, cudaMemcpyDeviceToDevice) != cudaSuccess ||
-            cudaMemcpy(m->d_pa + i * P, p->d_pa, sizeof(double) * P, cudaMemcpyDeviceToDevice) != cudaSuccess ||
-            cudaMemcpy(m->d_pb + i * P, p->d_pb, sizeof(double) * P, cudaMemcpyDeviceToDevice) != cudaSuccess)
-            return fail(NS_ECUDA);
-    }
     if (cudaMemcpy(m->d_chain_off, off.data(), sizeof(int) * (n_runs + 1), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(NS_ECUDA);
     m->state.assign(n_runs, 0);
@@ -1164,7 +1165,8 @@ static int multi_start_iteration(ns_multi* m, int i) {
     NS_TRY(grow_dead(r, r->h_sc->n_dead + r->k));
     const size_t sm = (size_t)r->n_pad * (sizeof(double) + sizeof(int)) + sizeof(double) * r->k;
     k_sort_delete<<<1, 1024, sm, m->st>>>(r->rd, r->n_pad, r->k, 1);
-    k_live_cov<<<r->d, 256, 0, m->st>>>(r->rd, r->cfg.ridge);
+    k_live_mean<<<r->d, 256, 0, m->st>>>(r->rd);
+    k_live_cov<<<r->d * (r->d + 1) / 2, 256, 0, m->st>>>(r->rd, r->cfg.ridge);
     k_cholesky<<<1, 128, 0, m->st>>>(r->rd);
     k_directions<<<(unsigned)(((long long)r->k * r->R + 7) / 8), 256, 0, m->st>>>(r->rd);
     k_chains_start<<<(r->k + 127) / 128, 128, 0, m->st>>>(r->rd);

@@ -41,19 +41,26 @@ template <> __device__ __forceinline__ const float* pick<float>(const double*, c
 // Transcendentals: accurate library versions, or (FAST, BF16 modes) the SFU
 // approximations, whose ~1e-6 relative error is far below the bf16 emulator's.
 template <typename T, bool FAST> struct Math;
+// div / rsq: IEEE quotient and 1/sqrt, or (FAST) the SFU reciprocal forms.
 template <> struct Math<double, false> {
     static __device__ __forceinline__ double ex(double x) { return exp(x); }
     static __device__ __forceinline__ double lg(double x) { return log(x); }
     static __device__ __forceinline__ double p10(double v) { return exp(v * kLn10); }
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
 };
 template <> struct Math<float, false> {
     static __device__ __forceinline__ float ex(float x) { return expf(x); }
     static __device__ __forceinline__ float lg(float x) { return logf(x); }
     static __device__ __forceinline__ float p10(float v) { return exp2f(v * 3.32192809488736234787f); }
+    static __device__ __forceinline__ float div(float a, float b) { return a / b; }
+    static __device__ __forceinline__ float rsq(float x) { return 1.f / sqrtf(x); }
 };
 template <> struct Math<float, true> {
     static __device__ __forceinline__ float ex(float x) { return __expf(x); }
     static __device__ __forceinline__ float lg(float x) { return __logf(x); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
     static __device__ __forceinline__ float p10(float v) {
         float y;
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v * 3.32192809488736234787f));
@@ -158,9 +165,9 @@ k_windows(const ShearParams sp, const double* __restrict__ theta_full, T* __rest
             for (int g = 0; g < 4; ++g) {
                 const T ag = mid + half * (T)c_glx2[g];
                 const T lg = M::lg(ag);
-                const T ia = T(1) / ag;
+                const T ia = M::div(T(1), ag);
                 const T eg = om * ia * ia * ia + (T(1) - om) * M::ex(-pde * lg - T(3) * wa * (T(1) - ag));
-                inc += (T)c_glw2[g] * ia * ia / sqrt_<T>(eg);
+                inc += (T)c_glw2[g] * ia * ia * M::rsq(eg);
             }
             inc *= chiH * half;
         }
@@ -172,9 +179,9 @@ k_windows(const ShearParams sp, const double* __restrict__ theta_full, T* __rest
         const T c = t0[n];
         chi[n] = c;
         lnchi[n] = (n >= 1) ? M::lg(c) : T(0);
-        const T oma = om * M::ex(T(-3) * lna_[n]) / (Ez[n] * Ez[n]);
+        const T oma = M::div(om * M::ex(T(-3) * lna_[n]), Ez[n] * Ez[n]);
         t1[n] = M::ex(gamma * M::lg(oma));
-        omw[n] = wa_[n] * chiH / (a_[n] * a_[n] * Ez[n]);
+        omw[n] = M::div(wa_[n] * chiH, a_[n] * a_[n] * Ez[n]);
     }
     __syncthreads();
     for (int n = tid; n < N; n += nt)
@@ -188,11 +195,17 @@ k_windows(const ShearParams sp, const double* __restrict__ theta_full, T* __rest
     T pn[NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) pn[i] = T(0);
+    T zc[NB], isg[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        zc[i] = th[11 + i] + (T)sp.nz_mean[i];
+        isg[i] = M::div(T(1), (T)sp.nz_sigma[i]);
+    }
     for (int n = tid; n < N; n += nt) {
-        const T wz = wa_[n] / (a_[n] * a_[n]);
+        const T wz = M::div(wa_[n], a_[n] * a_[n]);
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
-            const T u = (z_[n] - th[11 + i] - (T)sp.nz_mean[i]) / (T)sp.nz_sigma[i];
+            const T u = FAST ? (z_[n] - zc[i]) * isg[i] : (z_[n] - th[11 + i] - (T)sp.nz_mean[i]) / (T)sp.nz_sigma[i];
             const T raw = M::ex(T(-0.5) * u * u);
             V[i * N + n] = raw;
             pn[i] += wz * raw;
@@ -220,6 +233,7 @@ k_windows(const ShearParams sp, const double* __restrict__ theta_full, T* __rest
     for (int i = 0; i < NB; ++i) { s0[i] = T(0); s1[i] = T(0); }
     for (int n = lo; n < hi; ++n) {
         const T e = Ez[n];
+        const T ichi = (FAST && n >= 1) ? M::div(T(1), chi[n]) : T(0);
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
             const T nchi = V[i * N + n] * e * inv_norm[i];
@@ -227,7 +241,7 @@ k_windows(const ShearParams sp, const double* __restrict__ theta_full, T* __rest
             if (n >= 1) {
                 const T wn = omw[n] * nchi;
                 s0[i] += wn;
-                s1[i] += wn / chi[n];
+                s1[i] += FAST ? wn * ichi : wn / chi[n];
             }
         }
     }
@@ -252,11 +266,15 @@ k_windows(const ShearParams sp, const double* __restrict__ theta_full, T* __rest
         for (int w = wid + 1; w < kProjWarps; ++w) { e0[i] += red[w * 2 * NB + i]; e1[i] += red[w * 2 * NB + NB + i]; }
     const T pref = T(1.5) * om / (chiH * chiH);
     const T A_IA = th[9], eta = th[10];
+    const T ipiv = M::div(T(1), (T)sp.ia_pivot);
+    const T c1om = (T)sp.c1rho * om;
     for (int n = hi - 1; n >= lo; --n) {
         const T c = chi[n];
-        const T sq = (n >= 1) ? sqrt_<T>(omw[n] / (c * c)) : T(0);
-        const T amp = A_IA * M::ex(eta * M::lg((T(1) + z_[n]) / (T)sp.ia_pivot)) * (T)sp.c1rho * om / Dg[n];
-        const T pc = pref * c / a_[n];
+        const T ic = (FAST && n >= 1) ? M::div(T(1), c) : T(0);
+        const T sq = (n >= 1) ? (FAST ? sqrt_<T>(omw[n]) * ic : sqrt_<T>(omw[n] / (c * c))) : T(0);
+        const T amp = FAST ? M::div(A_IA * M::ex(eta * M::lg((T(1) + z_[n]) * ipiv)) * c1om, Dg[n])
+                           : A_IA * M::ex(eta * M::lg((T(1) + z_[n]) / (T)sp.ia_pivot)) * (T)sp.c1rho * om / Dg[n];
+        const T pc = FAST ? pref * c * M::div(T(1), a_[n]) : pref * c / a_[n];
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
             const T nchi = V[i * N + n];
@@ -265,7 +283,7 @@ k_windows(const ShearParams sp, const double* __restrict__ theta_full, T* __rest
                 v = sq * (pc * (e0[i] - c * e1[i]) - amp * nchi);
                 const T wn = omw[n] * nchi;
                 e0[i] += wn;
-                e1[i] += wn / c;
+                e1[i] += FAST ? wn * ic : wn / c;
             }
             V[i * N + n] = v;
         }
@@ -381,6 +399,7 @@ k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* _
     using M = Math<T, FAST>;
     constexpr int NP = NB * (NB + 1) / 2;
     static_assert(2 * NP <= 32, "two multipoles of pair sums must fit one warp transpose");
+    pdl_begin();
     const int row = blockIdx.y;
     if (row >= *nrows) return;
     const int l_base = blockIdx.x * kLGroup;
@@ -569,6 +588,7 @@ template <typename TR, typename TA>
 __global__ void __launch_bounds__(256)
 k_whiten(const TR* __restrict__ resid, int D, const TA* __restrict__ LinvT, TA* __restrict__ partial, int ntile,
          int KC, int* __restrict__ done, double c0, double* __restrict__ logL, const int* __restrict__ nrows) {
+    pdl_begin();
     const int M = *nrows;
     const int row0 = blockIdx.y * kWR;
     if (row0 >= M) return;
@@ -708,8 +728,8 @@ int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL
         attr = true;
     }
     dim3 g(ntile, (grid_rows + kWR - 1) / kWR);
-    k_whiten<TR, TA><<<g, 256, smem, st>>>(resid, D, LinvT, (TA*)partial, ntile, KC, done, c0, logL, nrows);
-    NS_CUDA_TRY(cudaGetLastError());
+    NS_CUDA_TRY(launch_pdl(k_whiten<TR, TA>, g, dim3(256), smem, st, resid, D, LinvT, (TA*)partial, ntile, KC, done,
+                           c0, logL, nrows));
     return NS_OK;
 }
 template int launch_chi2<float, float>(const float*, int, const float*, double, double*, void*, int*, const int*,
@@ -766,8 +786,8 @@ static int limber_nb(const ShearParams& sp, const double* theta_full, const T* t
         attr_done = true;
     }
     dim3 g((sp.n_ell + kLGroup - 1) / kLGroup, grid_rows);
-    k_limber<T, NB, FAST><<<g, kProjThreads, smem, st>>>(sp, theta_full, table, win, resid, model_out, nrows, err);
-    NS_CUDA_TRY(cudaGetLastError());
+    NS_CUDA_TRY(launch_pdl(k_limber<T, NB, FAST>, g, dim3(kProjThreads), smem, st, sp, theta_full, table, win, resid,
+                           model_out, nrows, err));
     return NS_OK;
 }
 
