@@ -236,6 +236,121 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     }
 }
 
+// Output layer with swapped operands for a small row count: the MMA's M is
+// 128 output features (rows of W, the A operand) and its N is BR activation
+// rows (the B operand), D^T[f][r] = W[f][:] . X[r][:] in TMEM.  With
+// BR = 256 the 39-d output layer (10000 features, <= 500 rows) is one wave of
+// CTAs; each thread owns one feature, so mu / bias are loaded once per thread
+// and for every row the 32 lanes of a warp store 32 consecutive features.
+template <int BR>
+struct CfgS {
+    static constexpr int STAGES = 4;
+    static constexpr int A_BYTES = 128 * BK * 2;
+    static constexpr int B_BYTES = BR * BK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+    static constexpr uint32_t TMEM_COLS = BR;
+};
+
+template <int BR>
+__global__ void __launch_bounds__(128, 1)
+k_gemm_tc_swap(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmX,
+               const float* __restrict__ bias, const float* __restrict__ out_mu, float out_sigma,
+               float* __restrict__ Cout, const int* __restrict__ nrows, int N, int K, int* __restrict__ err) {
+    using C = CfgS<BR>;
+    pdl_begin();
+    const int M = *nrows;
+    const int f0 = blockIdx.x * 128, r0 = blockIdx.y * BR;
+    if (r0 >= M) return;
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - raw);
+    const uint32_t bar0 = base + C::STAGES * C::STAGE_BYTES;
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (C::STAGES + s); };
+    const uint32_t accf = bar0 + 8u * (2 * C::STAGES);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + C::STAGES * C::STAGE_BYTES + 8 * (2 * C::STAGES + 1));
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int s = 0; s < C::STAGES; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), 1); }
+        mbar_init(accf, 1);
+        mbar_init_fence();
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tmem_slot)), "r"(C::TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int nk = (K + BK - 1) / BK;
+
+    if (warp == 0 && lane == 0) {
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % C::STAGES;
+            if (kb >= C::STAGES && !mbar_wait(empty_bar(s), ((kb / C::STAGES) & 1) ^ 1)) { s_fail = 1; break; }
+            const uint32_t sa = base + s * C::STAGE_BYTES;
+            mbar_expect_tx(full_bar(s), C::STAGE_BYTES);
+            tma_load_2d(sa, &tmW, full_bar(s), kb * BK, f0);
+            tma_load_2d(sa + C::A_BYTES, &tmX, full_bar(s), kb * BK, r0);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // M = 128 features, N = BR rows
+        constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BR >> 3) << 17) |
+                                   ((uint32_t)(128 >> 4) << 24);
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % C::STAGES;
+            if (!mbar_wait(full_bar(s), (kb / C::STAGES) & 1)) { s_fail = 1; break; }
+            fence_after();
+            const uint32_t sa = base + s * C::STAGE_BYTES;
+            const uint64_t da = smem_desc(sa), db = smem_desc(sa + C::A_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+                mma_bf16(tmem, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0);
+            mma_commit(empty_bar(s));
+        }
+        mma_commit(accf);
+    }
+    __syncwarp();
+
+    const bool ok = mbar_wait(accf, 0);
+    fence_after();
+    __syncwarp();
+    if (ok && !s_fail) {
+        const int f = f0 + warp * 32 + lane;
+        const bool valid = f < N;
+        const float mu_f = valid ? __ldg(out_mu + f) : 0.f;
+        const float b_f = valid ? __ldg(bias + f) : 0.f;
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c = 0; c < BR / 32; ++c) {
+            if (r0 + c * 32 >= M) break;
+            float v[32];
+            tmem_ld32(lane_addr + c * 32, v);
+            if (!valid) continue;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int r = r0 + c * 32 + j;
+                if (r < M) Cout[(size_t)r * N + f] = mu_f + out_sigma * (v[j] + b_f);
+            }
+        }
+    }
+    if ((!ok || s_fail) && threadIdx.x == 0 && err) atomicOr(err, NS_BIT_TIMEOUT);
+    fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(C::TMEM_COLS) : "memory");
+    }
+}
+
 template <int BN>
 static int launch_bn(const CUtensorMap* tmA, const CUtensorMap* tmB, const float* bias, const float* mu,
                      float sigma, void* Cout, const int* nrows, int grid_rows, int N, int K, int epi,
@@ -268,6 +383,23 @@ int launch_gemm_tc(const CUtensorMap* tmA, const CUtensorMap* tmB, int tile_n, c
         case 256: return tc::launch_bn<256>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, act_beta, d_err, st);
         default: return NS_EINVAL;
     }
+}
+
+int launch_gemm_tc_out_swap(const CUtensorMap* tmW, const CUtensorMap* tmX, const float* bias, const float* out_mu,
+                            float out_sigma, float* C, const int* d_nrows, int grid_rows, int N, int K, int* d_err,
+                            cudaStream_t st) {
+    if (grid_rows <= 0) return NS_OK;
+    constexpr int BR = kSwapRows;
+    using CS = tc::CfgS<BR>;
+    static bool attr = false;
+    if (!attr) {
+        NS_CUDA_TRY(cudaFuncSetAttribute(tc::k_gemm_tc_swap<BR>, cudaFuncAttributeMaxDynamicSharedMemorySize, CS::SMEM));
+        attr = true;
+    }
+    dim3 grid((N + 127) / 128, (grid_rows + BR - 1) / BR);
+    NS_CUDA_TRY(launch_pdl(tc::k_gemm_tc_swap<BR>, grid, dim3(128), (size_t)CS::SMEM, st, *tmW, *tmX, bias, out_mu,
+                           out_sigma, C, d_nrows, N, K, d_err));
+    return NS_OK;
 }
 
 int gemm_tc_supported(int N, int K) {

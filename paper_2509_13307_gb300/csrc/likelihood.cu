@@ -345,6 +345,11 @@ static int run_emulator_bf16(const ns_problem* p, Workspace* ws, int grid_rows, 
                 (const __nv_bfloat16*)ws->act[cur], (const float*)hd->W, (const float*)hd->bias,
                 ActDev<float>{0, nullptr, nullptr}, (const float*)hd->mu, (const float*)hd->sig_vec,
                 (float)hd->sigma, (float*)hd->out, ws->d_nrows, grid_rows, N, K, EPI_OUT, st)));
+        } else if (last && p->tile_n[l] == 128) {
+            // the output layer with few rows: features as the MMA's M (one wave of CTAs)
+            NS_TRY(launch_gemm_tc_out_swap(&p->tmB[l], &ws->tmX_out, (const float*)p->d_b[l],
+                                           (const float*)p->d_out_mu, (float)p->out_sigma, (float*)ws->table,
+                                           ws->d_nrows, grid_rows, N, K, ws->d_err, st));
         } else {
             const ActDev<float> a = layer_act<float>(p, l);
             const int epi = last ? TC_EPI_OUT : (p->act == NS_ACT_SIGMOID_LINEAR ? TC_EPI_SIGLIN : TC_EPI_TANH);

@@ -51,6 +51,7 @@ struct Workspace {
     double* logL = nullptr;       // cap
     // tcgen05 tensor maps (BF16 precision): A operand of layer l >= 1 and its output
     std::vector<CUtensorMap> tmA;
+    CUtensorMap tmX_out{};        // the last layer's activations in kSwapRows-row boxes
     std::vector<void*> owned;
     // second stream for the emulator-independent windows stage; fork/join events
     cudaStream_t side = nullptr;
@@ -179,6 +180,13 @@ int launch_gemm_tc(const CUtensorMap* tmA, const CUtensorMap* tmB, int tile_n,
                    void* C, const int* d_nrows, int grid_rows, int N, int K, int epi,
                    const float* act_beta, int* d_err, cudaStream_t st);
 int make_tensor_map_bf16(CUtensorMap* tm, const void* base, int rows, int K, int box_rows);
+// Output layer with swapped operands (rows of W as the MMA's M, activation rows
+// as its N, kSwapRows per CTA): tmW boxes 128 rows of W, tmX boxes kSwapRows
+// activation rows; FP32 out = mu + sigma (acc + b), row-major rows x N.
+constexpr int kSwapRows = 256;
+int launch_gemm_tc_out_swap(const CUtensorMap* tmW, const CUtensorMap* tmX, const float* bias, const float* out_mu,
+                            float out_sigma, float* C, const int* d_nrows, int grid_rows, int N, int K, int* d_err,
+                            cudaStream_t st);
 // Dense FP64 set-up kernels (dense_linalg.cu): C (device, overwritten by L) ->
 // L^-1 (new device buffer) and sum ln L_aa; NS_EINVAL if C is not SPD.
 int device_cholesky_inverse(double* dC, int D, double** Xout, double* sum_log_diag, cudaStream_t st);

@@ -171,6 +171,8 @@ int workspace_create(const ns_problem* p, int cap, Workspace* ws) {
         int cur = 0;
         for (int l = 1; l < p->n_layers; ++l) {
             NS_TRY(make_tensor_map_bf16(&ws->tmA[l], ws->act[cur], rows_pad, p->dims[l], 128));
+            if (l == p->n_layers - 1)
+                NS_TRY(make_tensor_map_bf16(&ws->tmX_out, ws->act[cur], rows_pad, p->dims[l], kSwapRows));
             cur ^= 1;
         }
     }
