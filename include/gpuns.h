@@ -167,6 +167,9 @@ typedef struct {
     int step_cap;                 /* cap on stepping-out steps and on shrinkage steps */
     double ridge;                 /* added to the live-covariance diagonal */
     int rounds_per_sync;          /* likelihood rounds launched between host checks (<= 0: auto) */
+    int chain_groups;             /* 1 or 2 groups of chains whose likelihood rounds run on two
+                                     streams and overlap on the GPU (results are identical);
+                                     <= 0: auto (2 for k >= 128, shear kind) */
 } ns_config;
 
 typedef struct {

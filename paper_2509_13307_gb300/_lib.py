@@ -66,7 +66,7 @@ class ProblemDesc(C.Structure):
 class Config(C.Structure):
     _fields_ = [("n_live", C.c_int), ("n_delete", C.c_int), ("repeats", C.c_int), ("tol", C.c_double),
                 ("seed", C.c_ulonglong), ("width", C.c_double), ("step_cap", C.c_int), ("ridge", C.c_double),
-                ("rounds_per_sync", C.c_int)]
+                ("rounds_per_sync", C.c_int), ("chain_groups", C.c_int)]
 
 
 class Status(C.Structure):

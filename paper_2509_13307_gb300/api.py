@@ -302,12 +302,12 @@ class NestedRun:
 
     def __init__(self, problem: Problem, n_live: int, n_delete: int, repeats: int | None = None,
                  tol: float = 1e-3, seed: int = 3, width: float = 1.0, step_cap: int = 100,
-                 ridge: float = 1e-12, rounds_per_sync: int = 0, stream=None):
+                 ridge: float = 1e-12, rounds_per_sync: int = 0, chain_groups: int = 0, stream=None):
         self.lib = problem.lib
         self.problem = problem
         self.n_live, self.n_delete, self.d = n_live, n_delete, problem.d
         cfg = L.Config(n_live, n_delete, 0 if repeats is None else repeats, tol, seed, width, step_cap, ridge,
-                       rounds_per_sync)
+                       rounds_per_sync, chain_groups)
         self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         L.check(self.lib.ns_init(problem.handle, C.byref(cfg), _stream(self._stream_obj), C.byref(h)), "ns_init")
@@ -398,7 +398,7 @@ class MultiRun:
         n = len(problems)
         arr = (C.c_void_p * n)(*[p.handle.value for p in problems])
         cfgs = (L.Config * n)(*[L.Config(sc.n_live, sc.n_delete, 0 if sc.repeats is None else sc.repeats, sc.tol,
-                                         sc.seed, sc.width, sc.step_cap, sc.ridge, 0) for sc in samplers])
+                                         sc.seed, sc.width, sc.step_cap, sc.ridge, 0, 1) for sc in samplers])
         self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         L.check(self.lib.ns_multi_init(arr, n, cfgs, _stream(self._stream_obj), C.byref(h)), "ns_multi_init")

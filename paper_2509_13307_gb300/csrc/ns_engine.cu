@@ -69,6 +69,8 @@ struct RunDev {
     int prop_stride;      // d for a single run; the largest d when runs share the batch
     int* batch_ctr;       // row counter of the round's batch (shared by packed runs)
     int run_id;
+    int chain0;           // first chain of this group of rounds
+    int grp_chains;       // chains of this group
     // prior transform fused into the proposal emission (Table 1)
     int P;                // full parameter count
     const int* pkind;     // per full parameter: ns_prior_kind
@@ -535,11 +537,12 @@ __device__ void advance_chain(const RunDev& r, int c, int lane) {
     }
 }
 
+// One warp per chain of the group [chain0, chain0 + grp_chains).
 __global__ void __launch_bounds__(256) k_slice_advance(RunDev r) {
     pdl_begin();
     const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (c >= r.k) return;
-    advance_chain(r, c, threadIdx.x & 31);
+    if (c >= r.grp_chains) return;
+    advance_chain(r, r.chain0 + c, threadIdx.x & 31);
 }
 
 // All chains of several packed runs: global warp g -> (run, chain) through the
@@ -691,6 +694,13 @@ struct ns_run {
     StageProbe probe;                 // optional timing of one stage in round 0 of each graph launch
     double prof_ms = 0.0;
     long long prof_launches = 0, prof_rows = 0;
+    // chain groups: group 0 uses rd / ws; group 1 (chains [k0, k)) its own
+    // batch, proposals and likelihood workspace, with rounds on a second stream
+    int n_groups = 1, k0 = 0;
+    Workspace ws1;
+    RunDev grd[2]{};
+    cudaStream_t cap_st1 = nullptr;
+    cudaEvent_t ev_gfork = nullptr, ev_gjoin = nullptr;
 };
 
 static int run_alloc(ns_run* r, size_t bytes, void** p) {
@@ -724,34 +734,72 @@ static int grow_dead(ns_run* r, long long need) {
 static int sync_scalars(ns_run* r) {
     NS_CUDA_TRY(cudaMemcpyAsync(r->h_sc, r->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, r->st));
     NS_TRY(workspace_err_fetch(&r->ws, r->st));
+    if (r->n_groups > 1) NS_TRY(workspace_err_fetch(&r->ws1, r->st));
     NS_CUDA_TRY(cudaStreamSynchronize(r->st));
-    if (const int bits = workspace_err_bits(&r->ws)) {
+    if (const int bits = workspace_err_bits(&r->ws) | (r->n_groups > 1 ? workspace_err_bits(&r->ws1) : 0)) {
         r->h_sc->status |= bits;
         return NS_ETIMEOUT;
     }
     return NS_OK;
 }
 
-static int launch_round(ns_run* r, cudaStream_t st, const StageProbe* probe) {
-    NS_CUDA_TRY(launch_pdl(k_set_int, dim3(1), dim3(1), 0, st, &r->sc->batch, 0));
-    NS_CUDA_TRY(launch_pdl(k_slice_advance, dim3((r->k + 7) / 8), dim3(256), 0, st, r->rd));
-    return run_likelihood(r->p, &r->ws, r->k, r->ws.logL, nullptr, st, probe);
+static int launch_round(ns_run* r, int g, cudaStream_t st, const StageProbe* probe) {
+    Workspace* ws = g ? &r->ws1 : &r->ws;
+    NS_CUDA_TRY(launch_pdl(k_set_int, dim3(1), dim3(1), 0, st, r->grd[g].batch_ctr, 0));
+    NS_CUDA_TRY(launch_pdl(k_slice_advance, dim3((r->grd[g].grp_chains + 7) / 8), dim3(256), 0, st, r->grd[g]));
+    return run_likelihood(r->p, ws, r->grd[g].grp_chains, ws->logL, nullptr, st, probe);
+}
+
+// Per-group copies of the run state for the round kernels (rebuilt with the
+// graph, since the dead-list pointers in rd change when it grows).
+static void refresh_groups(ns_run* r) {
+    r->grd[0] = r->rd;
+    r->grd[0].chain0 = 0;
+    r->grd[0].grp_chains = r->n_groups > 1 ? r->k0 : r->k;
+    if (r->n_groups > 1) {
+        RunDev& g1 = r->grd[1];
+        g1 = r->rd;
+        g1.chain0 = r->k0;
+        g1.grp_chains = r->k - r->k0;
+        g1.batch_ctr = r->ws1.d_nrows;
+        g1.logL = r->ws1.logL;
+        g1.theta_full = r->ws1.theta_full;
+        g1.prop = r->rd.prop + (size_t)r->k0 * r->d;   // disjoint rows of the proposal buffer
+    }
 }
 
 static int build_graph(ns_run* r, int rounds) {
     if (r->graph) { cudaGraphExecDestroy(r->graph); r->graph = nullptr; }
+    refresh_groups(r);
     cudaGraph_t g;
+    int lo = 0, hi = 0;
+    NS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     if (!r->cap_st) {
         // the round's main chain at the highest priority, so the emulator GEMMs
         // are scheduled ahead of the windows stage running beside them
-        int lo = 0, hi = 0;
-        NS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
         NS_CUDA_TRY(cudaStreamCreateWithPriority(&r->cap_st, cudaStreamNonBlocking, hi));
+    }
+    if (r->n_groups > 1 && !r->cap_st1) {
+        NS_CUDA_TRY(cudaStreamCreateWithPriority(&r->cap_st1, cudaStreamNonBlocking, hi));
+        NS_CUDA_TRY(cudaEventCreateWithFlags(&r->ev_gfork, cudaEventDisableTiming));
+        NS_CUDA_TRY(cudaEventCreateWithFlags(&r->ev_gjoin, cudaEventDisableTiming));
     }
     NS_CUDA_TRY(cudaStreamBeginCapture(r->cap_st, cudaStreamCaptureModeThreadLocal));
     int s = NS_OK;
+    if (r->n_groups > 1) {
+        // the two groups' rounds are independent chains of kernels on two streams
+        if (cudaEventRecord(r->ev_gfork, r->cap_st) != cudaSuccess ||
+            cudaStreamWaitEvent(r->cap_st1, r->ev_gfork, 0) != cudaSuccess)
+            s = NS_ECUDA;
+    }
     for (int i = 0; i < rounds && s == NS_OK; ++i)
-        s = launch_round(r, r->cap_st, (i == 0 && r->probe.stage != PROBE_NONE) ? &r->probe : nullptr);
+        s = launch_round(r, 0, r->cap_st, (i == 0 && r->probe.stage != PROBE_NONE) ? &r->probe : nullptr);
+    if (r->n_groups > 1) {
+        for (int i = 0; i < rounds && s == NS_OK; ++i) s = launch_round(r, 1, r->cap_st1, nullptr);
+        if (s == NS_OK && (cudaEventRecord(r->ev_gjoin, r->cap_st1) != cudaSuccess ||
+                           cudaStreamWaitEvent(r->cap_st, r->ev_gjoin, 0) != cudaSuccess))
+            s = NS_ECUDA;
+    }
     cudaError_t e = cudaStreamEndCapture(r->cap_st, &g);
     if (s != NS_OK) { if (e == cudaSuccess) cudaGraphDestroy(g); return s; }
     NS_CUDA_TRY(e);
@@ -773,6 +821,10 @@ static void run_release(ns_run* r) {
     for (void* q : r->owned) cudaFree(q);
     if (r->h_sc) cudaFreeHost(r->h_sc);
     workspace_free(&r->ws);
+    workspace_free(&r->ws1);
+    if (r->cap_st1) cudaStreamDestroy(r->cap_st1);
+    if (r->ev_gfork) cudaEventDestroy(r->ev_gfork);
+    if (r->ev_gjoin) cudaEventDestroy(r->ev_gjoin);
     delete r;
 }
 
@@ -839,6 +891,8 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
     rd.prop_stride = d;
     rd.batch_ctr = &rd.sc->batch;
     rd.run_id = 0;
+    rd.chain0 = 0;
+    rd.grp_chains = k;
     rd.P = p->P;
     rd.pkind = p->d_pkind;
     rd.pa = p->d_pa;
@@ -853,6 +907,14 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
     if ((s = grow_dead(r, 16LL * k + n))) return fail(s);
     // the workspace row count is the round's batch counter
     r->ws.d_nrows = &rd.sc->batch;
+    // two groups of chains whose rounds overlap on the GPU (the shear
+    // likelihood's tensor-core and FP32 stages then run side by side)
+    const int want = cfg->chain_groups;
+    r->n_groups = (k >= 2 && (want == 2 || (want <= 0 && k >= 128 && p->kind == NS_KIND_SHEAR))) ? 2 : 1;
+    if (r->n_groups > 1) {
+        r->k0 = (k + 1) / 2;
+        if ((s = workspace_create(p, k - r->k0, &r->ws1))) return fail(s);
+    }
     // initial live points
     k_init_points<<<(n + 127) / 128, 128, 0, r->st>>>(n, d, cfg->seed, rd.prop);
     k_set_int<<<1, 1, 0, r->st>>>(&rd.sc->batch, n);
@@ -1131,7 +1193,9 @@ extern "C" int ns_multi_init(const ns_problem* const* problems, int n_runs, cons
     std::vector<int> off(n_runs + 1, 0);
     for (int i = 0; i < n_runs; ++i) {
         ns_run* r = nullptr;
-        int s = ns_init(problems[i], &cfgs[i], stream, &r);
+        ns_config ci = cfgs[i];
+        ci.chain_groups = 1;      // packed runs share one batch instead
+        int s = ns_init(problems[i], &ci, stream, &r);
         if (s) return fail(s);
         m->runs.push_back(r);
         m->stride = std::max(m->stride, r->d);

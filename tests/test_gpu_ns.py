@@ -76,6 +76,34 @@ def test_bookkeeping_shear_tiny_batched():
     _compare_iterations(ons, run, 2)
 
 
+def test_bookkeeping_two_chain_groups():
+    """Chains split into two groups whose rounds run on two streams: the
+    bookkeeping is still the oracle's (each chain's proposals and likelihoods
+    do not depend on which batch scores them)."""
+    from paper_2509_13307_gb300 import NestedRun
+    inp, orc = oracle_for("shear_tiny")
+    sc = w.shear_tiny(repeats=6).sampler
+    prob = cuda_problem("shear_tiny", "fp64", max_batch=sc.n_live)
+    ons = NestedSampler.from_config(orc.loglike_cube, prob.d, sc)
+    ons.initialise()
+    run = NestedRun.from_config(prob, sc, chain_groups=2)
+    _compare_iterations(ons, run, 2)
+
+
+def test_chain_groups_bf16_identical():
+    """BF16: one and two chain groups give bit-identical runs."""
+    from paper_2509_13307_gb300 import NestedRun
+    sc = w.shear_tiny(repeats=4).sampler
+    prob = cuda_problem("shear_tiny", "bf16", max_batch=sc.n_live)
+    r1 = NestedRun.from_config(prob, sc, chain_groups=1)
+    r2 = NestedRun.from_config(prob, sc, chain_groups=2)
+    s1, s2 = r1.step(3), r2.step(3)
+    x1, l1 = r1.live_points()
+    x2, l2 = r2.live_points()
+    assert np.array_equal(x1, x2) and np.array_equal(l1, l2)
+    assert s1.logZ == s2.logZ and s1.evaluations == s2.evaluations
+
+
 def test_full_run_matches_oracle():
     """Both samplers to convergence: same number of dead points, log Z, H and
     the simulated-shrinkage error (same Philox replays)."""
