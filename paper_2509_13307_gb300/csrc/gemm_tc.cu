@@ -90,9 +90,9 @@ __device__ __forceinline__ float tanh_fast(float x) {
 
 template <int BN>
 struct Cfg {
-    // as many stages as fit in ~200 KB of shared memory (more bytes in flight
-    // hide the TMA latency; the tiles here are L2-resident)
-    static constexpr int STAGES = (BN >= 256) ? 4 : (BN >= 128 ? 6 : 8);
+    // narrow (hidden-layer) tiles keep 4 stages (80 KB) so that a GEMM CTA
+    // fits on an SM beside two Limber CTAs of the other chain group
+    static constexpr int STAGES = (BN >= 256) ? 4 : (BN >= 128 ? 6 : 4);
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -244,7 +244,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 // and for every row the 32 lanes of a warp store 32 consecutive features.
 template <int BR>
 struct CfgS {
-    static constexpr int STAGES = 4;
+    static constexpr int STAGES = 2;   // 96 KB: leaves room for other kernels' CTAs on the SM
     static constexpr int A_BYTES = 128 * BK * 2;
     static constexpr int B_BYTES = BR * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
