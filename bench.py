@@ -335,7 +335,8 @@ def ours(args):
     res = timed_steps(prob, args.warmup, args.steps, profile="projection")
     clk = clocks.stop()
 
-    t_job, ev_job = job_totals(res["ms"] / 1e3, res["evals"], world, dev)
+    t_local, ev_local = res["ms"] / 1e3, res["evals"]
+    t_job, ev_job = job_totals(t_local, ev_local, world, dev)
     value = ev_job / t_job
 
     # per round: slice, prior transform, windows, emulator input layer, one
