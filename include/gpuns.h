@@ -123,13 +123,27 @@ typedef struct {
     const double* tmpl;           /* n_data x n_tmpl noise templates (may be NULL if n_tmpl = 0) */
 } ns_shear_desc;
 
-/* CMB-like Gaussian likelihood (Sec. 3.1 test problem, dense-covariance form):
- * the model is the emulator output itself (TT, TE, EE stacked, D = dims[n_layers]),
- * inputs = the full parameter vector; log L = -1/2 |L^-1 (d - m)|^2 + c0.
- * The emulator's last layer must be linear (it always is: the head has no
- * activation).  Precisions FP64, FP32 and BF16 (hidden layers on tensor cores,
- * head and chi^2 in FP32); LITERAL needs FP64. */
-typedef struct { int solve; } ns_cmb_desc;
+/* CMB problem kind (Sec. 3.1).  The model is the emulator output itself (TT,
+ * TE, EE stacked, dims[n_layers] values), inputs = the full parameter vector;
+ * the emulator's last layer is linear.  Two likelihood forms:
+ *   NS_CMB_GAUSS (dense covariance): log L = -1/2 |L^-1 (d - m)|^2 + c0 with
+ *     d and cov of length D = dims[n_layers]; `solve` as above.
+ *   NS_CMB_TT_CV (the paper's cosmic-variance-limited TT analysis, Sec. 3.1):
+ *     for each of the first n_tt outputs (multipoles ell[i]), k = 2 ell + 1 and
+ *     k d_ell / C_ell(theta) follows a chi-squared law with k degrees of
+ *     freedom; log L = sum_ell [ln f_chi2(k d / C; k) + ln(k / C)], i.e. the
+ *     density of d_ell given C_ell.  data = the n_tt observed TT values
+ *     (n_data = n_tt), cov = NULL.
+ * Precisions FP64, FP32 and BF16 (hidden layers on tensor cores, head and the
+ * likelihood sums in FP32, constants and the final sum in FP64); LITERAL
+ * needs FP64. */
+enum ns_cmb_form { NS_CMB_GAUSS = 0, NS_CMB_TT_CV = 1 };
+typedef struct {
+    int solve;                    /* ns_cmb_solve (NS_CMB_GAUSS only) */
+    int form;                     /* ns_cmb_form */
+    int n_tt;                     /* NS_CMB_TT_CV: TT multipoles = the first n_tt emulator outputs */
+    const double* ell;            /* NS_CMB_TT_CV: their multipoles (n_tt values) */
+} ns_cmb_desc;
 
 /* Isotropic Gaussian test likelihood on the cube: log L = -1/2 |(x - mu)/sigma|^2 - d ln(sigma sqrt(2 pi)). */
 typedef struct { double mu; double sigma; } ns_gauss_desc;
@@ -143,7 +157,8 @@ typedef struct {
     const double* data;           /* D */
     const double* cov;            /* D x D symmetric positive definite; factorised in FP64.
                                      data and cov may both be NULL: a model-only problem whose
-                                     loglike calls fail with NS_EINVAL */
+                                     loglike calls fail with NS_EINVAL (the CMB TT_CV form takes
+                                     data and no covariance) */
     ns_emulator_desc emu;
     ns_shear_desc shear;
     ns_gauss_desc gauss;
@@ -225,6 +240,12 @@ int ns_model_batch(const ns_problem* p, const double* theta_dev, int B,
  * NS_EINVAL for the GAUSS kind. */
 int ns_emulator_batch(const ns_problem* p, const double* theta_dev, int B,
                       double* out_dev, void* stream);
+
+/* BF16 problems: the N-tile width of every tensor-core layer (0 for layers on
+ * CUDA cores) and, for the hidden layers, the time per launch [ms] the tile
+ * autotuner measured at creation on min(max_batch, 512) rows; ms may be NULL.
+ * n >= the number of emulator layers. */
+int ns_problem_tiles(const ns_problem* p, int* tile_n, float* ms, int n);
 
 /* Device status bits of the problem's batch calls (NS_BIT_TIMEOUT: a bounded
  * device wait inside a likelihood kernel gave up; the affected rows are NaN).

@@ -10,11 +10,18 @@ Steps, each following the cited passage:
               Inputs are the 6 parameters standardised over the prior box.
   model       m(theta) = the emulator output (TT, TE, EE stacked).
   loglike     Gaussian: -1/2 |L^-1 (d - m)|^2 - sum ln L_aa - D/2 ln 2 pi, the
-              whitening by explicit forward substitution (no fast algebra).
+              whitening by explicit forward substitution (no fast algebra);
+              or, for the cosmic-variance-limited TT analysis of Sec. 3.1
+              (form "tt_cv"), the density of the observed d_ell given
+              C_ell(theta) when k d_ell / C_ell is chi-squared with
+              k = 2 ell + 1 degrees of freedom:
+              ln L = sum_ell [ln f_k(k d / C) + ln(k / C)],
+              ln f_k(x) = (k/2 - 1) ln x - x/2 - (k/2) ln 2 - ln Gamma(k/2).
 
 Mock data and covariance: C = s W with W the seeded Wishart-style base of the
 workload inputs and s setting the mean variance to (cov_rel * rms m_fid)^2;
-data = m_fid + L eps.
+data = m_fid + L eps.  TT mock: d_ell = C_fid,ell X_ell / k_ell with the seeded
+chi-squared draws X_ell of the workload inputs.
 """
 
 from __future__ import annotations
@@ -31,14 +38,29 @@ def sigmoid_linear(x, g, beta):
     return (g + (1.0 - g) / (1.0 + np.exp(-beta * x))) * x
 
 
+def chi2_logpdf(x, k):
+    """ln of the chi-squared density with k degrees of freedom at x > 0."""
+    return (0.5 * k - 1.0) * math.log(x) - 0.5 * x - 0.5 * k * math.log(2.0) - math.lgamma(0.5 * k)
+
+
 class CMBOracle:
-    def __init__(self, inp: dict, data=None, cov=None, wishart=None):
+    def __init__(self, inp: dict, data=None, cov=None, wishart=None, form: str = "gauss"):
         self.inp = inp
         self.priors = inp["priors"]
         self.D = int(inp["n_data"])
+        self.form = form
+        if form == "tt_cv":
+            self.n_tt = len(inp["ell"])
+            self.k = 2.0 * np.asarray(inp["ell"], float) + 1.0
+            self.data = np.asarray(data, float) if data is not None else self.make_mock_tt()
+            return
         if data is None or cov is None:
             data, cov = self.make_mock(wishart)
         self.set_data(data, cov)
+
+    def make_mock_tt(self):
+        cfid = self.model(np.asarray(self.inp["fiducial"], float))[: self.n_tt]
+        return cfid * self.inp["tt_chi2"] / self.k
 
     # ----------------------------------------------------------- emulator
     @staticmethod
@@ -110,7 +132,13 @@ class CMBOracle:
         y = self.whitened(theta)
         return float(np.sum(y * y))
 
+    def loglike_tt(self, theta):
+        C = self.model(theta)[: self.n_tt]
+        return float(sum(chi2_logpdf(k * d / c, k) + math.log(k / c) for k, d, c in zip(self.k, self.data, C)))
+
     def loglike_full(self, theta):
+        if self.form == "tt_cv":
+            return self.loglike_tt(theta)
         return -0.5 * self.chi2(theta) + self.c0
 
     def loglike(self, theta_free):

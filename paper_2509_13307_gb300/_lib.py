@@ -14,11 +14,12 @@ NS_BIT_SLICE_CAP, NS_BIT_NONFINITE, NS_BIT_TIMEOUT = 1, 2, 4
 NS_KIND_GAUSS, NS_KIND_SHEAR, NS_KIND_CMB = 0, 1, 2
 NS_ACT = {"tanh": 0, "sigmoid_linear": 1}
 NS_SOLVE = {"fold": 0, "literal": 1}
+NS_CMB_FORM = {"gauss": 0, "tt_cv": 1}
 NS_PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16_f64chi2": 3}
 NS_PRIOR = {"U": 0, "N": 1, "F": 2}
 
 EXPORTS = ["ns_strerror", "ns_problem_create", "ns_problem_free", "ns_problem_dim", "ns_prior_transform",
-           "loglike_batch", "ns_model_batch", "ns_emulator_batch", "ns_problem_status", "loglike_grad_batch", "ns_init", "ns_step", "ns_evidence",
+           "loglike_batch", "ns_model_batch", "ns_emulator_batch", "ns_problem_status", "ns_problem_tiles", "loglike_grad_batch", "ns_init", "ns_step", "ns_evidence",
            "ns_live_points", "ns_dead_points", "ns_last_iteration", "ns_profile_stage", "ns_profile_read",
            "ns_evidence_noalloc", "ns_multi_init", "ns_multi_step", "ns_multi_run",
            "ns_multi_free", "ns_free"]
@@ -52,7 +53,7 @@ class GaussDesc(C.Structure):
 
 
 class CmbDesc(C.Structure):
-    _fields_ = [("solve", C.c_int)]
+    _fields_ = [("solve", C.c_int), ("form", C.c_int), ("n_tt", C.c_int), ("ell", C.POINTER(C.c_double))]
 
 
 class ProblemDesc(C.Structure):
@@ -98,6 +99,7 @@ def load():
     lib.ns_model_batch.argtypes = [vp, vp, C.c_int, vp, vp]
     lib.ns_emulator_batch.argtypes = [vp, vp, C.c_int, vp, vp]
     lib.ns_problem_status.argtypes = [vp, C.POINTER(C.c_int), C.c_int]
+    lib.ns_problem_tiles.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_float), C.c_int]
     lib.loglike_grad_batch.argtypes = [vp, vp, C.c_int, vp, vp, vp]
     lib.ns_init.argtypes = [vp, C.POINTER(Config), vp, C.POINTER(vp)]
     lib.ns_step.argtypes = [vp, C.c_int, C.POINTER(Status)]

@@ -101,3 +101,28 @@ def test_bf16_rounding_matches_torch():
     x = np.random.default_rng(8).standard_normal(4096) * 10.0 ** np.random.default_rng(9).uniform(-3, 3, 4096)
     ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(CMBOracle.to_bf16(x), ref)
+
+
+def test_tt_cosmic_variance_form():
+    """The TT form: chi-squared log density against scipy, the closed form
+    -(k/2)(d/C + ln C) + const, and its maximum at C = d for every multipole."""
+    from scipy import stats
+    from oracle.cmb import chi2_logpdf
+    for k, x in ((5.0, 3.2), (41.0, 47.5), (2001.0, 1987.0)):
+        assert chi2_logpdf(x, k) == pytest.approx(stats.chi2.logpdf(x, k), rel=1e-12)
+    inp = w.make_cmb_inputs(w.cmb_tiny())
+    o = CMBOracle(inp, form="tt_cv")
+    th = np.array(inp["fiducial"]) * 1.01
+    C = o.model(th)[: o.n_tt]
+    k, d = o.k, o.data
+    const = np.sum((0.5 * k - 1) * np.log(k * d) - 0.5 * k * np.log(2.0)
+                   - np.array([math.lgamma(0.5 * q) for q in k]) + np.log(k))
+    closed = const - np.sum(0.5 * k * (d / C + np.log(C)))
+    assert o.loglike_full(th) == pytest.approx(closed, rel=1e-12)
+    # each term is maximised at C = d: d/dC [-(k/2)(d/C + ln C)] = (k/2)(d/C^2 - 1/C) = 0
+    for j in range(3):
+        f = lambda c: -(0.5 * k[j]) * (d[j] / c + math.log(c))
+        assert f(d[j]) > f(d[j] * 1.001) and f(d[j]) > f(d[j] * 0.999)
+    # mock: d = C_fid X / k with the seeded chi-squared draws
+    cfid = o.model(np.asarray(inp["fiducial"]))[: o.n_tt]
+    assert np.allclose(d * k / cfid, inp["tt_chi2"], rtol=1e-13)

@@ -135,6 +135,8 @@ def make_cmb_inputs(cfg: CMBConfig) -> dict:
     D = cfg.n_data
     rng_n = np.random.default_rng(cfg.seed_noise)
     noise_eps = rng_n.standard_normal(D)
+    # cosmic-variance TT mock: k d_ell / C_ell ~ chi^2 with k = 2 ell + 1
+    tt_chi2 = rng_n.chisquare(2.0 * ell + 1.0)
     nu = cfg.nu_factor * D
     return dict(kind="cmb", name=cfg.name, n_params=6, priors=priors,
                 fiducial=np.array(cfg.fiducial), emu_W=Ws, emu_b=bs,
@@ -142,7 +144,7 @@ def make_cmb_inputs(cfg: CMBConfig) -> dict:
                 emu_inputs=np.arange(6), emu_in_center=centers, emu_in_scale=scales,
                 emu_out_mu=mu, emu_out_sig=sig, ell=ell, n_data=D,
                 noise_eps=noise_eps, wishart_nu=nu, seed_cov=cfg.seed_cov,
-                cov_rel=0.1)
+                cov_rel=0.1, tt_chi2=tt_chi2)
 
 
 _WISHART_CACHE: dict = {}
