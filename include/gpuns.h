@@ -121,6 +121,9 @@ typedef struct {
     double c1rho;                 /* C_1 rho_cr (Eq. 6) */
     int n_tmpl;
     const double* tmpl;           /* n_data x n_tmpl noise templates (may be NULL if n_tmpl = 0) */
+    int z_interp;                 /* coarse emulator z -> table z (n_z_emu < n_z): 0 Catmull-Rom
+                                     (4 taps), 1 linear between the bracketing coarse nodes (the
+                                     paper's interpolated P(k), App. B) */
 } ns_shear_desc;
 
 /* CMB problem kind (Sec. 3.1).  The model is the emulator output itself (TT,

@@ -210,11 +210,17 @@ class ShearOracle:
         return P
 
     def zinterp(self, Tc):
-        """Coarse-z emulator table -> the n_z table by Catmull-Rom in z (coarse grid
-        uniform on [0, z_max])."""
+        """Coarse-z emulator table -> the n_z table (coarse grid uniform on
+        [0, z_max]): Catmull-Rom in z, or linear between the bracketing coarse
+        nodes (inp["z_interp"] == "linear", the paper's interpolated P(k))."""
         nzc = Tc.shape[0]
-        P = self.pad_table(Tc)[:, 1:-1]
         zf = np.linspace(0.0, self.z_max, self.n_z)
+        if self.inp.get("z_interp", "catmull_rom") == "linear":
+            u = zf / (self.z_max / (nzc - 1))
+            i = np.clip(np.floor(_re(u)).astype(int), 0, nzc - 2)
+            t = u - i
+            return (1.0 - t)[:, None] * Tc[i] + t[:, None] * Tc[i + 1]
+        P = self.pad_table(Tc)[:, 1:-1]
         j, t = self.bracket(zf, 0.0, self.z_max / (nzc - 1), nzc)
         w = self.catmull_rom_weights(t)
         out = np.zeros((self.n_z, self.n_k), dtype=Tc.dtype)

@@ -45,7 +45,7 @@ class ShearDesc(C.Structure):
                 ("n_k", C.c_int), ("lnk_min", C.c_double), ("lnk_max", C.c_double),
                 ("n_z", C.c_int), ("z_max", C.c_double), ("n_z_emu", C.c_int),
                 ("n_chi", C.c_int), ("a_min", C.c_double), ("ia_pivot", C.c_double), ("c1rho", C.c_double),
-                ("n_tmpl", C.c_int), ("tmpl", C.POINTER(C.c_double))]
+                ("n_tmpl", C.c_int), ("tmpl", C.POINTER(C.c_double)), ("z_interp", C.c_int)]
 
 
 class GaussDesc(C.Structure):

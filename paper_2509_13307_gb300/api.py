@@ -37,17 +37,20 @@ class Problem:
     """A likelihood problem resident on the current CUDA device."""
 
     def __init__(self, inp: dict, precision: str = "fp64", max_batch: int = 1024, data=None, cov=None,
-                 solve: str = "fold"):
+                 solve: str = "fold", form: str = "gauss"):
         self.lib = L.load()
         self.inp = inp
         self.kind = inp["kind"]
         self.precision = precision
         self.max_batch = int(max_batch)
         self.solve = solve
+        self.form = form
         self._h = C.c_void_p()
         if self.kind == "shear" and (data is None or cov is None):
             data, cov = self._make_mock()
-        elif self.kind == "cmb" and (data is None or cov is None):
+        elif self.kind == "cmb" and form == "tt_cv" and data is None:
+            data = self._make_mock_tt()
+        elif self.kind == "cmb" and form != "tt_cv" and (data is None or cov is None):
             data, cov = self._make_mock_cmb()
         self.data = None if data is None else np.ascontiguousarray(data, dtype=np.float64)
         self.cov = None if cov is None else np.ascontiguousarray(cov, dtype=np.float64)
@@ -84,6 +87,19 @@ class Problem:
                                   inp["sigma_e"] ** 2 / inp["n_gal_sr"], inp["cov_V"], inp["cov_rank_amp"])
         data = mfid + np.linalg.cholesky(cov) @ inp["noise_eps"]
         return data, cov
+
+    def _make_mock_tt(self):
+        """Cosmic-variance TT mock: d_ell = C_fid,ell X_ell / (2 ell + 1) with the
+        seeded chi-squared draws X_ell and the library's FP64 fiducial spectra."""
+        inp = self.inp
+        form, self.form = self.form, "gauss"
+        self._create("fp64", 1, None, None, None)
+        self.form = form
+        th = torch.tensor(np.asarray(inp["fiducial"], float)[None, :], dtype=torch.float64, device="cuda")
+        mfid = self.model(th)[0].cpu().numpy()
+        self._free()
+        n = len(inp["ell"])
+        return mfid[:n] * inp["tt_chi2"] / (2.0 * np.asarray(inp["ell"], float) + 1.0)
 
     def _make_mock_cmb(self):
         """C = s W (seeded Wishart base, s from the library's FP64 fiducial
@@ -159,6 +175,14 @@ class Problem:
                 e.out_sigma = 1.0
                 e.out_sigma_vec = _dptr(sv)
                 desc.cmb.solve = L.NS_SOLVE[self.solve]
+                desc.cmb.form = L.NS_CMB_FORM[self.form]
+                if self.form == "tt_cv":
+                    ell = np.ascontiguousarray(inp["ell"], dtype=np.float64)
+                    keep.append(ell)
+                    desc.cmb.n_tt = len(ell)
+                    desc.cmb.ell = _dptr(ell)
+                    desc.n_data = len(ell) if data is not None else 0
+                    desc.cov = C.POINTER(C.c_double)()
                 h = C.c_void_p()
                 L.check(self.lib.ns_problem_create(C.byref(desc), C.byref(h)), "ns_problem_create")
                 self._h = h
@@ -185,6 +209,7 @@ class Problem:
             s.ia_pivot = inp["ia_pivot"]
             s.c1rho = inp["c1rho"]
             s.n_tmpl = inp["n_tmpl"]
+            s.z_interp = {"catmull_rom": 0, "linear": 1}[inp.get("z_interp", "catmull_rom")]
             if inp["n_tmpl"]:
                 t = np.ascontiguousarray(tmpl, dtype=np.float64)
                 keep.append(t)
@@ -239,6 +264,14 @@ class Problem:
         L.check(self.lib.ns_emulator_batch(self._h, C.c_void_p(theta.data_ptr()), B, C.c_void_p(out.data_ptr()),
                                            _stream(stream)), "ns_emulator_batch")
         return out
+
+    def tiles(self):
+        """BF16: (N-tile width per layer, autotuned time per launch [ms]) of the tensor-core layers."""
+        n = len(self.inp["emu_W"])
+        t = (C.c_int * n)()
+        ms = (C.c_float * n)()
+        L.check(self.lib.ns_problem_tiles(self._h, t, ms, n), "ns_problem_tiles")
+        return list(t), list(ms)
 
     def device_status(self, clear: bool = False) -> int:
         """Status bits of earlier batch calls (NS_BIT_TIMEOUT = 4: a bounded

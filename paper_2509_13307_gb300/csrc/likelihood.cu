@@ -276,6 +276,7 @@ struct Head {
     const void* sig_vec;
     double sigma;
     void* out;
+    int n_out = 0;           // outputs computed (the first rows of W); 0: all
 };
 
 static Head model_head(const ns_problem* p, void* out) {
@@ -298,7 +299,7 @@ static int run_emulator_simt(const ns_problem* p, Workspace* ws, int grid_rows, 
         if (l == L - 1) {
             NS_TRY((launch_gemm_simt<T, T>((const T*)ws->act[cur], (const T*)hd.W, (const T*)hd.bias, ActDev<T>{0, nullptr, nullptr},
                                            (const T*)hd.mu, (const T*)hd.sig_vec, (T)hd.sigma, (T*)hd.out,
-                                           ws->d_nrows, grid_rows, N, K, EPI_OUT, st)));
+                                           ws->d_nrows, grid_rows, hd.n_out ? hd.n_out : N, K, EPI_OUT, st)));
         } else {
             NS_TRY((launch_gemm_simt<T, T>((const T*)ws->act[cur], (const T*)p->d_W[l], (const T*)p->d_b[l],
                                            layer_act<T>(p, l), nullptr, nullptr, T(0), (T*)ws->act[cur ^ 1],
@@ -344,7 +345,8 @@ static int run_emulator_bf16(const ns_problem* p, Workspace* ws, int grid_rows, 
             NS_TRY((launch_gemm_simt<float, __nv_bfloat16>(
                 (const __nv_bfloat16*)ws->act[cur], (const float*)hd->W, (const float*)hd->bias,
                 ActDev<float>{0, nullptr, nullptr}, (const float*)hd->mu, (const float*)hd->sig_vec,
-                (float)hd->sigma, (float*)hd->out, ws->d_nrows, grid_rows, N, K, EPI_OUT, st)));
+                (float)hd->sigma, (float*)hd->out, ws->d_nrows, grid_rows, hd->n_out ? hd->n_out : N, K, EPI_OUT,
+                st)));
         } else if (last && p->tile_n[l] == 128) {
             // the output layer with few rows: features as the MMA's M (one wave of CTAs)
             NS_TRY(launch_gemm_tc_out_swap(&p->tmB[l], &ws->tmX_out, (const float*)p->d_b[l],
@@ -393,6 +395,31 @@ __global__ void __launch_bounds__(256) k_rowsq(const T* __restrict__ y, int D, d
     if (threadIdx.x == 0) logL[row] = c0 - 0.5 * part[0];
 }
 
+// Cosmic-variance TT log L per row: c0 - sum_ell (k/2) g(C_ell / d_ell) with
+// g(r) = ln r + 1/r - 1 = log1p(u) - u / (1 + u), u = r - 1 (no cancellation
+// near the peak); partial sums widened to FP64 in a fixed-order block tree.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cmb_tt(const T* __restrict__ C, int n_tt, int ld, const T* __restrict__ dobs,
+                                                const T* __restrict__ halfk, double c0, double* __restrict__ logL,
+                                                const int* __restrict__ nrows) {
+    const int row = blockIdx.x;
+    if (row >= *nrows) return;
+    __shared__ double part[256];
+    const T* c = C + (size_t)row * ld;
+    T s = T(0);
+    for (int i = threadIdx.x; i < n_tt; i += 256) {
+        const T u = c[i] / dobs[i] - T(1);
+        s += halfk[i] * (log1p(u) - u / (T(1) + u));
+    }
+    part[threadIdx.x] = (double)s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) logL[row] = c0 - part[0];
+}
+
 int run_emulator_only(const ns_problem* p, Workspace* ws, int grid_rows, double* out, cudaStream_t st) {
     if (grid_rows <= 0) return NS_OK;
     const int n_out = p->dims.back();
@@ -419,6 +446,25 @@ static int run_cmb(const ns_problem* p, Workspace* ws, int grid_rows, double* lo
     const int D = p->D;
     if (model_out) return run_emulator_only(p, ws, grid_rows, model_out, st);
     const bool f64 = p->precision == NS_PREC_FP64;
+    if (p->cmb_form == NS_CMB_TT_CV) {
+        // the TT block of the head only (the first n_tt outputs), then the sums
+        Head hd = model_head(p, ws->table);
+        hd.n_out = p->n_tt;
+        if (f64) NS_TRY(run_emulator_simt<double>(p, ws, grid_rows, st, hd));
+        else if (p->precision == NS_PREC_FP32) NS_TRY(run_emulator_simt<float>(p, ws, grid_rows, st, hd));
+        else NS_TRY(run_emulator_bf16(p, ws, grid_rows, st, probe, &hd));
+        NS_TRY(probe_begin(probe, PROBE_CHI2, ws, st));
+        if (f64)
+            k_cmb_tt<double><<<grid_rows, 256, 0, st>>>((const double*)ws->table, p->n_tt, p->n_tt,
+                                                        (const double*)p->d_tt_obs, (const double*)p->d_tt_halfk,
+                                                        p->c0, logL_out, ws->d_nrows);
+        else
+            k_cmb_tt<float><<<grid_rows, 256, 0, st>>>((const float*)ws->table, p->n_tt, p->n_tt,
+                                                       (const float*)p->d_tt_obs, (const float*)p->d_tt_halfk,
+                                                       p->c0, logL_out, ws->d_nrows);
+        NS_CUDA_TRY(cudaGetLastError());
+        return probe_end(probe, PROBE_CHI2, st);
+    }
     if (p->cmb_solve == NS_SOLVE_LITERAL) {
         const int L = p->n_layers;
         const Head hd{p->d_W[L - 1], p->d_b[L - 1], p->d_lit_mu, p->d_lit_sig, 0.0, ws->resid};

@@ -75,7 +75,8 @@ struct ns_problem {
     std::vector<void*> d_W;          // per layer, compute dtype (layer 0: FP64 or FP32)
     std::vector<void*> d_b;          // per layer, FP64 (FP64 mode) else FP32
     std::vector<CUtensorMap> tmB;    // BF16: weight tensor maps for layers >= 1
-    std::vector<int> tile_n;         // BF16: N tile per layer (autotuned)
+    std::vector<int> tile_n;         // BF16: N tile per layer (hidden layers autotuned at creation)
+    std::vector<float> tile_ms;      // BF16: measured time per launch of the chosen hidden tiles
     int* d_inputs = nullptr;
     double* d_in_center = nullptr;
     double* d_in_scale = nullptr;
@@ -103,6 +104,10 @@ struct ns_problem {
     void* d_zeroD = nullptr;         // D zeros: bias of the folded head
     double* d_lit_mu = nullptr;      // LITERAL: d - mu
     double* d_lit_sig = nullptr;     // LITERAL: -sigma
+    int cmb_form = 0;                // ns_cmb_form
+    int n_tt = 0;                    // TT_CV: multipoles (the first n_tt outputs)
+    void* d_tt_obs = nullptr;        // TT_CV: observed d_ell (compute dtype)
+    void* d_tt_halfk = nullptr;      // TT_CV: k/2 = ell + 1/2 (compute dtype)
     std::vector<void*> owned;
     gpuns::Workspace ws;             // scratch of loglike_batch / ns_model_batch
 };

@@ -118,9 +118,9 @@ int workspace_create(const ns_problem* p, int cap, Workspace* ws) {
             ws->act[i] = v;
             NS_CUDA_TRY(cudaMemset(v, 0, (size_t)elt * rows_pad * p->hidden_max));
         }
-        NS_TRY(dalloc((size_t)tab_elt * cap * p->D, &v, ws->owned));
+        NS_TRY(dalloc((size_t)tab_elt * cap * std::max(p->D, p->dims.back()), &v, ws->owned));
         ws->table = v;
-        if (p->cmb_solve == NS_SOLVE_LITERAL) {
+        if (p->cmb_solve == NS_SOLVE_LITERAL && p->cmb_form == NS_CMB_GAUSS) {
             NS_TRY(dalloc(sizeof(double) * (size_t)cap * p->D, &v, ws->owned));
             ws->resid = v;
             NS_TRY(dalloc(sizeof(double) * (size_t)cap * ((p->D + 63) / 64), &v, ws->owned));
@@ -217,7 +217,26 @@ static int upload_compute(const ns_problem* p, const double* h, size_t n, void**
 // W' = L^-1 diag(sigma) W_out, c' = L^-1 (d - mu - sigma b_out).
 static int cmb_setup(ns_problem* p, const ns_problem_desc* desc) {
     p->cmb_solve = desc->cmb.solve;
+    p->cmb_form = desc->cmb.form;
     if (!p->has_lik) return NS_OK;
+    if (p->cmb_form == NS_CMB_TT_CV) {
+        // log L = c0 - sum_ell (k/2) g(C / d),  g(r) = ln r + 1/r - 1, with
+        // c0 = sum_ell [(k/2 - 1) ln(k d) - (k/2) ln 2 - ln Gamma(k/2) + ln k - (k/2)(ln d + 1)]
+        const int n = desc->cmb.n_tt;
+        p->n_tt = n;
+        std::vector<double> hk(n);
+        double c0 = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const double k = 2.0 * desc->cmb.ell[i] + 1.0, d = desc->data[i];
+            hk[i] = 0.5 * k;
+            c0 += (0.5 * k - 1.0) * std::log(k * d) - 0.5 * k * std::log(2.0) - std::lgamma(0.5 * k) + std::log(k) -
+                  0.5 * k * (std::log(d) + 1.0);
+        }
+        p->c0 = c0;
+        NS_TRY(upload_compute(p, desc->data, n, &p->d_tt_obs, p->owned));
+        NS_TRY(upload_compute(p, hk.data(), n, &p->d_tt_halfk, p->owned));
+        return NS_OK;
+    }
     const ns_emulator_desc& e = desc->emu;
     const int L = e.n_layers, D = p->D, H = e.dims[L - 1];
     const double* Wout = e.W[L - 1];
@@ -311,6 +330,70 @@ static int cmb_setup(ns_problem* p, const ns_problem_desc* desc) {
     return NS_OK;
 }
 
+// Tile autotuner for the tensor-core hidden layers: each candidate N-tile
+// width (32, 64, 128) runs the layer on max_batch rows (at most 512) of the
+// workspace-sized activations, timed with CUDA events over 5 launches after a
+// warm-up; a wider tile replaces a narrower one only when it is at least 3%
+// faster, since in the nested-sampling rounds narrow tiles leave shared
+// memory for the other chain group's kernels.  Every width gives bit-identical
+// results (the accumulation order per element does not depend on it).
+static int autotune_hidden_tiles(ns_problem* p, int last_hidden) {
+    if (last_hidden < 1) return NS_OK;
+    const int rows = std::min(p->max_batch, 512);
+    const int rows_pad = ((rows + 127) / 128) * 128;
+    int kmax = 0, nmax = 0;
+    for (int l = 1; l <= last_hidden; ++l) { kmax = std::max(kmax, p->dims[l]); nmax = std::max(nmax, p->dims[l + 1]); }
+    void *a = nullptr, *o = nullptr;
+    int* dn = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto done = [&](int code) {
+        cudaFree(a); cudaFree(o); cudaFree(dn);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (st) cudaStreamDestroy(st);
+        return code;
+    };
+    if (cudaMalloc(&a, (size_t)2 * rows_pad * kmax) != cudaSuccess ||
+        cudaMalloc(&o, (size_t)2 * rows_pad * nmax) != cudaSuccess || cudaMalloc(&dn, sizeof(int)) != cudaSuccess)
+        return done(NS_ENOMEM);
+    if (cudaMemset(a, 0, (size_t)2 * rows_pad * kmax) != cudaSuccess ||
+        cudaMemcpy(dn, &rows, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return done(NS_ECUDA);
+    p->tile_ms.assign(p->n_layers, 0.0f);
+    for (int l = 1; l <= last_hidden; ++l) {
+        const int K = p->dims[l], N = p->dims[l + 1];
+        CUtensorMap tmA, tmB;
+        int s = make_tensor_map_bf16(&tmA, a, rows_pad, K, 128);
+        if (s) return done(s);
+        int best = p->tile_n[l];
+        float best_ms = 1e30f;
+        for (int tn : {32, 64, 128}) {
+            if (tn > N) continue;
+            if ((s = make_tensor_map_bf16(&tmB, p->d_W[l], N, K, tn))) return done(s);
+            auto run = [&]() {
+                return launch_gemm_tc(&tmA, &tmB, tn, (const float*)p->d_b[l], nullptr, 0.f, o, dn, rows, N, K,
+                                      TC_EPI_TANH, nullptr, nullptr, st);
+            };
+            if ((s = run())) return done(s);
+            if (cudaEventRecord(e0, st) != cudaSuccess) return done(NS_ECUDA);
+            for (int i = 0; i < 5; ++i)
+                if ((s = run())) return done(s);
+            float ms = 0.f;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                return done(NS_ECUDA);
+            if (ms < 0.97f * best_ms) { best = tn; best_ms = ms; }
+        }
+        p->tile_n[l] = best;
+        p->tile_ms[l] = best_ms / 5.f;
+        if ((s = make_tensor_map_bf16(&p->tmB[l], p->d_W[l], N, K, best))) return done(s);
+    }
+    return done(NS_OK);
+}
+
 static int validate_desc(const ns_problem_desc* d) {
     if (!d || !d->priors || d->n_params < 1 || d->n_params > 256 || d->max_batch < 1) return NS_EINVAL;
     if (d->precision < 0 || d->precision > NS_PREC_BF16_F64CHI2) return NS_EINVAL;
@@ -331,10 +414,19 @@ static int validate_desc(const ns_problem_desc* d) {
         return NS_EINVAL;
     if (e.activation != NS_ACT_TANH && e.activation != NS_ACT_SIGMOID_LINEAR) return NS_EINVAL;
     if (e.activation == NS_ACT_SIGMOID_LINEAR && (!e.act_g || !e.act_beta)) return NS_EINVAL;
-    if ((d->data == nullptr) != (d->cov == nullptr)) return NS_EINVAL;
+    const bool tt = d->kind == NS_KIND_CMB && d->cmb.form == NS_CMB_TT_CV;
+    if (!tt && (d->data == nullptr) != (d->cov == nullptr)) return NS_EINVAL;
     if (d->kind == NS_KIND_CMB) {
         if (e.dims[0] < 1 || e.dims[0] > 32) return NS_EINVAL;
-        if (d->n_data != e.dims[e.n_layers] || d->n_data < 1) return NS_EINVAL;
+        if (d->cmb.form != NS_CMB_GAUSS && d->cmb.form != NS_CMB_TT_CV) return NS_EINVAL;
+        if (tt) {
+            if (d->cmb.n_tt < 1 || d->cmb.n_tt > e.dims[e.n_layers] || !d->cmb.ell || d->cov) return NS_EINVAL;
+            if (d->data && d->n_data != d->cmb.n_tt) return NS_EINVAL;
+            for (int i = 0; i < d->cmb.n_tt; ++i)
+                if (!(d->cmb.ell[i] >= 0) || (d->data && !(d->data[i] > 0))) return NS_EINVAL;
+        } else if (d->n_data != e.dims[e.n_layers] || d->n_data < 1) {
+            return NS_EINVAL;
+        }
         for (int j = 0; j < e.dims[0]; ++j)
             if (e.inputs[j] < 0 || e.inputs[j] >= d->n_params || !(e.in_scale[j] != 0)) return NS_EINVAL;
         if (d->cmb.solve != NS_SOLVE_FOLD && d->cmb.solve != NS_SOLVE_LITERAL) return NS_EINVAL;
@@ -346,6 +438,7 @@ static int validate_desc(const ns_problem_desc* d) {
     if (s.n_bins < 1 || s.n_bins > 5 || s.n_ell < 1 || s.n_k < 4 || s.n_z < 4 || s.n_chi < 3 || !(s.a_min > 0 && s.a_min < 1))
         return NS_EINVAL;
     if (s.n_z_emu < 4 || s.n_z_emu > s.n_z) return NS_EINVAL;
+    if (s.z_interp != 0 && s.z_interp != 1) return NS_EINVAL;
     if (d->n_params != 11 + 2 * s.n_bins + s.n_tmpl) return NS_EINVAL;
     const int D = s.n_bins * (s.n_bins + 1) / 2 * s.n_ell;
     if (d->n_data != D) return NS_EINVAL;
@@ -529,10 +622,13 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
             int s = make_tensor_map_bf16(&p->tmB[l], p->d_W[l], N, p->dims[l], tn);
             if (s) return fail(s);
         }
+        int s = autotune_hidden_tiles(p, e.n_layers - 2);   // hidden layers 1 .. L-2
+        if (s) return fail(s);
     }
 
     p->D = desc->n_data;
     p->has_lik = desc->cov != nullptr;
+    if (cmb && desc->cmb.form == NS_CMB_TT_CV) p->has_lik = desc->data != nullptr;
     if (cmb) {
         int s = cmb_setup(p, desc);
         if (!s) s = workspace_create(p, p->max_batch, &p->ws);
@@ -628,8 +724,19 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
             std::vector<int> zr(4 * sd.n_z);
             std::vector<double> zwt(4 * sd.n_z);
             const double dzc = sd.z_max / (p->n_z_emu - 1);
-            for (int j = 0; j < sd.n_z; ++j)
-                cr_taps(j * dz, 0.0, dzc, p->n_z_emu, &zr[4 * j], &zwt[4 * j]);
+            for (int j = 0; j < sd.n_z; ++j) {
+                if (sd.z_interp == 1) {
+                    // linear: taps (i, i + 1) with weights (1 - t, t); unused taps weight 0
+                    const double u = j * dz / dzc;
+                    int i = (int)std::floor(u);
+                    i = std::max(0, std::min(i, p->n_z_emu - 2));
+                    const double t = u - i;
+                    zr[4 * j] = i; zr[4 * j + 1] = i + 1; zr[4 * j + 2] = i + 1; zr[4 * j + 3] = i + 1;
+                    zwt[4 * j] = 1.0 - t; zwt[4 * j + 1] = t; zwt[4 * j + 2] = 0.0; zwt[4 * j + 3] = 0.0;
+                } else {
+                    cr_taps(j * dz, 0.0, dzc, p->n_z_emu, &zr[4 * j], &zwt[4 * j]);
+                }
+            }
             if ((s = upload(zr.data(), zr.size(), &p->d_zi_row, p->owned)) ||
                 (s = upload(zwt.data(), zwt.size(), &p->d_zi_w, p->owned)))
                 return fail(s);
@@ -708,6 +815,15 @@ extern "C" int ns_model_batch(const ns_problem* p, const double* theta_dev, int 
     cudaStream_t st = (cudaStream_t)stream;
     NS_TRY(batch_common(p, theta_dev, B, st));
     return run_likelihood(p, const_cast<Workspace*>(&p->ws), B, nullptr, model_dev, st);
+}
+
+extern "C" int ns_problem_tiles(const ns_problem* p, int* tile_n, float* ms, int n) {
+    if (!p || !tile_n || n < p->n_layers) return NS_EINVAL;
+    for (int l = 0; l < p->n_layers; ++l) {
+        tile_n[l] = ((int)p->tile_n.size() > l && l >= 1) ? p->tile_n[l] : 0;
+        if (ms) ms[l] = ((int)p->tile_ms.size() > l) ? p->tile_ms[l] : 0.f;
+    }
+    return NS_OK;
 }
 
 extern "C" int ns_problem_status(ns_problem* p, int* bits, int clear) {

@@ -11,7 +11,8 @@ from oracle.priors import cube_to_theta, free_indices
 from oracle.shear import ShearOracle
 
 CONFIGS = {"shear_tiny": w.shear_tiny, "shear5": w.shear5, "shear39": w.shear39,
-           "shear37": w.shear37_lcdm, "shear39_interp": w.shear39_interp}
+           "shear37": w.shear37_lcdm, "shear39_interp": w.shear39_interp,
+           "shear39_interp_linear": w.shear39_interp_linear}
 
 
 @functools.lru_cache(maxsize=None)

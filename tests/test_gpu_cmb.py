@@ -171,3 +171,90 @@ def test_full_size_c1():
         y, absterm, _, _ = _fold_terms(orc, t)
         bound = eps_m * float(np.abs(y) @ absterm) + 1e-9 * abs(orc.c0)
         assert abs(g - (orc.c0 - 0.5 * float(y @ y))) <= bound
+
+
+@functools.lru_cache(maxsize=None)
+def tt_oracle(name):
+    inp = w.make_cmb_inputs(CMB[name]())
+    return inp, CMBOracle(inp, form="tt_cv")
+
+
+def tt_problem(name, precision, max_batch=64):
+    from paper_2509_13307_gb300 import Problem
+    inp, orc = tt_oracle(name)
+    return Problem(inp, precision, max_batch=max_batch, data=orc.data, form="tt_cv")
+
+
+def _tt_pieces(orc, theta, bf16=False):
+    """Reference log L of the TT form from the oracle's (optionally bf16) hidden
+    activations, and the first-order bound pieces: r = C/d, the absolute-term
+    sum A_ell of each output (|mu| + sigma (|b| + sum_k |W h|)), and
+    d log L / d h."""
+    inp = orc.inp
+    n = orc.n_tt
+    W, b = inp["emu_W"][-1][:n], inp["emu_b"][-1][:n]
+    mu, sig = inp["emu_out_mu"][:n], inp["emu_out_sig"][:n]
+    h = orc.hidden(theta, bf16)
+    C = mu + sig * (W @ h + b)
+    k, d = orc.k, orc.data
+    r = C / d
+    g = np.log(r) + 1.0 / r - 1.0
+    ref = orc.loglike_tt(theta) if not bf16 else None
+    if bf16:
+        from oracle.cmb import chi2_logpdf
+        ref = float(sum(chi2_logpdf(q * dd / c, q) + math.log(q / c) for q, dd, c in zip(k, d, C)))
+    A = np.abs(mu) + sig * (np.abs(b) + np.abs(W) @ np.abs(h))
+    gp = 1.0 / r - 1.0 / r ** 2
+    dldh = -((0.5 * k * gp * sig / d) @ W)
+    return ref, r, g, A, gp, dldh, h
+
+
+@pytest.mark.parametrize("name", ["cmb_tiny", "cmb_d600"])
+def test_tt_fp64_matches_oracle(name):
+    inp, orc = tt_oracle(name)
+    th = _points(inp, 10, 41)
+    p = tt_problem(name, "fp64")
+    got = p.loglike(torch.tensor(th, device="cuda")).cpu().numpy()
+    ref = np.array([orc.loglike(t) for t in th])
+    assert np.allclose(got, ref, rtol=1e-9, atol=0), np.max(np.abs(got / ref - 1))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_tt_reduced_precision_within_derived_bound(precision):
+    """FP32 head: |dC_ell| <= 4 (K + 8) 2^-24 A_ell; log L moves by at most
+    sum (k/2) |g'(r)| |dC| / d, plus 2^-22 sum (k/2) g for the FP32 terms and
+    their sum.  BF16 additionally: against the oracle with the same bf16
+    roundings, plus two first-order activation-rounding flips
+    |d log L / d h_k| 2^-8 |h_k|."""
+    inp, orc = tt_oracle("cmb_tiny")
+    th = _points(inp, 12, 42)
+    p = tt_problem("cmb_tiny", precision)
+    got = p.loglike(torch.tensor(th, device="cuda")).cpu().numpy()
+    K = inp["emu_W"][-1].shape[1]
+    eps_m = 4 * (K + 8) * 2.0 ** -24
+    bf16 = precision == "bf16"
+    for t, gv in zip(th, got):
+        ref, r, g, A, gp, dldh, h = _tt_pieces(orc, t, bf16)
+        half_k = 0.5 * orc.k
+        bound = float(np.sum(half_k * np.abs(gp) * eps_m * A / orc.data)) + 2.0 ** -22 * float(np.sum(half_k * g))
+        if bf16:
+            bound += 2 * float(np.max(np.abs(dldh) * 2.0 ** -8 * np.abs(h)))
+        bound += 1e-9 * abs(ref)
+        assert abs(gv - ref) <= bound, (gv - ref, bound)
+
+
+def test_tt_nested_sampling_bookkeeping():
+    from paper_2509_13307_gb300 import NestedRun
+    inp, orc = tt_oracle("cmb_tiny")
+    sc = w.cmb_tiny(repeats=4).sampler
+    prob = tt_problem("cmb_tiny", "fp64", max_batch=sc.n_live)
+    ons = NestedSampler.from_config(orc.loglike_cube, prob.d, sc)
+    ons.initialise()
+    run = NestedRun.from_config(prob, sc)
+    for _ in range(2):
+        ons.iterate()
+        st = run.step(1)
+        rec = ons.records[-1]
+        lstar, dele, starts, evals = run.last_iteration()
+        assert np.array_equal(dele, rec.deleted) and np.array_equal(evals, rec.evals)
+        assert st.logZ == pytest.approx(ons.acc.logZ, rel=1e-11)

@@ -64,18 +64,20 @@ def test_packed_runs_reproduce_single_runs():
     multi.close()
 
 
-def test_interpolated_emulator_fp64_parity():
-    inp, orc = oracle_for("shear39_interp")
-    p = cuda_problem("shear39_interp", "fp64", max_batch=8)
+@pytest.mark.parametrize("name", ["shear39_interp", "shear39_interp_linear"])
+def test_interpolated_emulator_fp64_parity(name):
+    inp, orc = oracle_for(name)
+    p = cuda_problem(name, "fp64", max_batch=8)
     th = free_theta(inp, random_cube(4, p.d, 51))
     got = p.loglike(_t(th)).cpu().numpy()
     ref = np.array([orc.loglike(t) for t in th])
     assert np.all(np.abs(got / ref - 1) < 1e-9)
 
 
-def test_interpolated_emulator_adjoint():
-    inp, orc = oracle_for("shear39_interp")
-    p = cuda_problem("shear39_interp", "fp64", max_batch=8)
+@pytest.mark.parametrize("name", ["shear39_interp", "shear39_interp_linear"])
+def test_interpolated_emulator_adjoint(name):
+    inp, orc = oracle_for(name)
+    p = cuda_problem(name, "fp64", max_batch=8)
     th = free_theta(inp, random_cube(1, p.d, 52, 0.1, 0.9))
     _, g = p.loglike_grad(_t(th))
     ref = orc.grad_complex_step(th[0])

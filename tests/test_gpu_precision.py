@@ -88,3 +88,19 @@ def test_loglike_reduced_precision_bound(name, prec):
         err = abs(got[b] - ref)
         print(f"{name} {prec} row {b}: |dlogL| = {err:.3e}, bound {bound:.3e}, ratio {err / bound:.3f}")
         assert err <= bound
+
+
+def test_tile_autotuner_choice_is_valid_and_results_identical():
+    """The hidden-layer tile autotuner picks one of the supported widths and
+    reports the time it measured; the likelihood stays deterministic."""
+    import torch
+    from gpu_helpers import cuda_problem, free_theta, oracle_for, random_cube
+    inp, _ = oracle_for("shear_tiny")
+    p = cuda_problem("shear_tiny", "bf16", max_batch=64)
+    tiles, ms = p.tiles()
+    assert tiles[0] == 0 and all(t in (32, 64, 128) for t in tiles[1:])
+    assert all(m > 0 for m in ms[1:-1])
+    th = torch.tensor(free_theta(inp, random_cube(40, p.d, 31)), device="cuda")
+    a = p.loglike(th).cpu().numpy()
+    b = p.loglike(th).cpu().numpy()
+    assert (a == b).all()

@@ -346,3 +346,31 @@ def test_bf16_rounding_matches_library_conversion():
                         [1.0, 1.00390625, 1.005859375, -0.0, 65504.0]])
     ref = torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).double().numpy()
     assert np.array_equal(ShearOracle.to_bf16(a), ref)
+
+
+def test_zinterp_catmull_rom_and_linear():
+    """Coarse-z interpolation: Catmull-Rom reproduces linear functions of z
+    everywhere and quadratics away from the edges; linear interpolation
+    reproduces linear functions and the coarse values at the coarse nodes."""
+    from dataclasses import replace as dc_replace
+    for mode in ("catmull_rom", "linear"):
+        cfg = dc_replace(w.shear_tiny(), coarse_z=5, z_interp=mode)
+        inp = w.make_shear_inputs(cfg)
+        o = ShearOracle.__new__(ShearOracle)   # only the grid attributes zinterp reads
+        o.inp, o.n_z, o.n_k, o.z_max = inp, inp["n_z"], inp["n_k"], inp["z_max"]
+        zc = np.linspace(0.0, o.z_max, 5)
+        zf = np.linspace(0.0, o.z_max, o.n_z)
+        lin = (1.5 + 0.7 * zc)[:, None] * np.ones((1, o.n_k))
+        assert np.allclose(o.zinterp(lin), (1.5 + 0.7 * zf)[:, None] * np.ones((1, o.n_k)), rtol=1e-13, atol=1e-13)
+        if mode == "catmull_rom":
+            q = (zc ** 2)[:, None] * np.ones((1, o.n_k))
+            interior = (zf >= zc[1]) & (zf <= zc[-2])
+            assert np.allclose(o.zinterp(q)[interior], (zf[interior] ** 2)[:, None], rtol=1e-12, atol=1e-12)
+        else:
+            rng = np.random.default_rng(3)
+            T = rng.standard_normal((5, o.n_k))
+            out = o.zinterp(T)
+            for i, z in enumerate(zc):
+                j = np.argmin(np.abs(zf - z))
+                if abs(zf[j] - z) < 1e-12:
+                    assert np.allclose(out[j], T[i], rtol=0, atol=1e-14)

@@ -92,6 +92,7 @@ class ShearConfig:
     emu_out_sigma: float = 0.05   # emulator output scale in dex about the mean table
     emu_bias_sd: float = 0.1
     coarse_z: Optional[int] = None    # if set: emulator on this many z nodes, interpolated to n_z
+    z_interp: str = "catmull_rom"     # coarse -> fine z: "catmull_rom" or "linear" (the paper's)
     seed_emulator: int = 0
     seed_noise: int = 1
     seed_cov: int = 2
@@ -306,6 +307,12 @@ def shear39_interp(**sampler_kw) -> ShearConfig:
 
 def shear37_interp(**sampler_kw) -> ShearConfig:
     return replace(shear37_lcdm(**sampler_kw), name="shear37_interp", coarse_z=10)
+
+
+def shear39_interp_linear(**sampler_kw) -> ShearConfig:
+    """shear39 on 10 coarse z nodes linearly interpolated in z (the paper's
+    interpolated-P(k) runs)."""
+    return replace(shear39(**sampler_kw), name="shear39_interp_linear", coarse_z=10, z_interp="linear")
 
 
 def uneven_runs():

@@ -91,7 +91,7 @@ def make_shear_inputs(cfg: ShearConfig) -> dict:
         nz_sigma=np.array(cfg.nz_sigma, float),
         ell=ell, delta_ell=delta_ell,
         n_k=cfg.n_k, lnk_min=lnk_min, lnk_max=lnk_max,
-        n_z=cfg.n_z, z_max=cfg.z_max, n_z_emu=cfg.n_z_emu,
+        n_z=cfg.n_z, z_max=cfg.z_max, n_z_emu=cfg.n_z_emu, z_interp=cfg.z_interp,
         n_chi=cfg.n_chi, a_min=cfg.a_min,
         emu_W=Ws, emu_b=bs, emu_act="tanh",
         emu_inputs=np.array(cfg.emu_inputs, dtype=np.int32),
