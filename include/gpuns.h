@@ -257,9 +257,51 @@ int ns_problem_tiles(const ns_problem* p, int* tile_n, float* ms, int n);
 int ns_problem_status(ns_problem* p, int* bits, int clear);
 
 /* Log-likelihood and its gradient d log L / d theta (B x d) by a hand-written
- * adjoint of the likelihood stages.  NS_ENOTSUP where not built. */
+ * adjoint of the likelihood stages (shear kind; closed form for the Gaussian
+ * test kind).  NS_ENOTSUP where not built (CMB kind). */
 int loglike_grad_batch(const ns_problem* p, const double* theta_dev, int B,
                        double* logL_dev, double* grad_dev, void* stream);
+
+/* No-U-Turn sampler (Hoffman & Gelman 2014, slice variable, dual averaging) on
+ * the problem's posterior, for the HMC comparison runs of Sec. 3.2.  Target:
+ * unconstrained z in R^d with cube coordinate c = 1/(1 + e^-z), theta = the
+ * prior transform of c, log p(z) = log L(theta) + sum ln(c (1 - c)).  The
+ * chains advance in lockstep: each leapfrog round is one loglike_grad_batch
+ * call over the chains still building their subtree; the control logic runs
+ * on the host in FP64.  Random numbers: Philox4x32-10, counter
+ * (purpose | j << 8, iteration, chain, extra) with purposes 7 momentum (j =
+ * dimension pair, Box-Muller), 8 slice, 9 direction (j = depth), 10 merge
+ * (j = depth), 11 reservoir (j = depth, extra = leaf index).
+ * Warm-up: dual averaging (gamma 0.05, t0 10, kappa 0.75, mu = ln(10 eps0))
+ * towards target_accept; with adapt_mass the inverse mass becomes the
+ * regularised variance of z over warm-up iterations [W/4, 3W/4) and dual
+ * averaging restarts there; sampling uses the averaged step size.
+ * z0 (host, n_chains x d): starting points.  samples (host, n_chains x
+ * n_samples x d): z after each kept iteration (map to theta with
+ * ns_prior_transform of the logistic); logp (host, may be NULL): log p(z).
+ * step_size (host, n_chains, may be NULL): final step sizes.  Synchronous.
+ * Shear and Gaussian-test kinds; n_chains <= max_batch. */
+typedef struct {
+    int n_chains;
+    int n_warmup;
+    int n_samples;
+    unsigned long long seed;
+    double target_accept;         /* delta, e.g. 0.8 */
+    int max_depth;                /* trajectory doublings (1 .. 20), e.g. 10 */
+    double init_step;             /* eps0 > 0 */
+    int adapt_mass;               /* 1: diagonal inverse mass from the warm-up window */
+} ns_nuts_config;
+
+typedef struct {
+    long long gradient_evals;     /* leapfrog steps summed over chains */
+    long long batched_calls;      /* lockstep rounds (batched gradient calls) */
+    int divergences;              /* divergent transitions among the kept iterations */
+    double mean_depth;            /* mean trajectory doublings of the kept iterations */
+    double mean_accept;           /* mean acceptance statistic of the kept iterations */
+} ns_nuts_stats;
+
+int ns_nuts_run(const ns_problem* p, const ns_nuts_config* cfg, const double* z0, double* samples,
+                double* logp, double* step_size, ns_nuts_stats* stats, void* stream);
 
 /* Start a run: draws n live points uniformly in the cube (Philox counter
  * (INIT | chunk << 8, 0, point, 0)), evaluates them, zeroes the evidence

@@ -22,7 +22,7 @@ EXPORTS = ["ns_strerror", "ns_problem_create", "ns_problem_free", "ns_problem_di
            "loglike_batch", "ns_model_batch", "ns_emulator_batch", "ns_problem_status", "ns_problem_tiles", "loglike_grad_batch", "ns_init", "ns_step", "ns_evidence",
            "ns_live_points", "ns_dead_points", "ns_last_iteration", "ns_profile_stage", "ns_profile_read",
            "ns_evidence_noalloc", "ns_multi_init", "ns_multi_step", "ns_multi_run",
-           "ns_multi_free", "ns_free"]
+           "ns_multi_free", "ns_nuts_run", "ns_free"]
 
 
 class Prior(C.Structure):
@@ -70,6 +70,17 @@ class Config(C.Structure):
                 ("rounds_per_sync", C.c_int), ("chain_groups", C.c_int)]
 
 
+class NutsConfig(C.Structure):
+    _fields_ = [("n_chains", C.c_int), ("n_warmup", C.c_int), ("n_samples", C.c_int), ("seed", C.c_ulonglong),
+                ("target_accept", C.c_double), ("max_depth", C.c_int), ("init_step", C.c_double),
+                ("adapt_mass", C.c_int)]
+
+
+class NutsStats(C.Structure):
+    _fields_ = [("gradient_evals", C.c_longlong), ("batched_calls", C.c_longlong), ("divergences", C.c_int),
+                ("mean_depth", C.c_double), ("mean_accept", C.c_double)]
+
+
 class Status(C.Structure):
     _fields_ = [("iterations", C.c_longlong), ("evaluations", C.c_longlong), ("rounds", C.c_longlong),
                 ("converged", C.c_int), ("status_bits", C.c_int), ("logZ", C.c_double), ("logX", C.c_double),
@@ -99,6 +110,7 @@ def load():
     lib.ns_model_batch.argtypes = [vp, vp, C.c_int, vp, vp]
     lib.ns_emulator_batch.argtypes = [vp, vp, C.c_int, vp, vp]
     lib.ns_problem_status.argtypes = [vp, C.POINTER(C.c_int), C.c_int]
+    lib.ns_nuts_run.argtypes = [vp, C.POINTER(NutsConfig), dp, dp, dp, dp, C.POINTER(NutsStats), vp]
     lib.ns_problem_tiles.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_float), C.c_int]
     lib.loglike_grad_batch.argtypes = [vp, vp, C.c_int, vp, vp, vp]
     lib.ns_init.argtypes = [vp, C.POINTER(Config), vp, C.POINTER(vp)]

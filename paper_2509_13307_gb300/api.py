@@ -484,3 +484,28 @@ class MultiRun:
             self.close()
         except Exception:
             pass
+
+
+def nuts(problem: Problem, n_chains: int, n_warmup: int, n_samples: int, z0=None, seed: int = 5,
+         target_accept: float = 0.8, max_depth: int = 10, init_step: float = 0.1, adapt_mass: bool = True,
+         stream=None) -> dict:
+    """No-U-Turn sampling of the problem's posterior (ns_nuts_run): returns the
+    unconstrained samples z (chains x samples x d), the physical parameters
+    theta (prior transform of the logistic of z, on the device), log p(z), the
+    final step sizes and the run statistics."""
+    d = problem.d
+    z0 = np.zeros((n_chains, d)) if z0 is None else np.ascontiguousarray(z0, dtype=np.float64)
+    z0 = np.ascontiguousarray(z0, dtype=np.float64)
+    cfg = L.NutsConfig(n_chains, n_warmup, n_samples, seed, target_accept, max_depth, init_step, int(adapt_mass))
+    samples = np.empty((n_chains, n_samples, d))
+    logp = np.empty((n_chains, n_samples))
+    eps = np.empty(n_chains)
+    st = L.NutsStats()
+    L.check(problem.lib.ns_nuts_run(problem.handle, C.byref(cfg), _dptr(z0), _dptr(samples), _dptr(logp),
+                                    _dptr(eps), C.byref(st), _stream(stream)), "ns_nuts_run")
+    flat = torch.tensor(1.0 / (1.0 + np.exp(-samples.reshape(-1, d))), dtype=torch.float64, device="cuda")
+    theta = torch.cat([problem.prior_transform(flat[i:i + problem.max_batch])
+                       for i in range(0, flat.shape[0], problem.max_batch)]).cpu().numpy()
+    return dict(z=samples, theta=theta.reshape(n_chains, n_samples, d), logp=logp, step_size=eps,
+                stats=dict(gradient_evals=st.gradient_evals, batched_calls=st.batched_calls,
+                           divergences=st.divergences, mean_depth=st.mean_depth, mean_accept=st.mean_accept))

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgpuns.so")
 SOURCES = ["likelihood.cu", "projection.cu", "gemm_tc.cu", "problem.cu", "ns_engine.cu", "noalloc.cu", "adjoint.cu",
-           "dense_linalg.cu"]
+           "dense_linalg.cu", "nuts.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]

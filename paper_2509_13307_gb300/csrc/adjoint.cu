@@ -870,12 +870,33 @@ int make_grad_weights(const ns_problem* p, GradWeights* gw) {
 }
 }  // namespace
 
+// Isotropic Gaussian test likelihood and its gradient at free parameters
+// (every parameter of that kind is free).
+__global__ void k_gauss_grad(const double* __restrict__ theta, int d, double mu, double sigma,
+                             double* __restrict__ logL, double* __restrict__ grad, int B) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= B) return;
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) {
+        const double r = (theta[(size_t)row * d + i] - mu) / sigma;
+        s += r * r;
+        grad[(size_t)row * d + i] = -r / sigma;
+    }
+    logL[row] = -0.5 * s - d * log(sigma * 2.5066282746310005024);
+}
+
 extern "C" int loglike_grad_batch(const ns_problem* p, const double* theta_dev, int B, double* logL_dev,
                                   double* grad_dev, void* stream) {
     if (!p || B < 0 || B > p->max_batch || (B > 0 && (!theta_dev || !logL_dev || !grad_dev))) return NS_EINVAL;
-    if (p->kind != NS_KIND_SHEAR) return NS_ENOTSUP;
+    if (p->kind != NS_KIND_SHEAR && p->kind != NS_KIND_GAUSS) return NS_ENOTSUP;
     if (B == 0) return NS_OK;
     cudaStream_t st = (cudaStream_t)stream;
+    if (p->kind == NS_KIND_GAUSS) {
+        if (p->d != p->P) return NS_ENOTSUP;
+        k_gauss_grad<<<(B + 127) / 128, 128, 0, st>>>(theta_dev, p->d, p->g_mu, p->g_sigma, logL_dev, grad_dev, B);
+        NS_CUDA_TRY(cudaGetLastError());
+        return NS_OK;
+    }
     GradState* gs = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_grad_mu);

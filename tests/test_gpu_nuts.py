@@ -1,0 +1,63 @@
+"""NUTS driver (ns_nuts_run) against the oracle NUTS on the same Philox
+streams, its sampling of a known posterior, and a short run on the shear
+likelihood's adjoint."""
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as w
+from gpu_helpers import cuda_problem
+from oracle.gauss import GaussOracle
+from oracle.nuts import NUTS, UnconstrainedTarget
+
+pytestmark = pytest.mark.gpu
+
+
+def _gauss(d, max_batch=32):
+    from paper_2509_13307_gb300 import Problem
+    cfg = w.gauss_test(d)
+    inp = w.make_gauss_inputs(cfg)
+    return inp, Problem(inp, "fp64", max_batch=max_batch)
+
+
+def test_nuts_matches_oracle_on_gaussian_test_problem():
+    from paper_2509_13307_gb300 import nuts
+    d = 3
+    inp, prob = _gauss(d)
+    mu, sig = inp["mu"], inp["sigma"]
+
+    def lg(th):
+        r = (th - mu) / sig
+        return -0.5 * float(r @ r) - d * np.log(sig * np.sqrt(2 * np.pi)), -r / sig
+
+    z0 = np.array([[0.3, -0.2, 0.1], [-0.4, 0.25, 0.05]])
+    out = nuts(prob, 2, 20, 12, z0=z0, seed=17, init_step=0.05, adapt_mass=False)
+    orc = NUTS(UnconstrainedTarget(inp["priors"], lg), d, seed=17, adapt_mass=False)
+    for c in range(2):
+        zs, lps, st, eps, _ = orc.run_chain(c, z0[c], 20, 12, eps0=0.05)
+        assert np.allclose(out["z"][c], zs, rtol=1e-8, atol=1e-10)
+        assert np.allclose(out["logp"][c], lps, rtol=1e-10, atol=1e-10)
+        assert out["step_size"][c] == pytest.approx(eps, rel=1e-10)
+
+
+def test_nuts_samples_gaussian_posterior():
+    from paper_2509_13307_gb300 import nuts
+    d = 5
+    inp, prob = _gauss(d, max_batch=16)
+    out = nuts(prob, 16, 300, 250, seed=3, init_step=0.1)
+    th = out["theta"].reshape(-1, d)
+    assert np.all(np.abs(th.mean(axis=0) - inp["mu"]) < 0.01)
+    assert np.all(np.abs(th.std(axis=0) / inp["sigma"] - 1.0) < 0.12)
+    assert 0.6 < out["stats"]["mean_accept"] < 0.95
+    assert out["stats"]["divergences"] == 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_nuts_on_shear_adjoint(precision):
+    from paper_2509_13307_gb300 import nuts
+    prob = cuda_problem("shear_tiny", precision, max_batch=16)
+    out = nuts(prob, 8, 20, 10, seed=9, init_step=0.02, max_depth=6)
+    assert np.all(np.isfinite(out["logp"]))
+    assert out["stats"]["gradient_evals"] > 8 * 30
+    assert np.all(np.isfinite(out["theta"]))
