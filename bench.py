@@ -189,6 +189,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-multi", action="store_true", help="skip the packed-runs measurement")
     ap.add_argument("--no-cmb", action="store_true", help="skip the CMB (D = 7521) measurement")
+    ap.add_argument("--no-nuts", action="store_true", help="skip the NUTS measurement")
+    ap.add_argument("--nuts-warmup", type=int, default=100)
+    ap.add_argument("--nuts-samples", type=int, default=100)
     ap.add_argument("--profile", choices=["loglike", "round", "cmb"], default=None,
                     help="run a short fixed workload for a profiler and exit (no timing line): "
                          "'loglike' = 4 loglike_batch calls of --batch rows on the 39-d shear problem, "
@@ -440,6 +443,26 @@ def ours(args):
                      logZ_evals=st.evaluations, logZ_converged=st.converged)
         run.close()
 
+    # ---------------- NUTS on the adjoint (the HMC comparison of the 39-d
+    # shear problem): 64 chains in lockstep, a short warm-up and sample
+    if not args.no_nuts:
+        try:
+            from paper_2509_13307_gb300 import nuts
+            pn = Problem(inp, args.precision, max_batch=64)
+            torch.cuda.synchronize()
+            t0 = time.time()
+            out = nuts(pn, 64, args.nuts_warmup, args.nuts_samples, seed=5 + rank, init_step=0.02, max_depth=8)
+            dt = time.time() - t0
+            stn = out["stats"]
+            extra.update(nuts_chains=64, nuts_warmup=args.nuts_warmup, nuts_samples=args.nuts_samples,
+                         nuts_seconds=dt, nuts_grad_evals_per_s=stn["gradient_evals"] / dt,
+                         nuts_iters_per_s=64 * (args.nuts_warmup + args.nuts_samples) / dt,
+                         nuts_mean_depth=stn["mean_depth"], nuts_mean_accept=stn["mean_accept"],
+                         nuts_divergences=stn["divergences"])
+            pn.close()
+        except Exception as exc:
+            extra["nuts_error"] = repr(exc)[:200]
+
     # ---------------- the 6-parameter CMB configuration (D = 7521, dense
     # covariance, whitening fold, FP32 emulator): NS evaluations/s and the wall
     # time to a converged log Z
@@ -478,6 +501,20 @@ def ours(args):
             pc.close()
         except Exception as exc:
             extra["cmb_error"] = repr(exc)[:200]
+        # the paper's own CMB likelihood form: cosmic-variance-limited TT
+        try:
+            ptt = Problem(cinp, "fp32", max_batch=csc.n_live, form="tt_cv")
+            t0 = time.time()
+            trun = NestedRun.from_config(ptt, csc)
+            tst = trun.run(max_iters=5000)
+            tev = trun.evidence()
+            extra.update(cmb_tt_time_to_logZ_s=time.time() - t0, cmb_tt_logZ=tev["logZ"],
+                         cmb_tt_logZ_err=tev["logZ_err"], cmb_tt_evals=tst.evaluations,
+                         cmb_tt_converged=tst.converged)
+            trun.close()
+            ptt.close()
+        except Exception as exc:
+            extra["cmb_tt_error"] = repr(exc)[:200]
 
     # ---------------- end to end through the public API with host buffers
     B = sc.n_delete
