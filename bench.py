@@ -190,13 +190,14 @@ def main():
     ap.add_argument("--no-multi", action="store_true", help="skip the packed-runs measurement")
     ap.add_argument("--no-cmb", action="store_true", help="skip the CMB (D = 7521) measurement")
     ap.add_argument("--no-nuts", action="store_true", help="skip the NUTS measurement")
-    ap.add_argument("--nuts-warmup", type=int, default=100)
-    ap.add_argument("--nuts-samples", type=int, default=100)
-    ap.add_argument("--profile", choices=["loglike", "round", "cmb"], default=None,
+    ap.add_argument("--nuts-warmup", type=int, default=10)
+    ap.add_argument("--nuts-samples", type=int, default=10)
+    ap.add_argument("--profile", choices=["loglike", "round", "cmb", "grad"], default=None,
                     help="run a short fixed workload for a profiler and exit (no timing line): "
                          "'loglike' = 4 loglike_batch calls of --batch rows on the 39-d shear problem, "
                          "'round' = two warm NS iterations then one more inside an NVTX range 'prof', "
-                         "'cmb' = 4 loglike_batch calls on the D = 7521 CMB problem")
+                         "'cmb' = 4 loglike_batch calls on the D = 7521 CMB problem, "
+                         "'grad' = 4 loglike_grad_batch calls of --batch rows on the 39-d shear problem")
     ap.add_argument("--batch", type=int, default=500)
     args = ap.parse_args()
     if args.profile:
@@ -220,7 +221,7 @@ def profile_workload(args):
         prob = Problem(inp, args.precision if args.precision != "bf16" else "fp32", max_batch=args.batch)
     else:
         inp = w.make_shear_inputs(w.shear39())
-        prob = Problem(inp, args.precision, max_batch=max(args.batch, 1000))
+        prob = Problem(inp, args.precision, max_batch=max(args.batch, 1000))   # grad: max_batch sizes its workspace
     if args.profile == "round":
         sc = w.shear39().sampler
         run = NestedRun.from_config(prob, sc)
@@ -235,7 +236,10 @@ def profile_workload(args):
         cube = torch.tensor(np.random.default_rng(9).uniform(0.02, 0.98, (args.batch, len(free))), device="cuda")
         th = prob.prior_transform(cube)
         for _ in range(4):
-            prob.loglike(th)
+            if args.profile == "grad":
+                prob.loglike_grad(th)
+            else:
+                prob.loglike(th)
         torch.cuda.synchronize()
     print(f"profile workload {args.profile} done", flush=True)
     return 0
