@@ -116,7 +116,8 @@ __device__ inline float cvt_in(__nv_bfloat16 v) { return __bfloat162float(v); }
 // Input layer: h = act(W0 x + b0), x = (theta[inputs] - center) / scale.
 template <typename T, typename TO>
 __global__ void k_emu_input(const double* __restrict__ theta_full, int P, const int* __restrict__ inputs,
-                            const double* __restrict__ center, const double* __restrict__ scale, int K0,
+                            const double* __restrict__ center, const double* __restrict__ scale,
+                            const double* __restrict__ inv_scale, int K0,
                             const T* __restrict__ W0, const T* __restrict__ b0, ActDev<T> act, int N,
                             TO* __restrict__ out, const int* __restrict__ nrows) {
     pdl_begin();
@@ -125,7 +126,10 @@ __global__ void k_emu_input(const double* __restrict__ theta_full, int P, const 
     __shared__ T x[32];
     if (threadIdx.x < K0) {
         const int j = threadIdx.x;
-        x[j] = (T)((theta_full[(size_t)row * P + inputs[j]] - center[j]) / scale[j]);
+        // FP64 standardisation; reduced-precision emulators multiply by the
+        // reciprocal scale (an FP64 divide is a long sequence on GB300's FP64 pipe)
+        const double v = theta_full[(size_t)row * P + inputs[j]] - center[j];
+        x[j] = sizeof(T) == 8 ? (T)(v / scale[j]) : (T)(v * inv_scale[j]);
     }
     __syncthreads();
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -290,6 +294,7 @@ static int run_emulator_simt(const ns_problem* p, Workspace* ws, int grid_rows, 
     const int K0 = p->dims[0], H1 = p->dims[1];
     dim3 g0((H1 + 255) / 256, grid_rows);
     k_emu_input<T, T><<<g0, 256, 0, st>>>(ws->theta_full, p->P, p->d_inputs, p->d_in_center, p->d_in_scale,
+                                          p->d_in_inv_scale,
                                           K0, (const T*)p->d_W[0], (const T*)p->d_b[0], layer_act<T>(p, 0), H1,
                                           (T*)ws->act[0], ws->d_nrows);
     NS_CUDA_TRY(cudaGetLastError());
@@ -333,7 +338,8 @@ static int run_emulator_bf16(const ns_problem* p, Workspace* ws, int grid_rows, 
     dim3 g0((H1 + 255) / 256, grid_rows);
     NS_CUDA_TRY(launch_pdl(k_emu_input<float, __nv_bfloat16>, g0, dim3(256), 0, st, (const double*)ws->theta_full,
                            p->P, (const int*)p->d_inputs, (const double*)p->d_in_center,
-                           (const double*)p->d_in_scale, K0, (const float*)p->d_W[0], (const float*)p->d_b[0],
+                           (const double*)p->d_in_scale, (const double*)p->d_in_inv_scale, K0,
+                           (const float*)p->d_W[0], (const float*)p->d_b[0],
                            layer_act<float>(p, 0), H1, (__nv_bfloat16*)ws->act[0], (const int*)ws->d_nrows));
     int cur = 0;
     for (int l = 1; l < L; ++l) {

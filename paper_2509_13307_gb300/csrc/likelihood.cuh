@@ -33,6 +33,15 @@ struct ShearParams {
     const int* pj;
     const double* data;   // D
     const double* tmpl;   // D x n_tmpl
+    // FP32 copies read by the float kernels (GB300 runs FP64, conversions
+    // included, at a small fraction of its FP32 rate, so float kernels take no
+    // per-thread double -> float conversions)
+    float lnk_min_f, lnk_max_f, inv_dlnk_f, ia_pivot_f, c1rho_f;
+    const float* lnell_f;
+    const float* nz_mean_f;
+    const float* nz_sigma_f;
+    const float* data_f;
+    const float* tmpl_f;
 };
 
 struct Workspace {
@@ -80,6 +89,7 @@ struct ns_problem {
     int* d_inputs = nullptr;
     double* d_in_center = nullptr;
     double* d_in_scale = nullptr;
+    double* d_in_inv_scale = nullptr;  // 1 / in_scale (reduced-precision input layer)
     void* d_out_mu = nullptr;        // FP64 or FP32
     double out_sigma = 1.0;
     int hidden_max = 0;

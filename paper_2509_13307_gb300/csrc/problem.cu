@@ -557,6 +557,9 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
         if ((s = upload(e.inputs, (size_t)p->dims[0], &p->d_inputs, p->owned))) return fail(s);
         if ((s = upload(e.in_center, (size_t)p->dims[0], &p->d_in_center, p->owned))) return fail(s);
         if ((s = upload(e.in_scale, (size_t)p->dims[0], &p->d_in_scale, p->owned))) return fail(s);
+        std::vector<double> inv(p->dims[0]);
+        for (int j = 0; j < p->dims[0]; ++j) inv[j] = 1.0 / e.in_scale[j];
+        if ((s = upload(inv.data(), inv.size(), &p->d_in_inv_scale, p->owned))) return fail(s);
         const size_t no = p->dims.back();
         if (f64) {
             double* m;
@@ -720,6 +723,26 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
             sp.zrp = dzr; sp.zw4d = dz4; sp.zw4f = dz4f;
         }
         sp.nz_mean = dmu; sp.nz_sigma = dsg; sp.pi = dpi; sp.pj = dpj; sp.data = ddata; sp.tmpl = dtm;
+        {
+            // FP32 copies for the float kernels
+            sp.lnk_min_f = (float)sd.lnk_min;
+            sp.lnk_max_f = (float)sd.lnk_max;
+            sp.inv_dlnk_f = 1.0f / (float)sp.dlnk;
+            sp.ia_pivot_f = (float)sd.ia_pivot;
+            sp.c1rho_f = (float)sd.c1rho;
+            std::vector<float> lef(lnell.begin(), lnell.end()), muf(sd.nz_mean, sd.nz_mean + sd.n_bins),
+                sgf(sd.nz_sigma, sd.nz_sigma + sd.n_bins), daf(sp.D, 0.f), tmf((size_t)sp.D * sd.n_tmpl);
+            if (desc->data)
+                for (int a = 0; a < sp.D; ++a) daf[a] = (float)desc->data[a];
+            for (size_t i = 0; i < tmf.size(); ++i) tmf[i] = (float)sd.tmpl[i];
+            float *dlef, *dmuf, *dsgf, *ddaf, *dtmf = nullptr;
+            if ((s = upload(lef.data(), sd.n_ell, &dlef, p->owned)) ||
+                (s = upload(muf.data(), sd.n_bins, &dmuf, p->owned)) ||
+                (s = upload(sgf.data(), sd.n_bins, &dsgf, p->owned)) || (s = upload(daf.data(), sp.D, &ddaf, p->owned)))
+                return fail(s);
+            if (sd.n_tmpl > 0 && (s = upload(tmf.data(), tmf.size(), &dtmf, p->owned))) return fail(s);
+            sp.lnell_f = dlef; sp.nz_mean_f = dmuf; sp.nz_sigma_f = dsgf; sp.data_f = ddaf; sp.tmpl_f = dtmf;
+        }
         if (p->n_z_emu != sd.n_z) {
             std::vector<int> zr(4 * sd.n_z);
             std::vector<double> zwt(4 * sd.n_z);

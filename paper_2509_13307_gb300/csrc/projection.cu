@@ -29,14 +29,23 @@
 
 namespace gpuns {
 
-__constant__ double c_glx2[4] = {-0.86113631159405257522, -0.33998104358485626480,
-                                  0.33998104358485626480, 0.86113631159405257522};
-__constant__ double c_glw2[4] = {0.34785484513745385737, 0.65214515486254614263,
-                                  0.65214515486254614263, 0.34785484513745385737};
+// 4-point Gauss-Legendre nodes and weights on [-1, 1] as compile-time
+// constants of the kernel's own type (no double -> float conversions at run
+// time).
+template <typename T> __device__ __forceinline__ T gl4_x(int g) {
+    return g == 0 ? T(-0.86113631159405257522) : g == 1 ? T(-0.33998104358485626480)
+         : g == 2 ? T(0.33998104358485626480) : T(0.86113631159405257522);
+}
+template <typename T> __device__ __forceinline__ T gl4_w(int g) {
+    return (g == 0 || g == 3) ? T(0.34785484513745385737) : T(0.65214515486254614263);
+}
 
 template <typename T> __device__ __forceinline__ const T* pick(const double* d, const float* f);
 template <> __device__ __forceinline__ const double* pick<double>(const double* d, const float*) { return d; }
 template <> __device__ __forceinline__ const float* pick<float>(const double*, const float* f) { return f; }
+template <typename T> __device__ __forceinline__ T pick_s(double d, float f);
+template <> __device__ __forceinline__ double pick_s<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pick_s<float>(double, float f) { return f; }
 
 // Transcendentals: accurate library versions, or (FAST, BF16 modes) the SFU
 // approximations, whose ~1e-6 relative error is far below the bf16 emulator's.
@@ -163,11 +172,11 @@ k_windows(const ShearParams sp, const double* __restrict__ theta_full, T* __rest
             const T mid = T(0.5) * (a + a1), half = T(0.5) * (a - a1);
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
-                const T ag = mid + half * (T)c_glx2[g];
+                const T ag = mid + half * gl4_x<T>(g);
                 const T lg = M::lg(ag);
                 const T ia = M::div(T(1), ag);
                 const T eg = om * ia * ia * ia + (T(1) - om) * M::ex(-pde * lg - T(3) * wa * (T(1) - ag));
-                inc += (T)c_glw2[g] * ia * ia * M::rsq(eg);
+                inc += gl4_w<T>(g) * ia * ia * M::rsq(eg);
             }
             inc *= chiH * half;
         }
@@ -195,17 +204,19 @@ k_windows(const ShearParams sp, const double* __restrict__ theta_full, T* __rest
     T pn[NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) pn[i] = T(0);
+    const T* nz_mu = pick<T>(sp.nz_mean, sp.nz_mean_f);
+    const T* nz_sg = pick<T>(sp.nz_sigma, sp.nz_sigma_f);
     T zc[NB], isg[NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        zc[i] = th[11 + i] + (T)sp.nz_mean[i];
-        isg[i] = M::div(T(1), (T)sp.nz_sigma[i]);
+        zc[i] = th[11 + i] + nz_mu[i];
+        isg[i] = M::div(T(1), nz_sg[i]);
     }
     for (int n = tid; n < N; n += nt) {
         const T wz = M::div(wa_[n], a_[n] * a_[n]);
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
-            const T u = FAST ? (z_[n] - zc[i]) * isg[i] : (z_[n] - th[11 + i] - (T)sp.nz_mean[i]) / (T)sp.nz_sigma[i];
+            const T u = FAST ? (z_[n] - zc[i]) * isg[i] : (z_[n] - th[11 + i] - nz_mu[i]) / nz_sg[i];
             const T raw = M::ex(T(-0.5) * u * u);
             V[i * N + n] = raw;
             pn[i] += wz * raw;
@@ -266,14 +277,15 @@ k_windows(const ShearParams sp, const double* __restrict__ theta_full, T* __rest
         for (int w = wid + 1; w < kProjWarps; ++w) { e0[i] += red[w * 2 * NB + i]; e1[i] += red[w * 2 * NB + NB + i]; }
     const T pref = T(1.5) * om / (chiH * chiH);
     const T A_IA = th[9], eta = th[10];
-    const T ipiv = M::div(T(1), (T)sp.ia_pivot);
-    const T c1om = (T)sp.c1rho * om;
+    const T pivot = pick_s<T>(sp.ia_pivot, sp.ia_pivot_f), c1rho = pick_s<T>(sp.c1rho, sp.c1rho_f);
+    const T ipiv = M::div(T(1), pivot);
+    const T c1om = c1rho * om;
     for (int n = hi - 1; n >= lo; --n) {
         const T c = chi[n];
         const T ic = (FAST && n >= 1) ? M::div(T(1), c) : T(0);
         const T sq = (n >= 1) ? (FAST ? sqrt_<T>(omw[n]) * ic : sqrt_<T>(omw[n] / (c * c))) : T(0);
         const T amp = FAST ? M::div(A_IA * M::ex(eta * M::lg((T(1) + z_[n]) * ipiv)) * c1om, Dg[n])
-                           : A_IA * M::ex(eta * M::lg((T(1) + z_[n]) / (T)sp.ia_pivot)) * (T)sp.c1rho * om / Dg[n];
+                           : A_IA * M::ex(eta * M::lg((T(1) + z_[n]) / pivot)) * c1rho * om / Dg[n];
         const T pc = FAST ? pref * c * M::div(T(1), a_[n]) : pref * c / a_[n];
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
@@ -298,20 +310,20 @@ k_windows(const ShearParams sp, const double* __restrict__ theta_full, T* __rest
         for (int n = tid; n < N; n += nt) out[(i + 1) * Np + n] = V[i * N + n];
 }
 
-// Stage B: Limber sums for (evaluation, group of 4 multipoles) work items.
-// The CTA stages the evaluation's log10 P table in shared memory with bulk
-// (TMA) row copies, then adds ghost rows/columns by linear extrapolation.
-// Padded layout: row r + 1 holds z row r, data column k sits at padded column
-// k + 4 (16-byte aligned rows for the copies), ghosts at columns 3 and n_k + 4;
-// the row pitch PK is a multiple of 4 chosen so that the 4-word tap windows
-// of up to 8 consecutive rows fall in distinct banks.  Warps 0-3 take the
-// group's first two multipoles and warps 4-7 the other two, each lane walking
-// chi nodes (node z-taps, ln chi and the windows from the stage-A output),
-// doing the Catmull-Rom lookup and the pair sums; a transposed warp reduction,
-// then a fixed-order sum over the four warps of each half.  The same threads
-// then form the data-vector entries of their (pair, multipole) and write the
-// residual d - m (or the model).
-constexpr int kLGroup = 4;
+// Stage B: Limber sums, one CTA per evaluation.  The CTA stages the
+// evaluation's log10 P table in shared memory with bulk (TMA) row copies
+// (issued by the lanes of warp 0 in parallel), then adds ghost rows/columns by
+// linear extrapolation.  Padded layout: row r + 1 holds z row r, data column k
+// sits at padded column k + 4 (16-byte aligned rows for the copies), ghosts at
+// columns 3 and n_k + 4; the row pitch PK is a multiple of 4 chosen so that
+// the 4-word tap windows of up to 8 consecutive rows fall in distinct banks.
+// Warp w takes multipole pairs (2 w, 2 w + 1), (2 (w + nw), ...), each lane
+// walking chi nodes (node z-taps, ln chi and the windows from the stage-A
+// output), doing the Catmull-Rom lookup and the pair sums; a transposed warp
+// reduction leaves lane q with pair sum q, and that lane forms the data-vector
+// entry (1 + m_i)(1 + m_j) C_ij(ell) + T b and writes the residual d - m (or
+// the model).  The sums are in fixed order (deterministic).
+constexpr int kLimberWarps = 10;
 
 __host__ __device__ inline int limber_pitch(int n_k) {
     int pk = (n_k + 5 + 3) & ~3;
@@ -329,7 +341,7 @@ __device__ __forceinline__ void limber_pair_f32(const float* __restrict__ U, int
                                                 const int* __restrict__ zrp, const float* __restrict__ zwp,
                                                 const float* __restrict__ lnchi, const float* __restrict__ V,
                                                 int Np, float lne0, float lne1, float lkmin, float lkmax,
-                                                float inv_dk, int n0, float* acc) {
+                                                float inv_dk, int n0, int stride, float* acc) {
     using M = Math<float, FAST>;
     constexpr int NP = NB * (NB + 1) / 2;
     const float2 one = make_float2(1.f, 1.f), m1 = make_float2(-1.f, -1.f), two = make_float2(2.f, 2.f);
@@ -339,7 +351,7 @@ __device__ __forceinline__ void limber_pair_f32(const float* __restrict__ U, int
     float2 a2[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) a2[p] = make_float2(0.f, 0.f);
-    for (int n = n0; n < N; n += 128) {
+    for (int n = n0; n < N; n += stride) {
         const float* rz = U + zrp[n] * PK + 3;
         const float4 wz = *reinterpret_cast<const float4*>(zwp + 4 * n);
         const float lc = lnchi[n];
@@ -392,7 +404,7 @@ __device__ __forceinline__ void limber_pair_f32(const float* __restrict__ U, int
 }
 
 template <typename T, int NB, bool FAST>
-__global__ void __launch_bounds__(kProjThreads, sizeof(T) == 8 ? 1 : 3)
+__global__ void __launch_bounds__(32 * kLimberWarps, sizeof(T) == 8 ? 1 : 2)
 k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* __restrict__ table,
          const T* __restrict__ win, T* __restrict__ resid, double* __restrict__ model_out,
          const int* __restrict__ nrows, int* __restrict__ err) {
@@ -400,26 +412,33 @@ k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* _
     constexpr int NP = NB * (NB + 1) / 2;
     static_assert(2 * NP <= 32, "two multipoles of pair sums must fit one warp transpose");
     pdl_begin();
-    const int row = blockIdx.y;
+    const int row = blockIdx.x;
     if (row >= *nrows) return;
-    const int l_base = blockIdx.x * kLGroup;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;
-    const int N = sp.N, n_k = sp.n_k, n_z = sp.n_z;
+    const int N = sp.N, n_k = sp.n_k, n_z = sp.n_z, n_ell = sp.n_ell;
     const int PK = limber_pitch(n_k);
     const int Np = win_pitch(N);
     T* U = reinterpret_cast<T*>(smem_raw);          // padded table
     T* W = U + (n_z + 2) * PK;                      // ln chi, V_1..V_NB (pitch Np)
-    T* part = W + (NB + 1) * Np;                    // 8 warps x 32
-    const int tid = threadIdx.x, nt = kProjThreads;
-    const int lane = tid & 31, wid = tid >> 5;
+    T* thr = W + (NB + 1) * Np;                     // the row's parameters in T (n_params)
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    const int n_lp = (n_ell + 1) / 2;               // multipole pairs, one warp each
     const T* src = table + (size_t)row * n_z * n_k;
     const T* wsrc = win + (size_t)row * (NB + 1) * Np;
     const uint32_t row_bytes = (uint32_t)(n_k * sizeof(T));
     const uint32_t win_bytes = (uint32_t)((NB + 1) * Np * sizeof(T));
     const bool bulk = (row_bytes % 16) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0 &&
                       (reinterpret_cast<uintptr_t>(wsrc) & 15) == 0;
-    int fail = 0;
+    // every output of the row is NaN when a bounded wait gives up
+    auto fail_row = [&]() {
+        if (tid == 0 && err) atomicOr(err, NS_BIT_TIMEOUT);
+        for (int a = tid; a < sp.D; a += nt) {
+            if (model_out) model_out[(size_t)row * sp.D + a] = NAN;
+            else resid[(size_t)row * sp.D + a] = (T)NAN;
+        }
+    };
     if (bulk) {
         const uint32_t bar = smem_u32(&s_bar);
         if (tid == 0) {
@@ -427,36 +446,33 @@ k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* _
             mbar_init_fence();
         }
         __syncthreads();
-        if (tid == 0) {
-            mbar_expect_tx(bar, row_bytes * n_z + win_bytes);
-            bulk_g2s(smem_u32(W), wsrc, win_bytes, bar);
-            for (int r = 0; r < n_z; ++r)
+        if (wid == 0) {
+            // one arrival with the whole transaction count, then the copies,
+            // issued by the 32 lanes of warp 0 in parallel
+            if (lane == 0) mbar_expect_tx(bar, row_bytes * n_z + win_bytes);
+            __syncwarp();
+            if (lane == 0) bulk_g2s(smem_u32(W), wsrc, win_bytes, bar);
+            for (int r = lane; r < n_z; r += 32)
                 bulk_g2s(smem_u32(U + (r + 1) * PK + 4), src + (size_t)r * n_k, row_bytes, bar);
         }
-        // one warp polls the barrier while the others sleep at the CTA barrier;
+        for (int i = tid; i < sp.n_params; i += nt) thr[i] = (T)theta_full[(size_t)row * sp.n_params + i];
+        // warp 0 polls the barrier while the others sleep at the CTA barrier;
         // afterwards every thread observes the completed phase (acquire).
+        int fail = 0;
         if (wid == 0) fail = !mbar_wait(bar, 0);
         if (!__syncthreads_or(fail)) mbar_try_wait(bar, 0);
         else {
             // give copies still in flight a second bounded wait before leaving
             if (wid == 0) mbar_wait(bar, 0);
             __syncthreads();
-            if (tid == 0 && err) atomicOr(err, NS_BIT_TIMEOUT);
-            if (tid < 2 * 2 * NP) {
-                const int hf = tid / (2 * NP), q = tid % (2 * NP);
-                const int l = l_base + 2 * hf + q / NP, p = q % NP;
-                if (l < sp.n_ell) {
-                    const int a = p * sp.n_ell + l;
-                    if (model_out) model_out[(size_t)row * sp.D + a] = NAN;
-                    else resid[(size_t)row * sp.D + a] = (T)NAN;
-                }
-            }
+            fail_row();
             return;
         }
     } else {
-        for (int r = wid; r < n_z; r += kProjWarps)
+        for (int r = wid; r < n_z; r += nw)
             for (int k = lane; k < n_k; k += 32) U[(r + 1) * PK + 4 + k] = src[(size_t)r * n_k + k];
         for (int i = tid; i < (NB + 1) * Np; i += nt) W[i] = wsrc[i];
+        for (int i = tid; i < sp.n_params; i += nt) thr[i] = (T)theta_full[(size_t)row * sp.n_params + i];
         __syncthreads();
     }
     for (int k = 4 + tid; k < 4 + n_k; k += nt) {
@@ -469,80 +485,76 @@ k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* _
         U[r * PK + n_k + 4] = T(2) * U[r * PK + n_k + 3] - U[r * PK + n_k + 2];
     }
     __syncthreads();
-    const T lkmin = (T)sp.lnk_min, lkmax = (T)sp.lnk_max, inv_dk = T(1) / (T)sp.dlnk;
+    const T lkmin = pick_s<T>(sp.lnk_min, sp.lnk_min_f), lkmax = pick_s<T>(sp.lnk_max, sp.lnk_max_f);
+    const T inv_dk = pick_s<T>(1.0 / sp.dlnk, sp.inv_dlnk_f);
     const int* zrp = sp.zrp;
     const T* zwp = pick<T>(sp.zw4d, sp.zw4f);
     const T* lnchi = W;
     const T* V = W + Np;
-    const int half = wid >> 2;                 // which two multipoles of the group
-    const int l0 = l_base + 2 * half;
-    const bool has0 = l0 < sp.n_ell, has1 = l0 + 1 < sp.n_ell;
-    const T lne0 = has0 ? (T)sp.lnell[l0] : T(0), lne1 = has1 ? (T)sp.lnell[l0 + 1] : T(0);
-    T acc[32];
+    const T* lnell = pick<T>(sp.lnell, sp.lnell_f);
+    const T* tm = pick<T>(sp.tmpl, sp.tmpl_f);
+    const T* dat = pick<T>(sp.data, sp.data_f);
+    for (int lp = wid; lp < n_lp; lp += nw) {
+        const int l0 = 2 * lp;
+        const bool has1 = l0 + 1 < n_ell;
+        const T lne0 = lnell[l0], lne1 = has1 ? lnell[l0 + 1] : lne0;
+        T acc[32];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) acc[q] = T(0);
-    if constexpr (sizeof(T) == 4) {
-        if (has0) limber_pair_f32<NB, FAST>(U, PK, N, n_k, zrp, reinterpret_cast<const float*>(zwp),
-                                            reinterpret_cast<const float*>(lnchi), reinterpret_cast<const float*>(V),
-                                            Np, (float)lne0, (float)(has1 ? lne1 : lne0), (float)lkmin, (float)lkmax,
-                                            (float)inv_dk, 1 + lane + 32 * (wid & 3), reinterpret_cast<float*>(acc));
-    } else if (has0) {
-        for (int n = 1 + lane + 32 * (wid & 3); n < N; n += 128) {
-            const T* rz = U + zrp[n] * PK + 3;
-            const T wz0 = zwp[4 * n], wz1 = zwp[4 * n + 1], wz2 = zwp[4 * n + 2], wz3 = zwp[4 * n + 3];
-            const T lc = lnchi[n];
-            T vv[NB];
+        for (int q = 0; q < 32; ++q) acc[q] = T(0);
+        if constexpr (sizeof(T) == 4) {
+            limber_pair_f32<NB, FAST>(U, PK, N, n_k, zrp, reinterpret_cast<const float*>(zwp),
+                                      reinterpret_cast<const float*>(lnchi), reinterpret_cast<const float*>(V), Np,
+                                      (float)lne0, (float)lne1, (float)lkmin, (float)lkmax, (float)inv_dk, 1 + lane,
+                                      32, reinterpret_cast<float*>(acc));
+        } else {
+            for (int n = 1 + lane; n < N; n += 32) {
+                const T* rz = U + zrp[n] * PK + 3;
+                const T wz0 = zwp[4 * n], wz1 = zwp[4 * n + 1], wz2 = zwp[4 * n + 2], wz3 = zwp[4 * n + 3];
+                const T lc = lnchi[n];
+                T vv[NB];
 #pragma unroll
-            for (int i = 0; i < NB; ++i) vv[i] = V[i * Np + n];
+                for (int i = 0; i < NB; ++i) vv[i] = V[i * Np + n];
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                if (j == 1 && !has1) break;
-                T sk = (j == 0 ? lne0 : lne1) - lc;
-                sk = fmin(fmax(sk, lkmin), lkmax);
-                const T uk = (sk - lkmin) * inv_dk;
-                int ik = (int)floor(uk);
-                ik = min(max(ik, 0), n_k - 2);
-                const T t = uk - (T)ik, t2 = t * t;
-                // doubled Catmull-Rom weights (the z-taps are doubled too)
-                const T k0 = t * (t * (T(2) - t) - T(1));
-                const T k1 = T(2) + t2 * (T(3) * t - T(5));
-                const T k2 = t * (T(1) + t * (T(4) - T(3) * t));
-                const T k3 = t2 * (t - T(1));
-                const T* c = rz + ik;
-                const T v = wz0 * (k0 * c[0] + k1 * c[1] + k2 * c[2] + k3 * c[3]) +
-                            wz1 * (k0 * c[PK] + k1 * c[PK + 1] + k2 * c[PK + 2] + k3 * c[PK + 3]) +
-                            wz2 * (k0 * c[2 * PK] + k1 * c[2 * PK + 1] + k2 * c[2 * PK + 2] + k3 * c[2 * PK + 3]) +
-                            wz3 * (k0 * c[3 * PK] + k1 * c[3 * PK + 1] + k2 * c[3 * PK + 2] + k3 * c[3 * PK + 3]);
-                const T P = M::p10(T(0.25) * v);
-                T tv[NB];
+                for (int j = 0; j < 2; ++j) {
+                    if (j == 1 && !has1) break;
+                    T sk = (j == 0 ? lne0 : lne1) - lc;
+                    sk = fmin(fmax(sk, lkmin), lkmax);
+                    const T uk = (sk - lkmin) * inv_dk;
+                    int ik = (int)floor(uk);
+                    ik = min(max(ik, 0), n_k - 2);
+                    const T t = uk - (T)ik, t2 = t * t;
+                    // doubled Catmull-Rom weights (the z-taps are doubled too)
+                    const T k0 = t * (t * (T(2) - t) - T(1));
+                    const T k1 = T(2) + t2 * (T(3) * t - T(5));
+                    const T k2 = t * (T(1) + t * (T(4) - T(3) * t));
+                    const T k3 = t2 * (t - T(1));
+                    const T* c = rz + ik;
+                    const T v = wz0 * (k0 * c[0] + k1 * c[1] + k2 * c[2] + k3 * c[3]) +
+                                wz1 * (k0 * c[PK] + k1 * c[PK + 1] + k2 * c[PK + 2] + k3 * c[PK + 3]) +
+                                wz2 * (k0 * c[2 * PK] + k1 * c[2 * PK + 1] + k2 * c[2 * PK + 2] + k3 * c[2 * PK + 3]) +
+                                wz3 * (k0 * c[3 * PK] + k1 * c[3 * PK + 1] + k2 * c[3 * PK + 2] + k3 * c[3 * PK + 3]);
+                    const T P = M::p10(T(0.25) * v);
+                    T tv[NB];
 #pragma unroll
-                for (int i = 0; i < NB; ++i) tv[i] = vv[i] * P;
-                int p = 0;
+                    for (int i = 0; i < NB; ++i) tv[i] = vv[i] * P;
+                    int p = 0;
 #pragma unroll
-                for (int i = 0; i < NB; ++i)
+                    for (int i = 0; i < NB; ++i)
 #pragma unroll
-                    for (int jj = i; jj < NB; ++jj) { acc[j * NP + p] += tv[i] * vv[jj]; ++p; }
+                        for (int jj = i; jj < NB; ++jj) { acc[j * NP + p] += tv[i] * vv[jj]; ++p; }
+                }
             }
         }
-    }
-    const T mine = warp_transpose_sum(acc);
-    part[wid * 32 + lane] = mine;
-    __syncthreads();
-    if (tid < 2 * 2 * NP) {
-        const int hf = tid / (2 * NP), q = tid % (2 * NP);
-        const int j = q / NP, p = q % NP;
-        const int l = l_base + 2 * hf + j;
-        if (l < sp.n_ell) {
-            T cl = T(0);
-#pragma unroll
-            for (int w = 0; w < 4; ++w) cl += part[(4 * hf + w) * 32 + q];
+        // lane q < 2 NP ends with the sum of value q: multipole l0 + q / NP, pair q % NP
+        const T cl = warp_transpose_sum(acc);
+        const int l = l0 + lane / NP, p = lane % NP;
+        if (lane < 2 * NP && l < n_ell) {
             // data vector (1 + m_i)(1 + m_j) C_ij(ell) + T b; residual d - m
-            const double* th = theta_full + (size_t)row * sp.n_params;
-            const int a = p * sp.n_ell + l;
-            T m = (T(1) + (T)th[11 + NB + sp.pi[p]]) * (T(1) + (T)th[11 + NB + sp.pj[p]]) * cl;
-            for (int t = 0; t < sp.n_tmpl; ++t) m += (T)sp.tmpl[(size_t)a * sp.n_tmpl + t] * (T)th[11 + 2 * NB + t];
+            const int a = p * n_ell + l;
+            T m = (T(1) + thr[11 + NB + sp.pi[p]]) * (T(1) + thr[11 + NB + sp.pj[p]]) * cl;
+            for (int t = 0; t < sp.n_tmpl; ++t) m += tm[(size_t)a * sp.n_tmpl + t] * thr[11 + 2 * NB + t];
             if (model_out) model_out[(size_t)row * sp.D + a] = (double)m;
-            else resid[(size_t)row * sp.D + a] = (T)sp.data[a] - m;
+            else resid[(size_t)row * sp.D + a] = dat[a] - m;
         }
     }
 }
@@ -747,7 +759,7 @@ static size_t windows_smem(const ShearParams& sp) {
 constexpr size_t kLimberSmemMax = 227 * 1024 - 64;
 template <typename T>
 static size_t limber_smem(const ShearParams& sp) {
-    return ((size_t)(sp.n_z + 2) * limber_pitch(sp.n_k) + (size_t)(sp.nb + 1) * win_pitch(sp.N) + kProjWarps * 32) *
+    return ((size_t)(sp.n_z + 2) * limber_pitch(sp.n_k) + (size_t)(sp.nb + 1) * win_pitch(sp.N) + sp.n_params) *
            sizeof(T);
 }
 
@@ -785,9 +797,9 @@ static int limber_nb(const ShearParams& sp, const double* theta_full, const T* t
                                          (int)(227 * 1024 - fa.sharedSizeBytes)));
         attr_done = true;
     }
-    dim3 g((sp.n_ell + kLGroup - 1) / kLGroup, grid_rows);
-    NS_CUDA_TRY(launch_pdl(k_limber<T, NB, FAST>, g, dim3(kProjThreads), smem, st, sp, theta_full, table, win, resid,
-                           model_out, nrows, err));
+    const int warps = std::min(kLimberWarps, (sp.n_ell + 1) / 2);
+    NS_CUDA_TRY(launch_pdl(k_limber<T, NB, FAST>, dim3(grid_rows), dim3(32 * warps), smem, st, sp, theta_full, table,
+                           win, resid, model_out, nrows, err));
     return NS_OK;
 }
 
