@@ -346,13 +346,12 @@ def ours(args):
     t_job, ev_job = job_totals(t_local, ev_local, world, dev)
     value = ev_job / t_job
 
-    # per round and chain group: batch reset, slice (with the prior transform),
-    # windows, emulator input layer, one GEMM per further layer, Limber,
-    # whitening; per iteration 7 more (sort and delete, column means,
+    # per round (one chain group): batch reset, slice (with the prior
+    # transform), windows, emulator input layer, one GEMM per further layer,
+    # Limber, whitening; per iteration 7 more (sort and delete, column means,
     # covariance, Cholesky, directions, chain starts, insert).
     n_layers = len(inp["emu_W"])
-    groups = 2 if sc.n_delete >= 128 else 1
-    per_round = groups * (5 + (n_layers - 1) + 1)
+    per_round = 5 + (n_layers - 1) + 1
     gpu_launches = res["rounds"] * per_round + 7 * res["iters"]
 
     # ---------------- roofline of the dominant kernel (Limber stage), timed live

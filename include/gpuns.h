@@ -187,7 +187,7 @@ typedef struct {
     int rounds_per_sync;          /* likelihood rounds launched between host checks (<= 0: auto) */
     int chain_groups;             /* 1 or 2 groups of chains whose likelihood rounds run on two
                                      streams and overlap on the GPU (results are identical);
-                                     <= 0: auto (2 for k >= 128, shear kind) */
+                                     <= 0: 1 */
 } ns_config;
 
 typedef struct {

@@ -537,19 +537,23 @@ __device__ void advance_chain(const RunDev& r, int c, int lane) {
     }
 }
 
-// One warp per chain of the group [chain0, chain0 + grp_chains).
-__global__ void __launch_bounds__(256) k_slice_advance(RunDev r) {
+// One warp per chain of the group [chain0, chain0 + grp_chains), one warp per
+// CTA: the chains' FP64 arithmetic (positions, prior transform) spreads over
+// the FP64 units of every SM instead of a few.
+constexpr int kSliceWarps = 1;
+__global__ void __launch_bounds__(32 * kSliceWarps) k_slice_advance(RunDev r) {
     pdl_begin();
-    const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int c = blockIdx.x * kSliceWarps + (threadIdx.x >> 5);
     if (c >= r.grp_chains) return;
     advance_chain(r, r.chain0 + c, threadIdx.x & 31);
 }
 
 // All chains of several packed runs: global warp g -> (run, chain) through the
 // prefix offsets chain_off[0..n_runs].
-__global__ void __launch_bounds__(256) k_slice_advance_multi(const RunDev* __restrict__ runs,
-                                                             const int* __restrict__ chain_off, int n_runs) {
-    const int g = blockIdx.x * 8 + (threadIdx.x >> 5);
+__global__ void __launch_bounds__(32 * kSliceWarps) k_slice_advance_multi(const RunDev* __restrict__ runs,
+                                                                          const int* __restrict__ chain_off,
+                                                                          int n_runs) {
+    const int g = blockIdx.x * kSliceWarps + (threadIdx.x >> 5);
     if (g >= chain_off[n_runs]) return;
     int r = 0;
     while (r + 1 < n_runs && chain_off[r + 1] <= g) ++r;
@@ -746,7 +750,8 @@ static int sync_scalars(ns_run* r) {
 static int launch_round(ns_run* r, int g, cudaStream_t st, const StageProbe* probe) {
     Workspace* ws = g ? &r->ws1 : &r->ws;
     NS_CUDA_TRY(launch_pdl(k_set_int, dim3(1), dim3(1), 0, st, r->grd[g].batch_ctr, 0));
-    NS_CUDA_TRY(launch_pdl(k_slice_advance, dim3((r->grd[g].grp_chains + 7) / 8), dim3(256), 0, st, r->grd[g]));
+    NS_CUDA_TRY(launch_pdl(k_slice_advance, dim3((r->grd[g].grp_chains + kSliceWarps - 1) / kSliceWarps),
+                           dim3(32 * kSliceWarps), 0, st, r->grd[g]));
     return run_likelihood(r->p, ws, r->grd[g].grp_chains, ws->logL, nullptr, st, probe);
 }
 
@@ -907,10 +912,12 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
     if ((s = grow_dead(r, 16LL * k + n))) return fail(s);
     // the workspace row count is the round's batch counter
     r->ws.d_nrows = &rd.sc->batch;
-    // two groups of chains whose rounds overlap on the GPU (the shear
-    // likelihood's tensor-core and FP32 stages then run side by side)
+    // optionally two groups of chains whose rounds overlap on the GPU (the
+    // shear likelihood's tensor-core and FP32 stages then run side by side);
+    // one group is the default: on GB300 the 39-d shear rounds measured 109 us
+    // with one group of 500 chains against 117 us with two of 250
     const int want = cfg->chain_groups;
-    r->n_groups = (k >= 2 && (want == 2 || (want <= 0 && k >= 128 && p->kind == NS_KIND_SHEAR))) ? 2 : 1;
+    r->n_groups = (k >= 2 && want == 2) ? 2 : 1;
     if (r->n_groups > 1) {
         r->k0 = (k + 1) / 2;
         if ((s = workspace_create(p, k - r->k0, &r->ws1))) return fail(s);
@@ -1147,7 +1154,8 @@ static int multi_refresh_runs(ns_multi* m) {
 
 static int multi_launch_round(ns_multi* m, cudaStream_t st) {
     NS_CUDA_TRY(cudaMemsetAsync(m->ws.d_nrows, 0, sizeof(int), st));
-    k_slice_advance_multi<<<(m->total_chains + 7) / 8, 256, 0, st>>>(m->d_runs, m->d_chain_off, m->n_runs);
+    k_slice_advance_multi<<<(m->total_chains + kSliceWarps - 1) / kSliceWarps, 32 * kSliceWarps, 0, st>>>(
+        m->d_runs, m->d_chain_off, m->n_runs);
     NS_CUDA_TRY(cudaGetLastError());
     return run_likelihood(m->model, &m->ws, m->total_chains, m->ws.logL, nullptr, st);
 }

@@ -331,7 +331,8 @@ static int cmb_setup(ns_problem* p, const ns_problem_desc* desc) {
 }
 
 // Tile autotuner for the tensor-core hidden layers: each candidate N-tile
-// width (32, 64, 128) runs the layer on max_batch rows (at most 512) of the
+// width (32, 64, 128) runs the layer on max_batch rows (at most 384, about the
+// average batch of a nested-sampling likelihood round with k = 500) of the
 // workspace-sized activations, timed with CUDA events over 5 launches after a
 // warm-up; a wider tile replaces a narrower one only when it is at least 3%
 // faster, since in the nested-sampling rounds narrow tiles leave shared
@@ -339,7 +340,7 @@ static int cmb_setup(ns_problem* p, const ns_problem_desc* desc) {
 // results (the accumulation order per element does not depend on it).
 static int autotune_hidden_tiles(ns_problem* p, int last_hidden) {
     if (last_hidden < 1) return NS_OK;
-    const int rows = std::min(p->max_batch, 512);
+    const int rows = std::min(p->max_batch, 384);
     const int rows_pad = ((rows + 127) / 128) * 128;
     int kmax = 0, nmax = 0;
     for (int l = 1; l <= last_hidden; ++l) { kmax = std::max(kmax, p->dims[l]); nmax = std::max(nmax, p->dims[l + 1]); }

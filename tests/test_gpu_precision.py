@@ -104,3 +104,37 @@ def test_tile_autotuner_choice_is_valid_and_results_identical():
     a = p.loglike(th).cpu().numpy()
     b = p.loglike(th).cpu().numpy()
     assert (a == b).all()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_whitened_loglike_full_batch(prec):
+    """At the 39-d problem's round size (500 rows, more Limber CTAs than fit
+    one wave) every row's log L is checked against the same FP32 model vector
+    (ns_model_batch) whitened on the host in FP64: the residual d - m is
+    formed in FP32 as the kernels do, and the remaining difference is bounded
+    by the FP32 rounding of L^-1 and of the D-term dot products,
+    |d log L| <= (D + 16) 2^-24 sum_a |y_a| (|L^-1| |r|)_a + 64 2^-24 chi^2.
+    Three sampled rows are also held to the FP32 bound against the oracle."""
+    name = "shear39"
+    inp, orc = oracle_for(name)
+    B = 500
+    p = cuda_problem(name, prec, max_batch=B)
+    th = free_theta(inp, random_cube(B, p.d, 61))
+    thd = _t(th)
+    got = p.loglike(thd).cpu().numpy()
+    m = p.model(thd).cpu().numpy()
+    r = (orc.data.astype(np.float32)[None, :] - m.astype(np.float32)).astype(np.float64)
+    Linv = np.linalg.inv(orc.L)
+    y = r @ Linv.T
+    chi2 = np.sum(y * y, axis=1)
+    ref = orc.c0 - 0.5 * chi2
+    D = r.shape[1]
+    bound = (D + 16) * 2.0 ** -24 * np.sum(np.abs(y) * (np.abs(r) @ np.abs(Linv).T), axis=1) + 64 * 2.0 ** -24 * chi2
+    err = np.abs(got - ref)
+    assert np.all(np.isfinite(got))
+    assert np.all(err <= bound), (int(np.argmax(err / bound)), float(np.max(err / bound)))
+    print(f"{prec} whitened log L, 500 rows: max |dlogL| {err.max():.3e}, max ratio to bound {np.max(err / bound):.3f}")
+    if prec == "fp32":
+        for b in (0, 137, 499):
+            full = _full(inp, th[b])
+            assert abs(got[b] - orc.loglike_full(full)) <= _fp32_bound(orc, full)
