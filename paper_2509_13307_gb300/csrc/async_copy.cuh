@@ -41,13 +41,29 @@ __device__ __forceinline__ uint64_t globaltimer() {
     return t;
 }
 
-// Bounded wait on a barrier phase; false after kWaitNs.
+// try_wait with a suspend-time hint: the waiting thread may be suspended in
+// hardware until the phase completes or `ns` nanoseconds pass, instead of
+// re-polling (a spinning warp takes issue slots from the warps and co-resident
+// CTAs doing the work it waits for).
+constexpr uint32_t kSuspendNs = 20000;
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(bar), "r"(parity), "r"(kSuspendNs) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on a barrier phase; false after kWaitNs (checked every 64
+// suspended tries, i.e. at most ~1.3 ms apart).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t i = 1;; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 255u) == 0 && globaltimer() - t0 > kWaitNs) return false;
+        if (mbar_try_wait_suspend(bar, parity)) return true;
+        if ((i & 63u) == 0 && globaltimer() - t0 > kWaitNs) return false;
     }
 }
 

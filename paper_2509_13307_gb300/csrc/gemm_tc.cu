@@ -204,8 +204,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 #pragma unroll
                     for (int q = 0; q < 4; ++q) o4[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
                 } else {
-                    for (int j = 0; j < 32 && col0 + j < N; ++j)
-                        out[j] = __float2bfloat16_rn(act(v[j] + bias[col0 + j], col0 + j));
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (col0 + j < N) out[j] = __float2bfloat16_rn(act(v[j] + bias[col0 + j], col0 + j));
                 }
             } else {
                 float* out = reinterpret_cast<float*>(Cout) + (size_t)row * N + col0;
@@ -221,8 +222,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                         o4[q] = r;
                     }
                 } else {
-                    for (int j = 0; j < 32 && col0 + j < N; ++j)
-                        out[j] = out_mu[col0 + j] + out_sigma * (v[j] + bias[col0 + j]);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (col0 + j < N) out[j] = out_mu[col0 + j] + out_sigma * (v[j] + bias[col0 + j]);
                 }
             }
         }
