@@ -145,6 +145,28 @@ def limber_flops_per_eval(cfg) -> float:
     return cfg.n_ell * (N - 1) * (32 + 10 + nb + 2 * npairs) + D * (3 + 2 * cfg.n_tmpl)
 
 
+# DRAM traffic of k_limber per evaluation from one ncu capture (25,032,960 bytes
+# read and 0 written at 384 evaluations per launch, cold L2, the summary in
+# profiles/k_limber_bf16_shear39_B384.md).  It equals the kernel's algorithmic
+# input bytes, so it scales with the rows of a launch; it is reported only while
+# the kernel's sources are the ones the capture was taken on.
+LIMBER_TRAFFIC_BYTES_PER_EVAL = 25032960 / 384
+LIMBER_TRAFFIC_SOURCES = ("paper_2509_13307_gb300/csrc/projection.cu", "paper_2509_13307_gb300/csrc/async_copy.cuh",
+                          "paper_2509_13307_gb300/csrc/likelihood.cuh", "paper_2509_13307_gb300/csrc/common.cuh")
+LIMBER_TRAFFIC_SHA256 = "27fda3222cf7b6eab24c76a52e3f57081801b08521c4a3a0a31997754212094c"
+
+
+def limber_traffic(avg_rows: float):
+    """Measured DRAM bytes per k_limber launch of avg_rows evaluations, or None
+    when the kernel's sources changed since the capture."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in LIMBER_TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return LIMBER_TRAFFIC_BYTES_PER_EVAL * avg_rows if h.hexdigest() == LIMBER_TRAFFIC_SHA256 else None
+
+
 def windows_flops_per_eval(cfg) -> float:
     """Algorithmic FLOPs of the windows stage (k_windows) per evaluation: per
     node interval the 4-point distance quadrature (4 x 12), per node the
@@ -362,7 +384,9 @@ def ours(args):
     if prof and prof["launches"] > 0 and prof["ms"] > 0:
         achieved = prof["rows"] * flops / (prof["ms"] * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": limber_traffic(prof["rows"] / prof["launches"]),
+                    "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                    "scaled from 384 evaluations)",
                     "kernel": "k_limber<float,5,fast> (A10-A12: P lookup, Limber sums, data vector)",
                     "flop_per_eval": flops, "avg_launch_ms": prof["ms"] / prof["launches"],
                     "avg_rows_per_launch": prof["rows"] / prof["launches"],
