@@ -698,6 +698,45 @@ __global__ void k_gather_grad(const double* __restrict__ gfull, int P, const int
     }
 }
 
+// BF16 problems, split path.  Input layer: h = tanh(W0 x + b0) in FP32 with
+// x standardised once per row (reciprocal scale), written as a bf16 (hi, lo)
+// pair: layer 1's A operand and the stored activation for the backward pass.
+__global__ void k_emu_in_split(const double* __restrict__ theta_full, int P, const int* __restrict__ inputs,
+                               const double* __restrict__ center, const double* __restrict__ inv_scale, int K0,
+                               const float* __restrict__ W0, const float* __restrict__ b0, int N,
+                               __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                               const int* __restrict__ nrows) {
+    const int row = blockIdx.y;
+    if (row >= *nrows) return;
+    __shared__ float x[32];
+    if (threadIdx.x < K0) {
+        const int j = threadIdx.x;
+        x[j] = (float)((theta_full[(size_t)row * P + inputs[j]] - center[j]) * inv_scale[j]);
+    }
+    __syncthreads();
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float acc = b0[n];
+    for (int j = 0; j < K0; ++j) acc = fmaf(W0[(size_t)n * K0 + j], x[j], acc);
+    const float h = tanhf(acc);
+    const __nv_bfloat16 hh = __float2bfloat16_rn(h);
+    hi[(size_t)row * N + n] = hh;
+    lo[(size_t)row * N + n] = __float2bfloat16_rn(h - __bfloat162float(hh));
+}
+
+// g = s * in (rows x n) written as a bf16 (hi, lo) pair.
+__global__ void k_scale_split(const float* __restrict__ in, float s, int n, __nv_bfloat16* __restrict__ hi,
+                              __nv_bfloat16* __restrict__ lo, const int* __restrict__ nrows) {
+    const int row = blockIdx.y;
+    if (row >= *nrows) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float g = s * in[(size_t)row * n + i];
+        const __nv_bfloat16 gh = __float2bfloat16_rn(g);
+        hi[(size_t)row * n + i] = gh;
+        lo[(size_t)row * n + i] = __float2bfloat16_rn(g - __bfloat162float(gh));
+    }
+}
+
 template <typename T>
 static int dense(const T* A, const T* W, const T* bias, const T* mu, T sigma, T* C, const int* nrows, int grid_rows,
                  int N, int K, int mode, const T* aux, cudaStream_t st) {
@@ -817,6 +856,144 @@ static int run_grad(const ns_problem* p, GradWorkspace* g, const GradWeights* gw
     return NS_OK;
 }
 
+// BF16 problems: the emulator forward and backward on the tensor cores
+// (split-BF16 activations and gradients, exact bf16 weights, FP32 accumulate),
+// the projection adjoint in FP32.  Layer l (1 .. L-1) maps dims[l] -> dims[l+1].
+struct SplitGrad {
+    int rows_pad = 0;
+    std::vector<__nv_bfloat16*> Hhi, Hlo;   // input activations of layer l (rows_pad x dims[l])
+    __nv_bfloat16* Ghi[2] = {nullptr, nullptr};
+    __nv_bfloat16* Glo[2] = {nullptr, nullptr};  // backward ping-pong (rows_pad x wmax)
+    float* G1 = nullptr;                     // gradient of layer 1's pre-activations (rows_pad x dims[1])
+    std::vector<__nv_bfloat16*> WT;          // W_l^T (dims[l] x dims[l+1])
+    std::vector<CUtensorMap> tmHhi, tmHlo, tmW, tmGhi, tmGlo, tmWT;
+    std::vector<void*> owned;
+};
+
+constexpr int kSplitHiddenTile = 128;        // forward hidden layers and every backward layer
+constexpr int kSplitOutTile = 256;           // forward output layer
+
+static bool split_supported(const ns_problem* p) {
+    if (p->kind != NS_KIND_SHEAR || (p->precision != NS_PREC_BF16 && p->precision != NS_PREC_BF16_F64CHI2)) return false;
+    if (p->act != NS_ACT_TANH || p->d_out_sig || p->n_layers < 2 || p->dims[0] > 32) return false;
+    for (int l = 1; l <= p->n_layers; ++l)
+        if (p->dims[l] % 8) return false;
+    return true;
+}
+
+static int split_grad_create(const ns_problem* p, int cap, SplitGrad* g) {
+    const int L = p->n_layers;
+    const int rows_pad = ((cap + 127) / 128) * 128;
+    g->rows_pad = rows_pad;
+    auto alloc = [&](size_t bytes, void** out) -> int {
+        if (cudaMalloc(out, bytes) != cudaSuccess) return NS_ENOMEM;
+        g->owned.push_back(*out);
+        return cudaMemset(*out, 0, bytes) == cudaSuccess ? NS_OK : NS_ECUDA;
+    };
+    void* v;
+    g->Hhi.assign(L, nullptr);
+    g->Hlo.assign(L, nullptr);
+    for (int l = 1; l < L; ++l) {
+        NS_TRY(alloc(sizeof(__nv_bfloat16) * (size_t)rows_pad * p->dims[l], &v)); g->Hhi[l] = (__nv_bfloat16*)v;
+        NS_TRY(alloc(sizeof(__nv_bfloat16) * (size_t)rows_pad * p->dims[l], &v)); g->Hlo[l] = (__nv_bfloat16*)v;
+    }
+    int wmax = 0;
+    for (int l = 1; l <= L; ++l) wmax = std::max(wmax, p->dims[l]);
+    for (int i = 0; i < 2; ++i) {
+        NS_TRY(alloc(sizeof(__nv_bfloat16) * (size_t)rows_pad * wmax, &v)); g->Ghi[i] = (__nv_bfloat16*)v;
+        NS_TRY(alloc(sizeof(__nv_bfloat16) * (size_t)rows_pad * wmax, &v)); g->Glo[i] = (__nv_bfloat16*)v;
+    }
+    NS_TRY(alloc(sizeof(float) * (size_t)rows_pad * p->dims[1], &v)); g->G1 = (float*)v;
+    // W_l^T in bf16 (the problem's tensor-core weights are bf16 already)
+    g->WT.assign(L, nullptr);
+    for (int l = 1; l < L; ++l) {
+        const int No = p->dims[l + 1], Ki = p->dims[l];
+        std::vector<uint16_t> w((size_t)No * Ki), wt((size_t)No * Ki);
+        NS_CUDA_TRY(cudaMemcpy(w.data(), p->d_W[l], w.size() * 2, cudaMemcpyDeviceToHost));
+        for (int n = 0; n < No; ++n)
+            for (int k = 0; k < Ki; ++k) wt[(size_t)k * No + n] = w[(size_t)n * Ki + k];
+        if (cudaMalloc(&v, wt.size() * 2) != cudaSuccess) return NS_ENOMEM;
+        g->owned.push_back(v);
+        NS_CUDA_TRY(cudaMemcpy(v, wt.data(), wt.size() * 2, cudaMemcpyHostToDevice));
+        g->WT[l] = (__nv_bfloat16*)v;
+    }
+    g->tmHhi.resize(L); g->tmHlo.resize(L); g->tmW.resize(L); g->tmGhi.resize(L); g->tmGlo.resize(L); g->tmWT.resize(L);
+    for (int l = 1; l < L; ++l) {
+        const bool last = (l == L - 1);
+        NS_TRY(make_tensor_map_bf16(&g->tmHhi[l], g->Hhi[l], rows_pad, p->dims[l], 128));
+        NS_TRY(make_tensor_map_bf16(&g->tmHlo[l], g->Hlo[l], rows_pad, p->dims[l], 128));
+        NS_TRY(make_tensor_map_bf16(&g->tmW[l], p->d_W[l], p->dims[l + 1], p->dims[l],
+                                    last ? kSplitOutTile : kSplitHiddenTile));
+        // backward step l reads G_{l+1} (K = dims[l+1]) from buffer (L - l - 1) % 2
+        const int b = (L - l - 1) % 2;
+        NS_TRY(make_tensor_map_bf16(&g->tmGhi[l], g->Ghi[b], rows_pad, p->dims[l + 1], 128));
+        NS_TRY(make_tensor_map_bf16(&g->tmGlo[l], g->Glo[b], rows_pad, p->dims[l + 1], 128));
+        NS_TRY(make_tensor_map_bf16(&g->tmWT[l], g->WT[l], p->dims[l], p->dims[l + 1], kSplitHiddenTile));
+    }
+    return NS_OK;
+}
+
+static int run_grad_split(const ns_problem* p, GradWorkspace* gw_, SplitGrad* g, const double* theta_full,
+                          const int* d_nrows, int B, double* logL, double* grad, int* d_err, cudaStream_t st) {
+    const int L = p->n_layers;
+    const ShearParams& sp = p->sp;
+    const int n_out = p->dims.back();
+    // forward: input layer, hidden layers (split tanh), output layer (FP32 table)
+    {
+        dim3 g0((p->dims[1] + 255) / 256, B);
+        adj::k_emu_in_split<<<g0, 256, 0, st>>>(theta_full, p->P, p->d_inputs, p->d_in_center, p->d_in_inv_scale,
+                                                p->dims[0], (const float*)p->d_W[0], (const float*)p->d_b[0],
+                                                p->dims[1], g->Hhi[1], g->Hlo[1], d_nrows);
+        NS_CUDA_TRY(cudaGetLastError());
+        for (int l = 1; l < L; ++l) {
+            const bool last = (l == L - 1);
+            if (last)
+                NS_TRY(launch_gemm_split(&g->tmHhi[l], &g->tmHlo[l], &g->tmW[l], kSplitOutTile,
+                                         (const float*)p->d_b[l], (const float*)p->d_out_mu, (float)p->out_sigma,
+                                         gw_->table, nullptr, nullptr, nullptr, d_nrows, B, n_out, p->dims[l], SPL_OUT,
+                                         d_err, st));
+            else
+                NS_TRY(launch_gemm_split(&g->tmHhi[l], &g->tmHlo[l], &g->tmW[l], kSplitHiddenTile,
+                                         (const float*)p->d_b[l], nullptr, 0.f, g->Hhi[l + 1], g->Hlo[l + 1], nullptr,
+                                         nullptr, d_nrows, B, p->dims[l + 1], p->dims[l], SPL_TANH, d_err, st));
+        }
+    }
+    const float* tab = (const float*)gw_->table;
+    if (p->n_z_emu != sp.n_z) {
+        NS_TRY(launch_zinterp_generic(p, gw_->table, gw_->table_fine, d_nrows, B, (int)sizeof(float), st));
+        tab = (const float*)gw_->table_fine;
+    }
+    NS_TRY(launch_projection_adj<float>(sp, theta_full, tab, p->d_LinvT32, p->c0, (float*)gw_->scratch,
+                                        (float*)gw_->gtab, gw_->gfull, logL, d_nrows, B, st));
+    // d log L / d (output pre-scaling) = sigma * d log L / d table, split
+    const float* gtab = (const float*)gw_->gtab;
+    if (p->n_z_emu != sp.n_z) {
+        dim3 gz((p->n_z_emu * sp.n_k + 255) / 256, B);
+        adj::k_zinterp_adj<float><<<gz, 256, 0, st>>>((const float*)gw_->gtab, sp.n_z, p->d_zi_row, p->d_zi_w,
+                                                      (float*)gw_->gA, p->n_z_emu, sp.n_k, d_nrows);
+        gtab = (const float*)gw_->gA;
+    }
+    {
+        dim3 gs((n_out + 255) / 256, B);
+        adj::k_scale_split<<<gs, 256, 0, st>>>(gtab, (float)p->out_sigma, n_out, g->Ghi[0], g->Glo[0], d_nrows);
+        NS_CUDA_TRY(cudaGetLastError());
+    }
+    // backward: G_l = (G_{l+1} W_l) (1 - h_l^2), l = L-1 .. 1 (the last in FP32)
+    for (int l = L - 1; l >= 1; --l) {
+        const int out = (L - l) % 2;
+        const bool first = (l == 1);
+        NS_TRY(launch_gemm_split(&g->tmGhi[l], &g->tmGlo[l], &g->tmWT[l], kSplitHiddenTile, nullptr, nullptr, 0.f,
+                                 first ? (void*)g->G1 : (void*)g->Ghi[out], first ? nullptr : g->Glo[out], g->Hhi[l],
+                                 g->Hlo[l], d_nrows, B, p->dims[l], p->dims[l + 1],
+                                 first ? SPL_DTANH32 : SPL_DTANH, d_err, st));
+    }
+    adj::k_emu_in_back<float><<<B, 256, 0, st>>>(g->G1, (const float*)p->d_W[0], p->dims[1], p->dims[0], p->d_inputs,
+                                                 p->d_in_scale, gw_->gfull, p->P, d_nrows);
+    adj::k_gather_grad<<<B, 64, 0, st>>>(gw_->gfull, p->P, p->d_free_of_full, grad, p->d, B);
+    NS_CUDA_TRY(cudaGetLastError());
+    return NS_OK;
+}
+
 }  // namespace gpuns
 
 using namespace gpuns;
@@ -826,7 +1003,10 @@ struct GradState {
     const ns_problem* p = nullptr;
     GradWorkspace ws;
     GradWeights w;
+    SplitGrad split;                 // BF16 problems on the tensor cores
+    bool use_split = false;
     int* d_nrows = nullptr;
+    int* d_err = nullptr;
     double* theta_full = nullptr;
 };
 std::vector<GradState*> g_grad_states;
@@ -905,17 +1085,25 @@ extern "C" int loglike_grad_batch(const ns_problem* p, const double* theta_dev, 
             gs = new GradState();
             gs->p = p;
             const bool f64 = p->precision == NS_PREC_FP64;
+            gs->use_split = split_supported(p);
             int rc = f64 ? grad_ws_create<double>(p, p->max_batch, &gs->ws) : grad_ws_create<float>(p, p->max_batch, &gs->ws);
-            if (rc == NS_OK) rc = f64 ? make_grad_weights<double>(p, &gs->w) : make_grad_weights<float>(p, &gs->w);
+            if (rc == NS_OK && gs->use_split) rc = split_grad_create(p, p->max_batch, &gs->split);
+            else if (rc == NS_OK) rc = f64 ? make_grad_weights<double>(p, &gs->w) : make_grad_weights<float>(p, &gs->w);
             void* v = nullptr;
             if (rc == NS_OK && cudaMalloc(&v, sizeof(int)) != cudaSuccess) rc = NS_ENOMEM;
             gs->d_nrows = (int*)v;
+            v = nullptr;
+            if (rc == NS_OK && (cudaMalloc(&v, sizeof(int)) != cudaSuccess || cudaMemset(v, 0, sizeof(int)) != cudaSuccess))
+                rc = NS_ENOMEM;
+            gs->d_err = (int*)v;
+            v = nullptr;
             if (rc == NS_OK && cudaMalloc(&v, sizeof(double) * (size_t)p->max_batch * p->P) != cudaSuccess) rc = NS_ENOMEM;
             gs->theta_full = (double*)v;
             if (rc != NS_OK) {
                 for (void* q : gs->ws.owned) cudaFree(q);
                 for (void* q : gs->w.owned) cudaFree(q);
-                cudaFree(gs->d_nrows); cudaFree(gs->theta_full);
+                for (void* q : gs->split.owned) cudaFree(q);
+                cudaFree(gs->d_nrows); cudaFree(gs->d_err); cudaFree(gs->theta_full);
                 delete gs;
                 return rc;
             }
@@ -927,6 +1115,8 @@ extern "C" int loglike_grad_batch(const ns_problem* p, const double* theta_dev, 
     NS_CUDA_TRY(cudaGetLastError());
     if (p->precision == NS_PREC_FP64)
         return run_grad<double>(p, &gs->ws, &gs->w, gs->theta_full, gs->d_nrows, B, logL_dev, grad_dev, st);
+    if (gs->use_split)
+        return run_grad_split(p, &gs->ws, &gs->split, gs->theta_full, gs->d_nrows, B, logL_dev, grad_dev, gs->d_err, st);
     return run_grad<float>(p, &gs->ws, &gs->w, gs->theta_full, gs->d_nrows, B, logL_dev, grad_dev, st);
 }
 
@@ -938,7 +1128,9 @@ void gpuns_release_grad_state(const ns_problem* p) {
         if (s->p != p) continue;
         for (void* q : s->ws.owned) cudaFree(q);
         for (void* q : s->w.owned) cudaFree(q);
+        for (void* q : s->split.owned) cudaFree(q);
         cudaFree(s->d_nrows);
+        cudaFree(s->d_err);
         cudaFree(s->theta_full);
         delete s;
         g_grad_states.erase(g_grad_states.begin() + i);

@@ -353,6 +353,204 @@ k_gemm_tc_swap(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ 
     }
 }
 
+// ------------------------------------------------------------------ split-BF16 GEMM
+// FP32-accurate products on the bf16 tensor path, for the adjoint: the A
+// operand is held as two bf16 matrices whose sum is the FP32 value
+// (hi = bf16(a), lo = bf16(a - hi), ~2^-17 relative), B is exact in bf16 (the
+// emulator's weights), and every k-block issues MMA(A_hi, B) and MMA(A_lo, B)
+// into one FP32 accumulator.  One CTA computes a 128 x BN tile; TMA ring of
+// STAGES slots holding A_hi | A_lo | B boxes; warp roles as in k_gemm_tc.
+// Epilogues (thread = tile row):
+//   SPL_TANH   h = tanh(acc + b) -> (hi, lo) pair                    [forward hidden]
+//   SPL_OUT    mu + sigma (acc + b) -> FP32                          [forward output]
+//   SPL_DTANH  g = acc (1 - h^2), h = aux_hi + aux_lo -> (hi, lo)    [backward hidden]
+//   SPL_DTANH32 the same -> FP32                                      [backward, first hidden layer]
+template <int BN>
+struct CfgSplit {
+    static constexpr int STAGES = (BN >= 256) ? 3 : 4;
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = 2 * A_BYTES + B_BYTES;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+    static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+};
+
+__device__ __forceinline__ void split_store32(const float (&v)[32], __nv_bfloat16* hi, __nv_bfloat16* lo, int nvalid,
+                                              bool vec) {
+    if (vec) {
+        uint32_t ph[16], pl[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            const float2 hf = __bfloat1622float2(h2);
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+            ph[j] = *reinterpret_cast<const uint32_t*>(&h2);
+            pl[j] = *reinterpret_cast<const uint32_t*>(&l2);
+        }
+        uint4* oh = reinterpret_cast<uint4*>(hi);
+        uint4* ol = reinterpret_cast<uint4*>(lo);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            oh[q] = make_uint4(ph[4 * q], ph[4 * q + 1], ph[4 * q + 2], ph[4 * q + 3]);
+            ol[q] = make_uint4(pl[4 * q], pl[4 * q + 1], pl[4 * q + 2], pl[4 * q + 3]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < nvalid) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(v[j]);
+                hi[j] = h;
+                lo[j] = __float2bfloat16_rn(v[j] - __bfloat162float(h));
+            }
+    }
+}
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(128, 1)
+k_gemm_split(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
+             const __grid_constant__ CUtensorMap tmB, const float* __restrict__ bias, const float* __restrict__ out_mu,
+             float out_sigma, void* __restrict__ Cout, __nv_bfloat16* __restrict__ Clo,
+             const __nv_bfloat16* __restrict__ aux_hi, const __nv_bfloat16* __restrict__ aux_lo,
+             const int* __restrict__ nrows, int N, int K, int* __restrict__ err) {
+    using C = CfgSplit<BN>;
+    pdl_begin();
+    const int M = *nrows;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    if (m0 >= M) return;
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - raw);
+    const uint32_t bar0 = base + C::STAGES * C::STAGE_BYTES;
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (C::STAGES + s); };
+    const uint32_t accf = bar0 + 8u * (2 * C::STAGES);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + C::STAGES * C::STAGE_BYTES + 8 * (2 * C::STAGES + 1));
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int s = 0; s < C::STAGES; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), 1); }
+        mbar_init(accf, 1);
+        mbar_init_fence();
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tmem_slot)), "r"(C::TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int nk = (K + BK - 1) / BK;
+
+    if (warp == 0 && lane == 0) {
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % C::STAGES;
+            if (kb >= C::STAGES && !mbar_wait(empty_bar(s), ((kb / C::STAGES) & 1) ^ 1)) { s_fail = 1; break; }
+            const uint32_t sa = base + s * C::STAGE_BYTES;
+            mbar_expect_tx(full_bar(s), C::STAGE_BYTES);
+            tma_load_2d(sa, &tmAhi, full_bar(s), kb * BK, m0);
+            tma_load_2d(sa + C::A_BYTES, &tmAlo, full_bar(s), kb * BK, m0);
+            tma_load_2d(sa + 2 * C::A_BYTES, &tmB, full_bar(s), kb * BK, n0);
+        }
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = instr_desc<BN>();
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % C::STAGES;
+            if (!mbar_wait(full_bar(s), (kb / C::STAGES) & 1)) { s_fail = 1; break; }
+            fence_after();
+            const uint32_t sa = base + s * C::STAGE_BYTES;
+            const uint64_t dh = smem_desc(sa), dl = smem_desc(sa + C::A_BYTES), db = smem_desc(sa + 2 * C::A_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                mma_bf16(tmem, dh + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0);
+                mma_bf16(tmem, dl + 2 * kk, db + 2 * kk, idesc, 1u);
+            }
+            mma_commit(empty_bar(s));
+        }
+        mma_commit(accf);
+    }
+    __syncwarp();
+
+    const bool ok = mbar_wait(accf, 0);
+    fence_after();
+    __syncwarp();
+    if (ok && !s_fail) {
+        const int row = m0 + warp * 32 + lane;
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+            float v[32];
+            tmem_ld32(lane_addr + c * 32, v);
+            const int col0 = n0 + c * 32;
+            if (row >= M || col0 >= N) continue;
+            const int nvalid = min(32, N - col0);
+            const bool vec = nvalid == 32 && (N % 8) == 0;
+            const size_t off = (size_t)row * N + col0;
+            if (EPI == SPL_OUT) {
+                float* out = reinterpret_cast<float*>(Cout) + off;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (j < nvalid) out[j] = out_mu[col0 + j] + out_sigma * (v[j] + bias[col0 + j]);
+                continue;
+            }
+            if (EPI == SPL_TANH) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = (j < nvalid) ? tanhf(v[j] + bias[col0 + j]) : 0.f;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    if (j < nvalid) {
+                        const float h = __bfloat162float(aux_hi[off + j]) + __bfloat162float(aux_lo[off + j]);
+                        v[j] *= 1.f - h * h;
+                    }
+                }
+            }
+            if (EPI == SPL_DTANH32) {
+                float* out = reinterpret_cast<float*>(Cout) + off;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (j < nvalid) out[j] = v[j];
+            } else {
+                split_store32(v, reinterpret_cast<__nv_bfloat16*>(Cout) + off, Clo + off, nvalid, vec);
+            }
+        }
+    }
+    if ((!ok || s_fail) && threadIdx.x == 0 && err) atomicOr(err, NS_BIT_TIMEOUT);
+    fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(C::TMEM_COLS) : "memory");
+    }
+}
+
+template <int BN>
+static int launch_split_bn(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo, const CUtensorMap* tmB,
+                           const float* bias, const float* mu, float sigma, void* C, __nv_bfloat16* Clo,
+                           const __nv_bfloat16* aux_hi, const __nv_bfloat16* aux_lo, const int* nrows, int grid_rows,
+                           int N, int K, int epi, int* err, cudaStream_t st) {
+    using CF = CfgSplit<BN>;
+    static bool attr = false;
+    if (!attr) {
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_split<BN, SPL_TANH>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM));
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_split<BN, SPL_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM));
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_split<BN, SPL_DTANH>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM));
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_split<BN, SPL_DTANH32>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM));
+        attr = true;
+    }
+    dim3 grid((N + BN - 1) / BN, (grid_rows + BM - 1) / BM);
+    auto kern = epi == SPL_TANH ? k_gemm_split<BN, SPL_TANH> : epi == SPL_OUT ? k_gemm_split<BN, SPL_OUT>
+              : epi == SPL_DTANH ? k_gemm_split<BN, SPL_DTANH> : k_gemm_split<BN, SPL_DTANH32>;
+    NS_CUDA_TRY(launch_pdl(kern, grid, dim3(128), (size_t)CF::SMEM, st, *tmAhi, *tmAlo, *tmB, bias, mu, sigma, C, Clo,
+                           aux_hi, aux_lo, nrows, N, K, err));
+    return NS_OK;
+}
+
 template <int BN>
 static int launch_bn(const CUtensorMap* tmA, const CUtensorMap* tmB, const float* bias, const float* mu,
                      float sigma, void* Cout, const int* nrows, int grid_rows, int N, int K, int epi,
@@ -402,6 +600,25 @@ int launch_gemm_tc_out_swap(const CUtensorMap* tmW, const CUtensorMap* tmX, cons
     NS_CUDA_TRY(launch_pdl(tc::k_gemm_tc_swap<BR>, grid, dim3(128), (size_t)CS::SMEM, st, *tmW, *tmX, bias, out_mu,
                            out_sigma, C, d_nrows, N, K, d_err));
     return NS_OK;
+}
+
+int launch_gemm_split(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo, const CUtensorMap* tmB, int tile_n,
+                      const float* bias, const float* out_mu, float out_sigma, void* C, __nv_bfloat16* C_lo,
+                      const __nv_bfloat16* aux_hi, const __nv_bfloat16* aux_lo, const int* d_nrows, int grid_rows,
+                      int N, int K, int epi, int* d_err, cudaStream_t st) {
+    if (grid_rows <= 0) return NS_OK;
+    if (epi < SPL_TANH || epi > SPL_DTANH32) return NS_EINVAL;
+    if ((epi == SPL_TANH || epi == SPL_DTANH) && !C_lo) return NS_EINVAL;
+    if ((epi == SPL_DTANH || epi == SPL_DTANH32) && (!aux_hi || !aux_lo)) return NS_EINVAL;
+    switch (tile_n) {
+        case 64: return tc::launch_split_bn<64>(tmAhi, tmAlo, tmB, bias, out_mu, out_sigma, C, C_lo, aux_hi, aux_lo,
+                                                d_nrows, grid_rows, N, K, epi, d_err, st);
+        case 128: return tc::launch_split_bn<128>(tmAhi, tmAlo, tmB, bias, out_mu, out_sigma, C, C_lo, aux_hi, aux_lo,
+                                                  d_nrows, grid_rows, N, K, epi, d_err, st);
+        case 256: return tc::launch_split_bn<256>(tmAhi, tmAlo, tmB, bias, out_mu, out_sigma, C, C_lo, aux_hi, aux_lo,
+                                                  d_nrows, grid_rows, N, K, epi, d_err, st);
+        default: return NS_EINVAL;
+    }
 }
 
 int gemm_tc_supported(int N, int K) {

@@ -195,6 +195,17 @@ int launch_gemm_tc(const CUtensorMap* tmA, const CUtensorMap* tmB, int tile_n,
                    void* C, const int* d_nrows, int grid_rows, int N, int K, int epi,
                    const float* act_beta, int* d_err, cudaStream_t st);
 int make_tensor_map_bf16(CUtensorMap* tm, const void* base, int rows, int K, int box_rows);
+// Split-BF16 tcgen05 GEMM (adjoint): C = epi((A_hi + A_lo) W^T + ...) with A
+// given as a bf16 (hi, lo) pair whose sum is the FP32 operand; tmAhi / tmAlo box
+// 128 rows, tmB boxes tile_n (64, 128, 256) rows of W (N x K).  Epilogues:
+// SPL_TANH (C, C_lo) = split(tanh(acc + b)); SPL_OUT C (FP32) = mu + sigma (acc + b);
+// SPL_DTANH (C, C_lo) = split(acc (1 - h^2)), h = aux_hi + aux_lo (rows x N);
+// SPL_DTANH32 the same into FP32 C.  Row pitch of every output and aux: N.
+enum { SPL_TANH = 0, SPL_OUT = 1, SPL_DTANH = 2, SPL_DTANH32 = 3 };
+int launch_gemm_split(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo, const CUtensorMap* tmB, int tile_n,
+                      const float* bias, const float* out_mu, float out_sigma, void* C, __nv_bfloat16* C_lo,
+                      const __nv_bfloat16* aux_hi, const __nv_bfloat16* aux_lo, const int* d_nrows, int grid_rows,
+                      int N, int K, int epi, int* d_err, cudaStream_t st);
 // Output layer with swapped operands (rows of W as the MMA's M, activation rows
 // as its N, kSwapRows per CTA): tmW boxes 128 rows of W, tmX boxes kSwapRows
 // activation rows; FP32 out = mu + sigma (acc + b), row-major rows x N.
