@@ -29,14 +29,22 @@ namespace gpuns {
 
 namespace adj {
 
-__constant__ double c_glx[4] = {-0.86113631159405257522, -0.33998104358485626480,
-                                 0.33998104358485626480, 0.86113631159405257522};
-__constant__ double c_glw[4] = {0.34785484513745385737, 0.65214515486254614263,
-                                 0.65214515486254614263, 0.34785484513745385737};
+// 4-point Gauss-Legendre nodes and weights as compile-time constants of the
+// kernel's type (no double -> float conversions at run time).
+template <typename T> __device__ __forceinline__ T glx(int g) {
+    return g == 0 ? T(-0.86113631159405257522) : g == 1 ? T(-0.33998104358485626480)
+         : g == 2 ? T(0.33998104358485626480) : T(0.86113631159405257522);
+}
+template <typename T> __device__ __forceinline__ T glw(int g) {
+    return (g == 0 || g == 3) ? T(0.34785484513745385737) : T(0.65214515486254614263);
+}
 
 template <typename T> __device__ __forceinline__ const T* pick(const double* d, const float* f);
 template <> __device__ __forceinline__ const double* pick<double>(const double* d, const float*) { return d; }
 template <> __device__ __forceinline__ const float* pick<float>(const double*, const float* f) { return f; }
+template <typename T> __device__ __forceinline__ T pick_s(double d, float f);
+template <> __device__ __forceinline__ double pick_s<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pick_s<float>(double, float f) { return f; }
 
 template <typename T> __device__ __forceinline__ T ex(T x);
 template <> __device__ __forceinline__ double ex<double>(double x) { return exp(x); }
@@ -111,6 +119,12 @@ k_projection_adj(const AdjArgs A) {
     T* gtab = tab + PT;        // PT
     T* r = gtab + PT;          // D
     T* gm = r + D;             // D
+    const T* nz_mu = pick<T>(sp.nz_mean, sp.nz_mean_f);
+    const T* nz_sg = pick<T>(sp.nz_sigma, sp.nz_sigma_f);
+    const T* lnell = pick<T>(sp.lnell, sp.lnell_f);
+    const T* tmplT = pick<T>(sp.tmpl, sp.tmpl_f);
+    const T* dataT = pick<T>(sp.data, sp.data_f);
+    const T ia_piv = pick_s<T>(sp.ia_pivot, sp.ia_pivot_f), c1rho = pick_s<T>(sp.c1rho, sp.c1rho_f);
     const T* a_ = pick<T>(sp.a, sp.a_f);
     const T* lna_ = pick<T>(sp.lna, sp.lna_f);
     const T* z_ = pick<T>(sp.z, sp.z_f);
@@ -121,6 +135,7 @@ k_projection_adj(const AdjArgs A) {
     __shared__ T gth[128];
     __shared__ T gs[S_COUNT];
     __shared__ T red[64];
+    __shared__ T red2[8 * NP];                 // per-warp pair sums of one multipole
     __shared__ T Cl[NP * 64];
     __shared__ T gC[NP * 64];
     __shared__ T norm[NB];
@@ -149,10 +164,10 @@ k_projection_adj(const AdjArgs A) {
             const T a1 = a_[n + 1];
             const T mid = T(0.5) * (a + a1), half = T(0.5) * (a - a1);
             for (int g = 0; g < 4; ++g) {
-                const T ag = mid + half * (T)c_glx[g];
+                const T ag = mid + half * glx<T>(g);
                 const T lgg = lg<T>(ag);
                 const T e2 = om / (ag * ag * ag) + (T(1) - om) * ex<T>(-pde * lgg - T(3) * wa * (T(1) - ag));
-                inc += (T)c_glw[g] / (ag * ag * sqrt(e2));
+                inc += glw<T>(g) / (ag * ag * sqrt(e2));
             }
             inc *= chiH * half;
         }
@@ -178,7 +193,7 @@ k_projection_adj(const AdjArgs A) {
     for (int i = 0; i < NB; ++i) {
         T part = T(0);
         for (int n = tid; n < N; n += nt) {
-            const T u = (z_[n] - th[11 + i] - (T)sp.nz_mean[i]) / (T)sp.nz_sigma[i];
+            const T u = (z_[n] - th[11 + i] - nz_mu[i]) / nz_sg[i];
             const T rw = ex<T>(T(-0.5) * u * u);
             raw[i * N + n] = rw;
             part += wa_[n] * rw / (a_[n] * a_[n]);
@@ -199,7 +214,7 @@ k_projection_adj(const AdjArgs A) {
     }
     for (int n = tid; n < N; n += nt) {
         const T c = chi[n];
-        const T amp = A_IA * ex<T>(eta * lg<T>((T(1) + z_[n]) / (T)sp.ia_pivot)) * (T)sp.c1rho * om / Dg[n];
+        const T amp = A_IA * ex<T>(eta * lg<T>((T(1) + z_[n]) / ia_piv)) * c1rho * om / Dg[n];
         for (int i = 0; i < NB; ++i) {
             T v = T(0);
             if (n >= 1) {
@@ -226,12 +241,13 @@ k_projection_adj(const AdjArgs A) {
         }
     }
     __syncthreads();
-    const T lkmin = (T)sp.lnk_min, lkmax = (T)sp.lnk_max, inv_dk = T(1) / (T)sp.dlnk;
+    const T lkmin = pick_s<T>(sp.lnk_min, sp.lnk_min_f), lkmax = pick_s<T>(sp.lnk_max, sp.lnk_max_f);
+    const T inv_dk = pick_s<T>(1.0 / sp.dlnk, sp.inv_dlnk_f);
     // Limber: C_p(ell) (block reductions, fixed order)
     for (int l = 0; l < sp.n_ell; ++l) {
         T acc[NP];
         for (int p = 0; p < NP; ++p) acc[p] = T(0);
-        const T lne = (T)sp.lnell[l];
+        const T lne = lnell[l];
         for (int n = 1 + tid; n < N; n += nt) {
             T s = fmin(fmax(lne - lnchi[n], lkmin), lkmax);
             const T uk = (s - lkmin) * inv_dk;
@@ -247,10 +263,19 @@ k_projection_adj(const AdjArgs A) {
             for (int i = 0; i < NB; ++i)
                 for (int j = i; j < NB; ++j) { acc[p] += V[i * N + n] * V[j * N + n] * P; ++p; }
         }
+        // all NP pair sums at once: warp sums, then a fixed-order sum over warps
+#pragma unroll
         for (int p = 0; p < NP; ++p) {
-            const T s = block_sum(acc[p], red);
-            if (tid == 0) Cl[p * sp.n_ell + l] = s;
+            const T s = warp_sum(acc[p]);
+            if (lane == 0) red2[wid * NP + p] = s;
         }
+        __syncthreads();
+        if (tid < NP) {
+            T s = T(0);
+            for (int w = 0; w < (nt >> 5); ++w) s += red2[w * NP + tid];
+            Cl[tid * sp.n_ell + l] = s;
+        }
+        __syncthreads();
     }
     __syncthreads();
     // data vector, residual, whitening, log L
@@ -258,8 +283,8 @@ k_projection_adj(const AdjArgs A) {
         const int p = a / sp.n_ell, e = a % sp.n_ell;
         const int i = sp.pi[p], j = sp.pj[p];
         T m = (T(1) + th[11 + NB + i]) * (T(1) + th[11 + NB + j]) * Cl[p * sp.n_ell + e];
-        for (int t = 0; t < sp.n_tmpl; ++t) m += (T)sp.tmpl[(size_t)a * sp.n_tmpl + t] * th[11 + 2 * NB + t];
-        r[a] = (T)sp.data[a] - m;
+        for (int t = 0; t < sp.n_tmpl; ++t) m += tmplT[(size_t)a * sp.n_tmpl + t] * th[11 + 2 * NB + t];
+        r[a] = dataT[a] - m;
     }
     __syncthreads();
     const T* LT = reinterpret_cast<const T*>(A.LinvT);
@@ -290,7 +315,7 @@ k_projection_adj(const AdjArgs A) {
         gC[p * sp.n_ell + e] = g * fi * fj;
         atomicAdd(&gth[11 + NB + i], g * C * fj);
         atomicAdd(&gth[11 + NB + j], g * C * fi);
-        for (int t = 0; t < sp.n_tmpl; ++t) atomicAdd(&gth[11 + 2 * NB + t], g * (T)sp.tmpl[(size_t)a * sp.n_tmpl + t]);
+        for (int t = 0; t < sp.n_tmpl; ++t) atomicAdd(&gth[11 + 2 * NB + t], g * tmplT[(size_t)a * sp.n_tmpl + t]);
     }
     __syncthreads();
     // Limber + lookup reverse: threads own nodes, loop over multipoles
@@ -302,7 +327,7 @@ k_projection_adj(const AdjArgs A) {
         T wz[4];
         for (int pz = 0; pz < 4; ++pz) wz[pz] = zwp[4 * n + pz];
         for (int l = 0; l < sp.n_ell; ++l) {
-            const T s_raw = (T)sp.lnell[l] - lnchi[n];
+            const T s_raw = lnell[l] - lnchi[n];
             const bool clamped = (s_raw < lkmin) || (s_raw > lkmax);
             const T s = fmin(fmax(s_raw, lkmin), lkmax);
             const T uk = (s - lkmin) * inv_dk;
@@ -361,8 +386,8 @@ k_projection_adj(const AdjArgs A) {
     for (int n = 1 + tid; n < N; n += nt) {
         const T c = chi[n], an = a_[n];
         const T so = sqrt(omw[n]);
-        const T q = ex<T>(eta * lg<T>((T(1) + z_[n]) / (T)sp.ia_pivot));
-        const T ampc = q * (T)sp.c1rho * om / Dg[n];       // amp = A_IA * ampc
+        const T q = ex<T>(eta * lg<T>((T(1) + z_[n]) / ia_piv));
+        const T ampc = q * c1rho * om / Dg[n];       // amp = A_IA * ampc
         const T pc = pref * c / an;
         T g_so = T(0), g_c = T(0), g_amp = T(0);
         for (int i = 0; i < NB; ++i) {
@@ -385,7 +410,7 @@ k_projection_adj(const AdjArgs A) {
         gchi[n] += g_c;
         // amp = A_IA q c1rho Om / D
         l_aia += g_amp * ampc;
-        l_eta += g_amp * A_IA * ampc * lg<T>((T(1) + z_[n]) / (T)sp.ia_pivot);
+        l_eta += g_amp * A_IA * ampc * lg<T>((T(1) + z_[n]) / ia_piv);
         l_om += g_amp * A_IA * ampc / om;
         gD[n] += -g_amp * A_IA * ampc / Dg[n];
     }
@@ -423,19 +448,19 @@ k_projection_adj(const AdjArgs A) {
         for (int m = tid; m < N; m += nt) {
             const T gnc = raw[i * N + m];
             const T nc = nchi[i * N + m];
-            const T u = (z_[m] - th[11 + i] - (T)sp.nz_mean[i]) / (T)sp.nz_sigma[i];
+            const T u = (z_[m] - th[11 + i] - nz_mu[i]) / nz_sg[i];
             gE[m] += gnc * nc / Ez[m];
             l_chih += -gnc * nc / chiH;
             gnorm += -gnc * nc / nrm;
             // d raw / d Dz = raw u / sigma and nchi is proportional to raw
-            gdz += gnc * nc * u / (T)sp.nz_sigma[i];
+            gdz += gnc * nc * u / nz_sg[i];
         }
         gnorm = block_sum(gnorm, red);
         // norm = sum wa raw / a^2  ->  d norm / d Dz = sum wa raw u / sigma / a^2
         for (int m = tid; m < N; m += nt) {
-            const T u = (z_[m] - th[11 + i] - (T)sp.nz_mean[i]) / (T)sp.nz_sigma[i];
+            const T u = (z_[m] - th[11 + i] - nz_mu[i]) / nz_sg[i];
             const T rw = ex<T>(T(-0.5) * u * u);
-            gdz += gnorm * wa_[m] * rw * u / (T)sp.nz_sigma[i] / (a_[m] * a_[m]);
+            gdz += gnorm * wa_[m] * rw * u / nz_sg[i] / (a_[m] * a_[m]);
         }
         gdz = block_sum(gdz, red);
         l_chih = block_sum(l_chih, red);
@@ -493,13 +518,13 @@ k_projection_adj(const AdjArgs A) {
                 const T mid = T(0.5) * (a + a1), half = T(0.5) * (a - a1);
                 T inc = T(0);
                 for (int q = 0; q < 4; ++q) {
-                    const T ag = mid + half * (T)c_glx[q];
+                    const T ag = mid + half * glx<T>(q);
                     const T lgg = lg<T>(ag);
                     const T deg = ex<T>(-pde * lgg - T(3) * wa * (T(1) - ag));
                     const T e2 = om / (ag * ag * ag) + (T(1) - om) * deg;
                     const T F = T(1) / (ag * ag * sqrt(e2));
-                    inc += (T)c_glw[q] * F;
-                    const T gF = g * chiH * half * (T)c_glw[q];
+                    inc += glw<T>(q) * F;
+                    const T gF = g * chiH * half * glw<T>(q);
                     const T gE2 = gF * T(-0.5) * F / e2;
                     l_om += gE2 * (T(1) / (ag * ag * ag) - deg);
                     l_w0 += gE2 * (T(1) - om) * deg * (T(-3) * lgg);
@@ -552,12 +577,16 @@ int launch_projection_adj(const ShearParams& sp, const double* theta_full, const
     if (sp.n_ell > 64 || sp.n_params > 128) return NS_ENOTSUP;
     adj::AdjArgs A{sp, theta_full, table, LinvT, c0, scratch, (long long)adjoint_scratch_elems(sp), gtab, gfull,
                    logL, nrows};
+    auto go = [&](auto kern) -> int {
+        kern<<<grid_rows, 256, 0, st>>>(A);
+        return NS_OK;
+    };
     switch (sp.nb) {
-        case 1: adj::k_projection_adj<T, 1><<<grid_rows, 256, 0, st>>>(A); break;
-        case 2: adj::k_projection_adj<T, 2><<<grid_rows, 256, 0, st>>>(A); break;
-        case 3: adj::k_projection_adj<T, 3><<<grid_rows, 256, 0, st>>>(A); break;
-        case 4: adj::k_projection_adj<T, 4><<<grid_rows, 256, 0, st>>>(A); break;
-        case 5: adj::k_projection_adj<T, 5><<<grid_rows, 256, 0, st>>>(A); break;
+        case 1: NS_TRY(go(adj::k_projection_adj<T, 1>)); break;
+        case 2: NS_TRY(go(adj::k_projection_adj<T, 2>)); break;
+        case 3: NS_TRY(go(adj::k_projection_adj<T, 3>)); break;
+        case 4: NS_TRY(go(adj::k_projection_adj<T, 4>)); break;
+        case 5: NS_TRY(go(adj::k_projection_adj<T, 5>)); break;
         default: return NS_ENOTSUP;
     }
     NS_CUDA_TRY(cudaGetLastError());
