@@ -151,9 +151,8 @@ def limber_flops_per_eval(cfg) -> float:
 # input bytes, so it scales with the rows of a launch; it is reported only while
 # the kernel's sources are the ones the capture was taken on.
 LIMBER_TRAFFIC_BYTES_PER_EVAL = 25032960 / 384
-LIMBER_TRAFFIC_SOURCES = ("paper_2509_13307_gb300/csrc/projection.cu", "paper_2509_13307_gb300/csrc/async_copy.cuh",
-                          "paper_2509_13307_gb300/csrc/likelihood.cuh", "paper_2509_13307_gb300/csrc/common.cuh")
-LIMBER_TRAFFIC_SHA256 = "27fda3222cf7b6eab24c76a52e3f57081801b08521c4a3a0a31997754212094c"
+LIMBER_TRAFFIC_SOURCES = ("paper_2509_13307_gb300/csrc/projection.cu", "paper_2509_13307_gb300/csrc/async_copy.cuh")
+LIMBER_TRAFFIC_SHA256 = "bccda60cd961d8d13af9b26d7f4652bae5cad2f1c7c4aaf0d2b8c56abd6166f7"
 
 
 def limber_traffic(avg_rows: float):
