@@ -12,12 +12,13 @@
 //   k_directions    every (chain, move) slice direction of the iteration.
 //   k_chains_start  chain c starts at survivor floor(u (n - k)) (Philox START).
 //   rounds          until every chain has made R slice moves: k_slice_advance
-//                   (one warp per chain) consumes the previous proposal's log L,
+//                   (one warp per chain) consumes the previous proposals' log L,
 //                   runs the hit-and-run slice state machine (Neal 2003:
 //                   stepping out with width w, then shrinkage) through every
 //                   decision that needs no likelihood (points outside the unit
-//                   cube) and emits at most one proposal per chain into a
-//                   compacted batch; the fused likelihood then scores the batch.
+//                   cube) and emits its proposals into a compacted batch (both
+//                   ends of the slice while stepping out, one point while
+//                   shrinking); the fused likelihood then scores the batch.
 //                   Rounds are launched as a captured CUDA graph.
 //   k_insert        chain c's point replaces the c-th deleted slot; the
 //                   termination test ln(Z + X <L_live>) - ln Z < tol.
@@ -33,7 +34,7 @@
 
 namespace gpuns {
 
-enum Phase : int { PH_NEWMOVE = 0, PH_LEFT = 1, PH_RIGHT = 2, PH_SHRINK = 3, PH_DONE = 4 };
+enum Phase : int { PH_NEWMOVE = 0, PH_OUT = 1, PH_SHRINK = 3, PH_DONE = 4 };
 
 struct Scalars {
     double logZ, logX, H, lstar;
@@ -63,8 +64,10 @@ struct RunDev {
     int* ch_phase;
     int* ch_move;
     int* ch_step;
+    int* ch_step2;        // right-end step count while stepping out
     int* ch_evals;
     int* ch_row;
+    int* ch_row2;         // pending right-end row while stepping out
     double* prop;         // proposals (rows x prop_stride), cube coordinates
     int prop_stride;      // d for a single run; the largest d when runs share the batch
     int* batch_ctr;       // row counter of the round's batch (shared by packed runs)
@@ -193,7 +196,7 @@ __global__ void k_init_points(int n, int d, unsigned long long seed, double* __r
 // Chains start finished with no pending proposal until their first iteration.
 __global__ void k_reset_chains(RunDev r) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < r.k) { r.ch_phase[c] = PH_DONE; r.ch_row[c] = -1; r.ch_evals[c] = 0; }
+    if (c < r.k) { r.ch_phase[c] = PH_DONE; r.ch_row[c] = -1; r.ch_row2[c] = -1; r.ch_evals[c] = 0; }
 }
 
 __global__ void k_init_finish(RunDev r, const double* __restrict__ logL) {
@@ -346,8 +349,10 @@ __global__ void k_chains_start(RunDev r) {
         r.ch_phase[c] = PH_NEWMOVE;
         r.ch_move[c] = 0;
         r.ch_step[c] = 0;
+        r.ch_step2[c] = 0;
         r.ch_evals[c] = 0;
         r.ch_row[c] = -1;
+        r.ch_row2[c] = -1;
     }
     if (c == 0) { r.sc->n_active = r.k; r.sc->batch = 0; }
 }
@@ -422,8 +427,18 @@ __device__ __forceinline__ void emit_theta(const RunDev& r, int row, double y0, 
 }
 
 // One warp per chain; lanes own dimensions lane and lane + 32.
+// Stepping out (Neal 2003) widens the two ends of the slice independently:
+// the left end's tests never depend on the right end's and neither draws
+// random numbers, so both ends are proposed in the same round (up to two rows
+// per chain).  The points evaluated, their order within each end, the caps,
+// the final interval and every random number are those of widening the left
+// end first and then the right, so the bookkeeping equals the sequential
+// sampler's exactly.  Phase word: phase | done_ends << 8 (bit 0 left, bit 1
+// right); ch_row / ch_row2 hold the pending left (or shrinkage) / right rows,
+// ch_step / ch_step2 the left (or shrinkage) / right step counts.
 __device__ void advance_chain(const RunDev& r, int c, int lane) {
-    int phase = r.ch_phase[c];
+    const int pw = r.ch_phase[c];
+    int phase = pw & 0xff, ends = (pw >> 8) & 3;
     if (phase == PH_DONE) return;
     const int d = r.d;
     const int it = (int)r.sc->iter;
@@ -434,33 +449,47 @@ __device__ void advance_chain(const RunDev& r, int c, int lane) {
     const bool has0 = lane < d, has1 = lane + 32 < d;
     double x0 = has0 ? x[lane] : 0.0, x1 = has1 ? x[lane + 32] : 0.0;
     double u0v = has0 ? u[lane] : 0.0, u1v = has1 ? u[lane + 32] : 0.0;
-    int move = r.ch_move[c], step = r.ch_step[c], row = r.ch_row[c], evals = r.ch_evals[c];
+    int move = r.ch_move[c], step = r.ch_step[c], step2 = r.ch_step2[c];
+    int row = r.ch_row[c], row2 = r.ch_row2[c], evals = r.ch_evals[c];
     double l = r.ch_l[c], rr = r.ch_r[c], t = r.ch_t[c], chL = r.ch_L[c];
     int flags = 0;
-
-    if (row >= 0) {
-        const double v = r.logL[row];
+    auto inside_of = [&](int rw) {
+        const double v = r.logL[rw];
         const bool fin = isfinite(v);
         if (!fin) flags |= NS_BIT_NONFINITE;
-        const bool inside = fin && (v > lstar);
-        if (phase == PH_LEFT) {
-            if (inside) { l -= w; ++step; } else { phase = PH_RIGHT; step = 0; }
-        } else if (phase == PH_RIGHT) {
-            if (inside) { rr += w; ++step; } else { phase = PH_SHRINK; step = 0; }
-        } else if (phase == PH_SHRINK) {
-            if (inside) {
-                x0 = __dadd_rn(x0, __dmul_rn(t, u0v));
-                x1 = __dadd_rn(x1, __dmul_rn(t, u1v));
-                chL = v;
-                ++move;
-                phase = PH_NEWMOVE;
-            } else {
-                if (t < 0.0) l = t; else rr = t;
-                ++step;
-            }
+        return fin && (v > lstar);
+    };
+
+    if (phase == PH_OUT) {
+        if (row >= 0) { if (inside_of(row)) { l -= w; ++step; } else ends |= 1; row = -1; }
+        if (row2 >= 0) { if (inside_of(row2)) { rr += w; ++step2; } else ends |= 2; row2 = -1; }
+    } else if (phase == PH_SHRINK && row >= 0) {
+        const double v = r.logL[row];
+        if (inside_of(row)) {
+            x0 = __dadd_rn(x0, __dmul_rn(t, u0v));
+            x1 = __dadd_rn(x1, __dmul_rn(t, u1v));
+            chL = v;
+            ++move;
+            phase = PH_NEWMOVE;
+        } else {
+            if (t < 0.0) l = t; else rr = t;
+            ++step;
         }
         row = -1;
     }
+    // the proposal at s along the direction, or -1 (no evaluation) when it
+    // leaves the open unit cube
+    auto propose = [&](double s) -> int {
+        const double y0 = __dadd_rn(x0, __dmul_rn(s, u0v)), y1 = __dadd_rn(x1, __dmul_rn(s, u1v));
+        const bool inc = (!has0 || (y0 > 0.0 && y0 < 1.0)) && (!has1 || (y1 > 0.0 && y1 < 1.0));
+        if (!__all_sync(0xffffffffu, inc)) return -1;
+        int rw = 0;
+        if (lane == 0) rw = atomicAdd(r.batch_ctr, 1);
+        rw = __shfl_sync(0xffffffffu, rw, 0);
+        emit_theta(r, rw, has0 ? y0 : 0.0, has1 ? y1 : 0.0, lane);
+        ++evals;
+        return rw;
+    };
     for (int guard = 0; guard < 4 * r.cap_steps + 8; ++guard) {
         if (phase == PH_NEWMOVE) {
             if (move >= r.R) { phase = PH_DONE; break; }
@@ -471,33 +500,22 @@ __device__ void advance_chain(const RunDev& r, int c, int lane) {
             const double s0 = philox_uniforms(r.seed, P_STEPOUT, 0, (uint32_t)it, (uint32_t)c, (uint32_t)move).a;
             l = __dmul_rn(-w, s0);
             rr = l + w;
-            phase = PH_LEFT;
-            step = 0;
+            phase = PH_OUT;
+            ends = 0;
+            step = step2 = 0;
             continue;
         }
-        if (phase == PH_LEFT || phase == PH_RIGHT) {
-            if (step >= r.cap_steps) {
-                flags |= NS_BIT_SLICE_CAP;
-                if (phase == PH_LEFT) phase = PH_RIGHT; else phase = PH_SHRINK;
-                step = 0;
-                continue;
+        if (phase == PH_OUT) {
+            if (!(ends & 1) && row < 0) {
+                if (step >= r.cap_steps) { flags |= NS_BIT_SLICE_CAP; ends |= 1; }
+                else if ((row = propose(l)) < 0) ends |= 1;
             }
-            const double s = (phase == PH_LEFT) ? l : rr;
-            const double y0 = __dadd_rn(x0, __dmul_rn(s, u0v)), y1 = __dadd_rn(x1, __dmul_rn(s, u1v));
-            const bool inc = (!has0 || (y0 > 0.0 && y0 < 1.0)) && (!has1 || (y1 > 0.0 && y1 < 1.0));
-            if (!__all_sync(0xffffffffu, inc)) {
-                if (phase == PH_LEFT) phase = PH_RIGHT; else phase = PH_SHRINK;
-                step = 0;
-                continue;
+            if (!(ends & 2) && row2 < 0) {
+                if (step2 >= r.cap_steps) { flags |= NS_BIT_SLICE_CAP; ends |= 2; }
+                else if ((row2 = propose(rr)) < 0) ends |= 2;
             }
-            int rw = 0;
-            if (lane == 0) rw = atomicAdd(r.batch_ctr, 1);
-            row = __shfl_sync(0xffffffffu, rw, 0);
-            if (has0) r.prop[(size_t)row * r.prop_stride + lane] = y0;
-            if (has1) r.prop[(size_t)row * r.prop_stride + lane + 32] = y1;
-            emit_theta(r, row, has0 ? y0 : 0.0, has1 ? y1 : 0.0, lane);
-            ++evals;
-            break;
+            if (ends == 3) { phase = PH_SHRINK; step = 0; continue; }
+            break;                                  // an end is being evaluated
         }
         if (phase == PH_SHRINK) {
             if (step >= r.cap_steps) {
@@ -509,20 +527,11 @@ __device__ void advance_chain(const RunDev& r, int c, int lane) {
             const double us = philox_uniforms(r.seed, P_SHRINK, (uint32_t)step, (uint32_t)it, (uint32_t)c,
                                               (uint32_t)move).a;
             t = __dadd_rn(l, __dmul_rn(us, __dsub_rn(rr, l)));
-            const double y0 = __dadd_rn(x0, __dmul_rn(t, u0v)), y1 = __dadd_rn(x1, __dmul_rn(t, u1v));
-            const bool inc = (!has0 || (y0 > 0.0 && y0 < 1.0)) && (!has1 || (y1 > 0.0 && y1 < 1.0));
-            if (!__all_sync(0xffffffffu, inc)) {
+            if ((row = propose(t)) < 0) {
                 if (t < 0.0) l = t; else rr = t;
                 ++step;
                 continue;
             }
-            int rw = 0;
-            if (lane == 0) rw = atomicAdd(r.batch_ctr, 1);
-            row = __shfl_sync(0xffffffffu, rw, 0);
-            if (has0) r.prop[(size_t)row * r.prop_stride + lane] = y0;
-            if (has1) r.prop[(size_t)row * r.prop_stride + lane + 32] = y1;
-            emit_theta(r, row, has0 ? y0 : 0.0, has1 ? y1 : 0.0, lane);
-            ++evals;
             break;
         }
         break;
@@ -530,7 +539,8 @@ __device__ void advance_chain(const RunDev& r, int c, int lane) {
     if (has0) { x[lane] = x0; u[lane] = u0v; }
     if (has1) { x[lane + 32] = x1; u[lane + 32] = u1v; }
     if (lane == 0) {
-        r.ch_phase[c] = phase; r.ch_move[c] = move; r.ch_step[c] = step; r.ch_row[c] = row;
+        r.ch_phase[c] = phase | (ends << 8); r.ch_move[c] = move; r.ch_step[c] = step; r.ch_step2[c] = step2;
+        r.ch_row[c] = row; r.ch_row2[c] = row2;
         r.ch_evals[c] = evals; r.ch_l[c] = l; r.ch_r[c] = rr; r.ch_t[c] = t; r.ch_L[c] = chL;
         if (flags) atomicOr(&r.sc->status, flags);
         if (phase == PH_DONE) atomicSub(&r.sc->n_active, 1);
@@ -752,7 +762,8 @@ static int launch_round(ns_run* r, int g, cudaStream_t st, const StageProbe* pro
     NS_CUDA_TRY(launch_pdl(k_set_int, dim3(1), dim3(1), 0, st, r->grd[g].batch_ctr, 0));
     NS_CUDA_TRY(launch_pdl(k_slice_advance, dim3((r->grd[g].grp_chains + kSliceWarps - 1) / kSliceWarps),
                            dim3(32 * kSliceWarps), 0, st, r->grd[g]));
-    return run_likelihood(r->p, ws, r->grd[g].grp_chains, ws->logL, nullptr, st, probe);
+    // up to two proposals per chain (both stepping-out ends)
+    return run_likelihood(r->p, ws, 2 * r->grd[g].grp_chains, ws->logL, nullptr, st, probe);
 }
 
 // Per-group copies of the run state for the round kernels (rebuilt with the
@@ -861,7 +872,9 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
     r->n_pad = 1;
     while (r->n_pad < n) r->n_pad <<= 1;
     int s;
-    const int cap = std::max(n, k);
+    // rounds hold up to two proposals per chain (both stepping-out ends); the
+    // initial live set is scored through the same workspace
+    const int cap = std::max(n, 2 * k);
     if ((s = workspace_create(p, cap, &r->ws))) return fail(s);
     RunDev& rd = r->rd;
     rd.n = n; rd.k = k; rd.d = d; rd.R = r->R; rd.cap_steps = cfg->step_cap;
@@ -886,8 +899,10 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
     RA(ch_phase, sizeof(int) * k);
     RA(ch_move, sizeof(int) * k);
     RA(ch_step, sizeof(int) * k);
+    RA(ch_step2, sizeof(int) * k);
     RA(ch_evals, sizeof(int) * k);
     RA(ch_row, sizeof(int) * k);
+    RA(ch_row2, sizeof(int) * k);
     RA(prop, sizeof(double) * cap * d);
     RA(sc, sizeof(Scalars));
 #undef RA
@@ -920,7 +935,7 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
     r->n_groups = (k >= 2 && want == 2) ? 2 : 1;
     if (r->n_groups > 1) {
         r->k0 = (k + 1) / 2;
-        if ((s = workspace_create(p, k - r->k0, &r->ws1))) return fail(s);
+        if ((s = workspace_create(p, 2 * (k - r->k0), &r->ws1))) return fail(s);
     }
     // initial live points
     k_init_points<<<(n + 127) / 128, 128, 0, r->st>>>(n, d, cfg->seed, rd.prop);
@@ -1157,7 +1172,7 @@ static int multi_launch_round(ns_multi* m, cudaStream_t st) {
     k_slice_advance_multi<<<(m->total_chains + kSliceWarps - 1) / kSliceWarps, 32 * kSliceWarps, 0, st>>>(
         m->d_runs, m->d_chain_off, m->n_runs);
     NS_CUDA_TRY(cudaGetLastError());
-    return run_likelihood(m->model, &m->ws, m->total_chains, m->ws.logL, nullptr, st);
+    return run_likelihood(m->model, &m->ws, 2 * m->total_chains, m->ws.logL, nullptr, st);
 }
 
 static int multi_build_graph(ns_multi* m, int rounds) {
@@ -1211,7 +1226,8 @@ extern "C" int ns_multi_init(const ns_problem* const* problems, int n_runs, cons
     }
     m->total_chains = off[n_runs];
     int s;
-    if ((s = workspace_create(p0, m->total_chains, &m->ws))) return fail(s);
+    // a round holds up to two proposals per chain (both stepping-out ends)
+    if ((s = workspace_create(p0, 2 * m->total_chains, &m->ws))) return fail(s);
     void* v;
     auto alloc = [&](size_t bytes) -> void* {
         void* q = nullptr;
