@@ -82,6 +82,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive FP32 columns of one TMEM lane per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int CW>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[CW]) {
+    if constexpr (CW == 16) tmem_ld16(taddr, v);
+    else tmem_ld32(taddr, v);
+}
+
 __device__ __forceinline__ float tanh_fast(float x) {
     float y;
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -174,13 +194,15 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     fence_after();
     __syncwarp();
     if (ok && !s_fail) {
+        // column chunks of CW accumulators per thread (tile row)
+        constexpr int CW = BN < 32 ? BN : 32;
         const int row = m0 + warp * 32 + lane;
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
-        for (int c = 0; c < BN / 32; ++c) {
-            float v[32];
-            tmem_ld32(lane_addr + c * 32, v);
-            const int col0 = n0 + c * 32;
+        for (int c = 0; c < BN / CW; ++c) {
+            float v[CW];
+            tmem_ld<CW>(lane_addr + c * CW, v);
+            const int col0 = n0 + c * CW;
             if (row >= M || col0 >= N) continue;
             if (EPI == 0 || EPI == 2) {
                 // hidden layer: tanh (EPI 0) or sigmoid-linear with per-unit
@@ -191,10 +213,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     return (g + (1.f - g) / (1.f + __expf(-__ldg(act_beta + col) * x))) * x;
                 };
                 __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(Cout) + (size_t)row * N + col0;
-                if (col0 + 32 <= N && (N % 8) == 0) {
-                    uint32_t pk[16];
+                if (col0 + CW <= N && (N % 8) == 0) {
+                    uint32_t pk[CW / 2];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
+                    for (int j = 0; j < CW / 2; ++j) {
                         const float a0 = act(v[2 * j] + __ldg(bias + col0 + 2 * j), col0 + 2 * j);
                         const float a1 = act(v[2 * j + 1] + __ldg(bias + col0 + 2 * j + 1), col0 + 2 * j + 1);
                         __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, a1);
@@ -202,18 +224,19 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     }
                     uint4* o4 = reinterpret_cast<uint4*>(out);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) o4[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                    for (int q = 0; q < CW / 8; ++q)
+                        o4[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
+                    for (int j = 0; j < CW; ++j)
                         if (col0 + j < N) out[j] = __float2bfloat16_rn(act(v[j] + bias[col0 + j], col0 + j));
                 }
             } else {
                 float* out = reinterpret_cast<float*>(Cout) + (size_t)row * N + col0;
-                if (col0 + 32 <= N && (N % 4) == 0) {
+                if (col0 + CW <= N && (N % 4) == 0) {
                     float4* o4 = reinterpret_cast<float4*>(out);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
+                    for (int q = 0; q < CW / 4; ++q) {
                         float4 r;
                         r.x = __ldg(out_mu + col0 + 4 * q + 0) + out_sigma * (v[4 * q + 0] + __ldg(bias + col0 + 4 * q + 0));
                         r.y = __ldg(out_mu + col0 + 4 * q + 1) + out_sigma * (v[4 * q + 1] + __ldg(bias + col0 + 4 * q + 1));
@@ -223,7 +246,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
+                    for (int j = 0; j < CW; ++j)
                         if (col0 + j < N) out[j] = out_mu[col0 + j] + out_sigma * (v[j] + bias[col0 + j]);
                 }
             }
@@ -577,6 +600,7 @@ int launch_gemm_tc(const CUtensorMap* tmA, const CUtensorMap* tmB, int tile_n, c
                    int epi, const float* act_beta, int* d_err, cudaStream_t st) {
     if (grid_rows <= 0) return NS_OK;
     switch (tile_n) {
+        case 16: return tc::launch_bn<16>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, act_beta, d_err, st);
         case 32: return tc::launch_bn<32>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, act_beta, d_err, st);
         case 64: return tc::launch_bn<64>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, act_beta, d_err, st);
         case 128: return tc::launch_bn<128>(tmA, tmB, bias, out_mu, out_sigma, C, d_nrows, grid_rows, N, K, epi, act_beta, d_err, st);

@@ -331,7 +331,7 @@ static int cmb_setup(ns_problem* p, const ns_problem_desc* desc) {
 }
 
 // Tile autotuner for the tensor-core hidden layers: each candidate N-tile
-// width (32, 64, 128) runs the layer on max_batch rows (at most 384, about the
+// width (16, 32, 64, 128) runs the layer on max_batch rows (at most 384, about the
 // average batch of a nested-sampling likelihood round with k = 500) of the
 // workspace-sized activations, timed with CUDA events over 5 launches after a
 // warm-up; a wider tile replaces a narrower one only when it is at least 3%
@@ -371,7 +371,7 @@ static int autotune_hidden_tiles(ns_problem* p, int last_hidden) {
         if (s) return done(s);
         int best = p->tile_n[l];
         float best_ms = 1e30f;
-        for (int tn : {32, 64, 128}) {
+        for (int tn : {16, 32, 64, 128}) {
             if (tn > N) continue;
             if ((s = make_tensor_map_bf16(&tmB, p->d_W[l], N, K, tn))) return done(s);
             auto run = [&]() {
