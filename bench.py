@@ -367,12 +367,13 @@ def ours(args):
     t_job, ev_job = job_totals(t_local, ev_local, world, dev)
     value = ev_job / t_job
 
-    # per round (one chain group): batch reset, slice (with the prior
-    # transform), windows, emulator input layer, one GEMM per further layer,
-    # Limber, whitening; per iteration 7 more (sort and delete, column means,
-    # covariance, Cholesky, directions, chain starts, insert).
+    # per round (one chain group): slice (with the prior transform and the
+    # next round's batch-counter reset), windows, emulator input layer, one
+    # GEMM per further layer, Limber, whitening; per iteration 7 more (sort and
+    # delete, column means, covariance, Cholesky, directions, chain starts,
+    # insert).
     n_layers = len(inp["emu_W"])
-    per_round = 5 + (n_layers - 1) + 1
+    per_round = 5 + (n_layers - 1)
     gpu_launches = res["rounds"] * per_round + 7 * res["iters"]
 
     # ---------------- roofline of the dominant kernel (Limber stage), timed live

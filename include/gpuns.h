@@ -184,7 +184,8 @@ typedef struct {
     double width;                 /* initial slice width along a unit-Mahalanobis direction */
     int step_cap;                 /* cap on stepping-out steps and on shrinkage steps */
     double ridge;                 /* added to the live-covariance diagonal */
-    int rounds_per_sync;          /* likelihood rounds launched between host checks (<= 0: auto) */
+    int rounds_per_sync;          /* likelihood rounds launched between host checks (<= 0: 16);
+                                     rounded up to an even number */
     int chain_groups;             /* 1 or 2 groups of chains whose likelihood rounds run on two
                                      streams and overlap on the GPU (results are identical);
                                      <= 0: 1 */

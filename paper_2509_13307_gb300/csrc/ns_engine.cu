@@ -40,6 +40,7 @@ struct Scalars {
     double logZ, logX, H, lstar;
     long long n_dead, iter, evals;
     int status, n_active, batch, converged;
+    int batch2[2];        // round batch counters of chain group 0 (round i uses batch2[i & 1])
 };
 
 struct RunDev {
@@ -71,6 +72,7 @@ struct RunDev {
     double* prop;         // proposals (rows x prop_stride), cube coordinates
     int prop_stride;      // d for a single run; the largest d when runs share the batch
     int* batch_ctr;       // row counter of the round's batch (shared by packed runs)
+    int* batch_next;      // the next round's counter, zeroed by this round's slice kernel (or null)
     int run_id;
     int chain0;           // first chain of this group of rounds
     int grp_chains;       // chains of this group
@@ -354,7 +356,7 @@ __global__ void k_chains_start(RunDev r) {
         r.ch_row[c] = -1;
         r.ch_row2[c] = -1;
     }
-    if (c == 0) { r.sc->n_active = r.k; r.sc->batch = 0; }
+    if (c == 0) { r.sc->n_active = r.k; r.sc->batch = 0; r.sc->batch2[0] = 0; r.sc->batch2[1] = 0; }
 }
 
 // Slice directions for every (chain, move) of the iteration, one warp each:
@@ -553,6 +555,8 @@ __device__ void advance_chain(const RunDev& r, int c, int lane) {
 constexpr int kSliceWarps = 1;
 __global__ void __launch_bounds__(32 * kSliceWarps) k_slice_advance(RunDev r) {
     pdl_begin();
+    // the previous round (the last reader of the other counter) has completed
+    if (blockIdx.x == 0 && threadIdx.x == 0 && r.batch_next) *r.batch_next = 0;
     const int c = blockIdx.x * kSliceWarps + (threadIdx.x >> 5);
     if (c >= r.grp_chains) return;
     advance_chain(r, r.chain0 + c, threadIdx.x & 31);
@@ -711,6 +715,7 @@ struct ns_run {
     // chain groups: group 0 uses rd / ws; group 1 (chains [k0, k)) its own
     // batch, proposals and likelihood workspace, with rounds on a second stream
     int n_groups = 1, k0 = 0;
+    int* grp1_ctr = nullptr;      // chain group 1's pair of round batch counters
     Workspace ws1;
     RunDev grd[2]{};
     cudaStream_t cap_st1 = nullptr;
@@ -757,13 +762,26 @@ static int sync_scalars(ns_run* r) {
     return NS_OK;
 }
 
-static int launch_round(ns_run* r, int g, cudaStream_t st, const StageProbe* probe) {
+// Round i of a captured launch: the batch counts into counter i & 1 of the
+// group's pair, and the slice kernel zeroes the other one for round i + 1
+// (no separate reset launch; launches hold an even number of rounds, so each
+// starts on counter 0, and every iteration starts with both zero).
+static int launch_round(ns_run* r, int g, int i, cudaStream_t st, const StageProbe* probe) {
     Workspace* ws = g ? &r->ws1 : &r->ws;
-    NS_CUDA_TRY(launch_pdl(k_set_int, dim3(1), dim3(1), 0, st, r->grd[g].batch_ctr, 0));
-    NS_CUDA_TRY(launch_pdl(k_slice_advance, dim3((r->grd[g].grp_chains + kSliceWarps - 1) / kSliceWarps),
-                           dim3(32 * kSliceWarps), 0, st, r->grd[g]));
+    int* pair = g ? r->grp1_ctr : r->rd.sc->batch2;
+    RunDev rd = r->grd[g];
+    rd.batch_ctr = pair + (i & 1);
+    rd.batch_next = pair + ((i + 1) & 1);
+    int* const saved = ws->d_nrows;
+    ws->d_nrows = rd.batch_ctr;
+    int s = NS_OK;
+    if (launch_pdl(k_slice_advance, dim3((rd.grp_chains + kSliceWarps - 1) / kSliceWarps), dim3(32 * kSliceWarps), 0,
+                   st, rd) != cudaSuccess)
+        s = NS_ECUDA;
     // up to two proposals per chain (both stepping-out ends)
-    return run_likelihood(r->p, ws, 2 * r->grd[g].grp_chains, ws->logL, nullptr, st, probe);
+    if (s == NS_OK) s = run_likelihood(r->p, ws, 2 * rd.grp_chains, ws->logL, nullptr, st, probe);
+    ws->d_nrows = saved;
+    return s;
 }
 
 // Per-group copies of the run state for the round kernels (rebuilt with the
@@ -809,9 +827,9 @@ static int build_graph(ns_run* r, int rounds) {
             s = NS_ECUDA;
     }
     for (int i = 0; i < rounds && s == NS_OK; ++i)
-        s = launch_round(r, 0, r->cap_st, (i == 0 && r->probe.stage != PROBE_NONE) ? &r->probe : nullptr);
+        s = launch_round(r, 0, i, r->cap_st, (i == 0 && r->probe.stage != PROBE_NONE) ? &r->probe : nullptr);
     if (r->n_groups > 1) {
-        for (int i = 0; i < rounds && s == NS_OK; ++i) s = launch_round(r, 1, r->cap_st1, nullptr);
+        for (int i = 0; i < rounds && s == NS_OK; ++i) s = launch_round(r, 1, i, r->cap_st1, nullptr);
         if (s == NS_OK && (cudaEventRecord(r->ev_gjoin, r->cap_st1) != cudaSuccess ||
                            cudaStreamWaitEvent(r->cap_st, r->ev_gjoin, 0) != cudaSuccess))
             s = NS_ECUDA;
@@ -936,6 +954,9 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
     if (r->n_groups > 1) {
         r->k0 = (k + 1) / 2;
         if ((s = workspace_create(p, 2 * (k - r->k0), &r->ws1))) return fail(s);
+        if ((s = run_alloc(r, 2 * sizeof(int), &v))) return fail(s);
+        r->grp1_ctr = (int*)v;
+        if (cudaMemsetAsync(v, 0, 2 * sizeof(int), r->st) != cudaSuccess) return fail(NS_ECUDA);
     }
     // initial live points
     k_init_points<<<(n + 127) / 128, 128, 0, r->st>>>(n, d, cfg->seed, rd.prop);
@@ -950,9 +971,11 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
     return NS_OK;
 }
 
+// Rounds per captured graph launch: even, so that the alternating batch
+// counters hand over from one launch to the next (launch_round).
 static int rounds_per_sync(const ns_run* r) {
-    if (r->cfg.rounds_per_sync > 0) return r->cfg.rounds_per_sync;
-    return 16;
+    const int R = r->cfg.rounds_per_sync > 0 ? r->cfg.rounds_per_sync : 16;
+    return (R + 1) & ~1;
 }
 
 static int one_iteration(ns_run* r) {
