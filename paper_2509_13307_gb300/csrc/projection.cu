@@ -347,7 +347,7 @@ __device__ __forceinline__ void limber_pair_f32(const float* __restrict__ U, int
     const float2 one = make_float2(1.f, 1.f), m1 = make_float2(-1.f, -1.f), two = make_float2(2.f, 2.f);
     const float2 three = make_float2(3.f, 3.f), m3 = make_float2(-3.f, -3.f), four = make_float2(4.f, 4.f);
     const float2 m5 = make_float2(-5.f, -5.f);
-    const float nk2 = (float)(n_k - 2);
+    const float gmax = 8388608.f + (float)(n_k - 2);
     float2 a2[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) a2[p] = make_float2(0.f, 0.f);
@@ -360,15 +360,16 @@ __device__ __forceinline__ void limber_pair_f32(const float* __restrict__ U, int
         for (int i = 0; i < NB; ++i) { const float x = V[i * Np + n]; vv[i] = make_float2(x, x); }
         const float u0 = (fminf(fmaxf(lne0 - lc, lkmin), lkmax) - lkmin) * inv_dk;
         const float u1 = (fminf(fmaxf(lne1 - lc, lkmin), lkmax) - lkmin) * inv_dk;
-        // cell index without conversion instructions: adding 2^23 rounds a
-        // value in [0, 2^22) to an integer held in the low mantissa bits.
-        // (u - 1/2) rounds to floor(u) except at exact integers, where the
-        // cell below with t = 1 gives the same interpolant.
-        const float f0 = fminf(fmaxf(__fadd_rn(__fadd_rn(u0 - 0.5f, 8388608.f), -8388608.f), 0.f), nk2);
-        const float f1 = fminf(fmaxf(__fadd_rn(__fadd_rn(u1 - 0.5f, 8388608.f), -8388608.f), 0.f), nk2);
-        const int ik0 = __float_as_int(__fadd_rn(f0, 8388608.f)) - 0x4B000000;
-        const int ik1 = __float_as_int(__fadd_rn(f1, 8388608.f)) - 0x4B000000;
-        const float2 t = make_float2(u0 - f0, u1 - f1);
+        // cell index without conversion instructions: g = u + (2^23 - 1/2),
+        // correctly rounded, is 2^23 + round(u - 1/2), an integer held in the
+        // low mantissa bits (u >= 0, so g >= 2^23).  round(u - 1/2) = floor(u)
+        // except at exact integers, where the cell below with t = 1 gives the
+        // same interpolant.  The clamp to cell n_k - 2 is taken on g (exact).
+        const float g0 = fminf(__fadd_rn(u0, 8388607.5f), gmax);
+        const float g1 = fminf(__fadd_rn(u1, 8388607.5f), gmax);
+        const int ik0 = __float_as_int(g0) - 0x4B000000;
+        const int ik1 = __float_as_int(g1) - 0x4B000000;
+        const float2 t = make_float2(u0 - __fadd_rn(g0, -8388608.f), u1 - __fadd_rn(g1, -8388608.f));
         const float2 t2 = __fmul2_rn(t, t);
         // doubled Catmull-Rom weights (the z-taps are doubled too)
         const float2 k0 = __fmul2_rn(t, __ffma2_rn(t, __ffma2_rn(t, m1, two), m1));
