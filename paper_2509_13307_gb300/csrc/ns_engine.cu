@@ -69,8 +69,7 @@ struct RunDev {
     int* ch_evals;
     int* ch_row;
     int* ch_row2;         // pending right-end row while stepping out
-    double* prop;         // proposals (rows x prop_stride), cube coordinates
-    int prop_stride;      // d for a single run; the largest d when runs share the batch
+    double* prop;         // the initial live points' cube coordinates (n x d)
     int* batch_ctr;       // row counter of the round's batch (shared by packed runs)
     int* batch_next;      // the next round's counter, zeroed by this round's slice kernel (or null)
     int run_id;
@@ -926,7 +925,6 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
 #undef RA
     rd.logL = r->ws.logL;
     k_reset_chains<<<(k + 127) / 128, 128, 0, r->st>>>(rd);
-    rd.prop_stride = d;
     rd.batch_ctr = &rd.sc->batch;
     rd.run_id = 0;
     rd.chain0 = 0;
@@ -1152,8 +1150,7 @@ struct ns_multi {
     cudaStream_t st = nullptr;
     cudaStream_t cap_st = nullptr;
     Workspace ws;
-    int stride = 0, total_chains = 0;
-    double* prop = nullptr;
+    int total_chains = 0;
     RunDev* d_runs = nullptr;
     int* d_chain_off = nullptr;
     std::vector<void*> owned;
@@ -1178,8 +1175,6 @@ static int multi_refresh_runs(ns_multi* m) {
     std::vector<RunDev> h(m->n_runs);
     for (int i = 0; i < m->n_runs; ++i) {
         h[i] = m->runs[i]->rd;
-        h[i].prop = m->prop;
-        h[i].prop_stride = m->stride;
         h[i].batch_ctr = m->ws.d_nrows;
         h[i].theta_full = m->ws.theta_full;
         h[i].run_id = i;
@@ -1244,7 +1239,6 @@ extern "C" int ns_multi_init(const ns_problem* const* problems, int n_runs, cons
         int s = ns_init(problems[i], &ci, stream, &r);
         if (s) return fail(s);
         m->runs.push_back(r);
-        m->stride = std::max(m->stride, r->d);
         off[i + 1] = off[i] + r->k;
     }
     m->total_chains = off[n_runs];
@@ -1258,10 +1252,9 @@ extern "C" int ns_multi_init(const ns_problem* const* problems, int n_runs, cons
         m->owned.push_back(q);
         return q;
     };
-    m->prop = (double*)alloc(sizeof(double) * (size_t)m->total_chains * m->stride);
     m->d_runs = (RunDev*)alloc(sizeof(RunDev) * n_runs);
     m->d_chain_off = (int*)alloc(sizeof(int) * (n_runs + 1));
-    if (!m->prop || !m->d_runs || !m->d_chain_off) return fail(NS_ENOMEM);
+    if (!m->d_runs || !m->d_chain_off) return fail(NS_ENOMEM);
     (void)v;
     if (cudaMemcpy(m->d_chain_off, off.data(), sizeof(int) * (n_runs + 1), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(NS_ECUDA);
