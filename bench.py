@@ -194,6 +194,18 @@ def replace_seed(sc, rank):
     return replace(sc, seed=sc.seed + 100 * rank)
 
 
+def measured_peaks() -> dict:
+    """The measured HBM copy bandwidth and bf16 GEMM throughput of
+    the GB300s, else the recipe's fallback figures."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops_sustained": float(d["bf16_tflops_sustained"]),
+                "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
 def fp32_alu_peak_tflops(sm_mhz: float) -> float:
     """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -391,8 +403,30 @@ def ours(args):
                     "flop_per_eval": flops, "avg_launch_ms": prof["ms"] / prof["launches"],
                     "avg_rows_per_launch": prof["rows"] / prof["launches"],
                     "peak_basis": "FP32 ALU 152 SM x 128 lanes x 2 x 2070 MHz (no measured FP32 peak in MEASURED_PEAKS.json)"}
+        if roofline["traffic"]:
+            # the same kernel against HBM: measured bytes per launch / launch time
+            gbs = roofline["traffic"] / (roofline["avg_launch_ms"] * 1e-3) / 1e9
+            roofline["hbm_achieved_GBps"] = gbs
+            roofline["hbm_frac"] = gbs / measured_peaks()["hbm_gbs"]
 
     extra = {}
+    # ---------------- the emulator's output layer (tcgen05) against the
+    # measured sustained bf16 tensor peak, timed live in the rounds
+    try:
+        r_emu = timed_steps(prob, 1, 2, profile="emu_out")
+        pe = r_emu["prof"]
+        if pe and pe["launches"] > 0 and pe["ms"] > 0:
+            k_out = inp["emu_W"][-1].shape
+            flop_row = 2.0 * k_out[0] * k_out[1]
+            ach = pe["rows"] * flop_row / (pe["ms"] * 1e-3) / 1e12
+            pk = measured_peaks()["bf16_tflops_sustained"]
+            extra["roofline_emulator_output_gemm"] = {
+                "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "kernel": "k_gemm_tc_swap<256> (emulator output layer %d -> %d, bf16 x bf16 -> fp32)" % (k_out[1], k_out[0]),
+                "avg_launch_ms": pe["ms"] / pe["launches"], "avg_rows_per_launch": pe["rows"] / pe["launches"],
+                "peak_basis": "measured cuBLAS bf16 sustained (MEASURED_PEAKS.json)"}
+    except Exception as exc:
+        extra["roofline_emulator_output_gemm_error"] = repr(exc)[:200]
     # ---------------- plain FP32 form on the same workload
     if args.precision != "fp32":
         p32 = Problem(inp, "fp32", max_batch=sc.n_live)

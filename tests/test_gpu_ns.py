@@ -65,6 +65,21 @@ def test_bookkeeping_shear5_plain_ns():
     _compare_iterations(ons, run, 3)
 
 
+def test_bookkeeping_odd_rounds_per_launch():
+    """Rounds per graph launch are rounded up to an even number (the round
+    batch counters alternate by parity): an odd request still reproduces the
+    oracle's bookkeeping exactly."""
+    from paper_2509_13307_gb300 import Problem, NestedRun
+    cfg = w.gauss_test(4, n_live=50, n_delete=10, seed=13)
+    inp = w.make_gauss_inputs(cfg)
+    orc = GaussOracle(inp)
+    ons = NestedSampler.from_config(orc.loglike, 4, cfg.sampler)
+    ons.initialise()
+    prob = Problem(inp, "fp64", max_batch=50)
+    run = NestedRun.from_config(prob, cfg.sampler, rounds_per_sync=3)
+    _compare_iterations(ons, run, 3)
+
+
 def test_bookkeeping_shear_tiny_batched():
     from paper_2509_13307_gb300 import NestedRun
     inp, orc = oracle_for("shear_tiny")
