@@ -113,30 +113,46 @@ template <> __device__ inline __nv_bfloat16 cvt_out<__nv_bfloat16, float>(float 
 template <typename T> __device__ inline T cvt_in(T v) { return v; }
 __device__ inline float cvt_in(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-// Input layer: h = act(W0 x + b0), x = (theta[inputs] - center) / scale.
-template <typename T, typename TO>
-__global__ void k_emu_input(const double* __restrict__ theta_full, int P, const int* __restrict__ inputs,
-                            const double* __restrict__ center, const double* __restrict__ scale,
-                            const double* __restrict__ inv_scale, int K0,
-                            const T* __restrict__ W0, const T* __restrict__ b0, ActDev<T> act, int N,
-                            TO* __restrict__ out, const int* __restrict__ nrows) {
+// Input layer: h = act(W0 x + b0), x = (theta[inputs] - center) / scale.  A
+// CTA takes kInRows consecutive rows; thread t owns units t, t + blockDim, ...
+// and keeps a unit's bias and K0 (<= KMAX) weights in registers over the CTA's
+// rows, so the weights are read once per CTA and the launch has
+// ceil(rows / kInRows) CTAs rather than one per (row, 256 units).
+constexpr int kInRows = 4;
+template <typename T, typename TO, int KMAX>
+__global__ void __launch_bounds__(256)
+k_emu_input(const double* __restrict__ theta_full, int P, const int* __restrict__ inputs,
+            const double* __restrict__ center, const double* __restrict__ scale,
+            const double* __restrict__ inv_scale, int K0,
+            const T* __restrict__ W0, const T* __restrict__ b0, ActDev<T> act, int N,
+            TO* __restrict__ out, const int* __restrict__ nrows) {
     pdl_begin();
-    const int row = blockIdx.y;
-    if (row >= *nrows) return;
-    __shared__ T x[32];
-    if (threadIdx.x < K0) {
-        const int j = threadIdx.x;
+    const int M = *nrows;
+    const int r0 = blockIdx.x * kInRows;
+    if (r0 >= M) return;
+    const int nr = min(kInRows, M - r0);
+    __shared__ T x[kInRows][KMAX];
+    for (int i = threadIdx.x; i < nr * K0; i += blockDim.x) {
+        const int r = i / K0, j = i - r * K0;
         // FP64 standardisation; reduced-precision emulators multiply by the
         // reciprocal scale (an FP64 divide is a long sequence on GB300's FP64 pipe)
-        const double v = theta_full[(size_t)row * P + inputs[j]] - center[j];
-        x[j] = sizeof(T) == 8 ? (T)(v / scale[j]) : (T)(v * inv_scale[j]);
+        const double v = theta_full[(size_t)(r0 + r) * P + inputs[j]] - center[j];
+        x[r][j] = sizeof(T) == 8 ? (T)(v / scale[j]) : (T)(v * inv_scale[j]);
     }
     __syncthreads();
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    T acc = b0[n];
-    for (int j = 0; j < K0; ++j) acc = fma(W0[(size_t)n * K0 + j], x[j], acc);
-    out[(size_t)row * N + n] = cvt_out<TO, T>(act_apply<T>(act, n, acc));
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        T w[KMAX];
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) w[j] = j < K0 ? W0[(size_t)n * K0 + j] : T(0);
+        const T bn = b0[n];
+        for (int r = 0; r < nr; ++r) {
+            T acc = bn;
+#pragma unroll
+            for (int j = 0; j < KMAX; ++j)
+                if (j < K0) acc = fma(w[j], x[r][j], acc);
+            out[(size_t)(r0 + r) * N + n] = cvt_out<TO, T>(act_apply<T>(act, n, acc));
+        }
+    }
 }
 
 // C[M x N] = epi(A[M x K] W[N x K]^T + b).  Threads own an interleaved
@@ -272,6 +288,26 @@ static ActDev<T> layer_act(const ns_problem* p, int l) {
     return a;
 }
 
+template <typename T, typename TO>
+static int launch_emu_input(const ns_problem* p, const Workspace* ws, int grid_rows, TO* out, bool pdl,
+                            cudaStream_t st) {
+    const int K0 = p->dims[0], H1 = p->dims[1];
+    const dim3 g((grid_rows + kInRows - 1) / kInRows);
+    auto kern = K0 <= 8 ? k_emu_input<T, TO, 8> : k_emu_input<T, TO, 32>;
+    if (pdl) {
+        NS_CUDA_TRY(launch_pdl(kern, g, dim3(256), 0, st, (const double*)ws->theta_full, p->P,
+                               (const int*)p->d_inputs, (const double*)p->d_in_center, (const double*)p->d_in_scale,
+                               (const double*)p->d_in_inv_scale, K0, (const T*)p->d_W[0], (const T*)p->d_b[0],
+                               layer_act<T>(p, 0), H1, out, (const int*)ws->d_nrows));
+    } else {
+        kern<<<g, 256, 0, st>>>(ws->theta_full, p->P, p->d_inputs, p->d_in_center, p->d_in_scale,
+                                p->d_in_inv_scale, K0, (const T*)p->d_W[0], (const T*)p->d_b[0], layer_act<T>(p, 0),
+                                H1, out, ws->d_nrows);
+        NS_CUDA_TRY(cudaGetLastError());
+    }
+    return NS_OK;
+}
+
 // The emulator's last layer: W h + b, de-standardised as mu + s * (.), written to out.
 struct Head {
     const void* W;
@@ -291,13 +327,7 @@ static Head model_head(const ns_problem* p, void* out) {
 template <typename T>
 static int run_emulator_simt(const ns_problem* p, Workspace* ws, int grid_rows, cudaStream_t st, const Head& hd) {
     const int L = p->n_layers;
-    const int K0 = p->dims[0], H1 = p->dims[1];
-    dim3 g0((H1 + 255) / 256, grid_rows);
-    k_emu_input<T, T><<<g0, 256, 0, st>>>(ws->theta_full, p->P, p->d_inputs, p->d_in_center, p->d_in_scale,
-                                          p->d_in_inv_scale,
-                                          K0, (const T*)p->d_W[0], (const T*)p->d_b[0], layer_act<T>(p, 0), H1,
-                                          (T*)ws->act[0], ws->d_nrows);
-    NS_CUDA_TRY(cudaGetLastError());
+    NS_TRY((launch_emu_input<T, T>(p, ws, grid_rows, (T*)ws->act[0], false, st)));
     int cur = 0;
     for (int l = 1; l < L; ++l) {
         const int K = p->dims[l], N = p->dims[l + 1];
@@ -334,13 +364,7 @@ static int probe_end(const StageProbe* pr, int stage, cudaStream_t st) {
 static int run_emulator_bf16(const ns_problem* p, Workspace* ws, int grid_rows, cudaStream_t st,
                              const StageProbe* probe, const Head* hd) {
     const int L = p->n_layers;
-    const int K0 = p->dims[0], H1 = p->dims[1];
-    dim3 g0((H1 + 255) / 256, grid_rows);
-    NS_CUDA_TRY(launch_pdl(k_emu_input<float, __nv_bfloat16>, g0, dim3(256), 0, st, (const double*)ws->theta_full,
-                           p->P, (const int*)p->d_inputs, (const double*)p->d_in_center,
-                           (const double*)p->d_in_scale, (const double*)p->d_in_inv_scale, K0,
-                           (const float*)p->d_W[0], (const float*)p->d_b[0],
-                           layer_act<float>(p, 0), H1, (__nv_bfloat16*)ws->act[0], (const int*)ws->d_nrows));
+    NS_TRY((launch_emu_input<float, __nv_bfloat16>(p, ws, grid_rows, (__nv_bfloat16*)ws->act[0], true, st)));
     int cur = 0;
     for (int l = 1; l < L; ++l) {
         const int K = p->dims[l], N = p->dims[l + 1];
