@@ -55,8 +55,6 @@ struct Workspace {
     void* table_fine = nullptr;   // cap x n_z*n_k (coarse-z emulators)
     void* resid = nullptr;        // cap x D residuals
     void* win = nullptr;          // cap x (nb + 1) x pitch: ln chi and windows (pitch = N rounded up to 4)
-    void* chi2_part = nullptr;    // cap x ceil(D / 64) partial chi^2 sums (FP64-sized)
-    int* chi2_done = nullptr;     // ceil(cap / 16) arrival counters of the whitening tiles (zeroed)
     double* logL = nullptr;       // cap
     // tcgen05 tensor maps (BF16 precision): A operand of layer l >= 1 and its output
     std::vector<CUtensorMap> tmA;
@@ -170,8 +168,8 @@ int launch_limber(const ShearParams& sp, const double* theta_full, const T* tabl
 bool projection_fits(const ShearParams& sp, int elt);
 // Whitened chi^2 and log L = c0 - chi^2 / 2 (projection.cu).
 template <typename TR, typename TA>
-int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL, void* partial, int* done,
-                const int* nrows, int grid_rows, cudaStream_t st);
+int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL, const int* nrows, int grid_rows,
+                cudaStream_t st);
 
 // Adjoint of the shear projection (adjoint.cu).
 int adjoint_scratch_elems(const ShearParams& sp);

@@ -123,11 +123,6 @@ int workspace_create(const ns_problem* p, int cap, Workspace* ws) {
         if (p->cmb_solve == NS_SOLVE_LITERAL && p->cmb_form == NS_CMB_GAUSS) {
             NS_TRY(dalloc(sizeof(double) * (size_t)cap * p->D, &v, ws->owned));
             ws->resid = v;
-            NS_TRY(dalloc(sizeof(double) * (size_t)cap * ((p->D + 63) / 64), &v, ws->owned));
-            ws->chi2_part = v;
-            NS_TRY(dalloc(sizeof(int) * (size_t)((cap + 15) / 16), &v, ws->owned));
-            ws->chi2_done = (int*)v;
-            NS_CUDA_TRY(cudaMemset(v, 0, sizeof(int) * (size_t)((cap + 15) / 16)));
         }
         if (p->precision == NS_PREC_BF16) {
             ws->tmA.resize(p->n_layers);
@@ -160,11 +155,6 @@ int workspace_create(const ns_problem* p, int cap, Workspace* ws) {
     NS_CUDA_TRY(cudaStreamCreateWithFlags(&ws->side, cudaStreamNonBlocking));
     NS_CUDA_TRY(cudaEventCreateWithFlags(&ws->ev_fork, cudaEventDisableTiming));
     NS_CUDA_TRY(cudaEventCreateWithFlags(&ws->ev_join, cudaEventDisableTiming));
-    NS_TRY(dalloc(sizeof(double) * (size_t)cap * ((p->sp.D + 63) / 64), &v, ws->owned));
-    ws->chi2_part = v;
-    NS_TRY(dalloc(sizeof(int) * (size_t)((cap + 15) / 16), &v, ws->owned));
-    ws->chi2_done = (int*)v;
-    NS_CUDA_TRY(cudaMemset(v, 0, sizeof(int) * (size_t)((cap + 15) / 16)));
 
     if (p->precision == NS_PREC_BF16 || p->precision == NS_PREC_BF16_F64CHI2) {
         ws->tmA.resize(p->n_layers);

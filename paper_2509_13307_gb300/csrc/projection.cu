@@ -19,15 +19,20 @@
 //      FP32x2 arithmetic) and the pair sums V_i V_j P.  A transposed warp
 //      reduction, then a fixed-order sum over warps (deterministic).
 //   5. data vector (1 + m_i)(1 + m_j) C_ij(ell) + T b and residual d - m.
-// k_whiten: Y = R L^-T in tiles of 16 rows x 64 columns (b <= a), per-tile
-//   row sums of y^2; the last tile of a row block adds them in fixed order
-//   and writes log L = c0 - chi^2 / 2 in FP64.
+// k_whiten: Y = R L^-T for blocks of rows, the 64-column tiles (b <= a) of a
+//   row block split over the CTAs of a thread-block cluster; rank 0 adds the
+//   ranks' row sums of y^2 in fixed order and writes log L = c0 - chi^2 / 2
+//   in FP64.
 #include <algorithm>
+
+#include <cooperative_groups.h>
 
 #include "likelihood.cuh"
 #include "async_copy.cuh"
 
 namespace gpuns {
+
+namespace cg = cooperative_groups;
 
 // 4-point Gauss-Legendre nodes and weights on [-1, 1] as compile-time
 // constants of the kernel's own type (no double -> float conversions at run
@@ -560,15 +565,18 @@ k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* _
     }
 }
 
-// Whitening Y = R L^-T over tiles of 16 rows x 64 columns (b <= a).  The
+// Whitening Y = R L^-T for a block of WR rows (8, or 16 for long data
+// vectors).  The ntile column tiles of 64 (b <= a) are split over the cs
+// CTAs of a cluster (rank q takes tiles q, q + cs, ...).  Per tile the
 // reduction range (rounded up to 32, zero-filled) is staged in shared memory
 // with 16-byte cp.async copies, in as few chunks as fit; the 8 warps split it
-// (warp w takes the w-th eighth), each lane accumulating 16 rows x 2 columns,
-// with the four R values of a row read as one vector.  The eight partial
-// tiles are added in fixed order; per-tile row sums of y^2 go to `partial`;
-// the last tile CTA of a row block (arrival counter) adds them in fixed order
-// and writes log L = c0 - chi^2 / 2.
-constexpr int kWR = 16, kWC = 64, kWarps = 8;
+// (warp w takes the w-th eighth), each lane accumulating WR rows x 2 columns
+// (one packed FP32x2 FMA per row and k in FP32), with the four R values of a
+// row read as one vector.  The warps' partial tiles are added in warp order
+// and the squares of y of a row in a fixed lane tree; warp r keeps row r's
+// sum over the CTA's tiles in tile order; rank 0 adds the ranks' sums in rank
+// order (cluster shared memory) and writes log L = c0 - chi^2 / 2.
+constexpr int kWC = 64, kWarps = 8, kWClusterMax = 8;
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
@@ -597,160 +605,192 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
     v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
 }
 
-template <typename TR, typename TA>
+template <typename TR, typename TA, int WR>
 __global__ void __launch_bounds__(256)
-k_whiten(const TR* __restrict__ resid, int D, const TA* __restrict__ LinvT, TA* __restrict__ partial, int ntile,
-         int KC, int* __restrict__ done, double c0, double* __restrict__ logL, const int* __restrict__ nrows) {
+k_whiten(const TR* __restrict__ resid, int D, const TA* __restrict__ LinvT, int ntile, int KC, double c0,
+         double* __restrict__ logL, const int* __restrict__ nrows) {
+    static_assert(WR == 8 || WR == 16, "8 or 16 rows per block");
     pdl_begin();
     const int M = *nrows;
-    const int row0 = blockIdx.y * kWR;
-    if (row0 >= M) return;
-    const int a0 = blockIdx.x * kWC;
+    const int row0 = blockIdx.y * WR;
+    if (row0 >= M) return;                         // every CTA of the cluster has this row block
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TA* Ls = reinterpret_cast<TA*>(smem_raw);                 // KC x kWC
-    TR* Rs = reinterpret_cast<TR*>(Ls + (size_t)KC * kWC);    // kWR x KC
-    TA* red = Ls;                                             // kWarps x kWR x kWC, after the last chunk
-    __shared__ int s_last;
+    TR* Rs = reinterpret_cast<TR*>(Ls + (size_t)KC * kWC);    // WR x KC
+    TA* red = Ls;                                             // kWarps x WR x kWC, after a tile's last chunk
+    __shared__ TA s_rank_sum[kWClusterMax][WR];               // rank 0: the ranks' row sums
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int b_end = min(D, a0 + kWC);
-    const int Kp = (b_end + 31) & ~31;
     const bool vecL = (D * sizeof(TA)) % 16 == 0 && (reinterpret_cast<uintptr_t>(LinvT) & 15) == 0;
     const bool vecR = (D * sizeof(TR)) % 16 == 0 && (reinterpret_cast<uintptr_t>(resid) & 15) == 0;
-    TA acc[kWR][2];
+    // rows handled by this thread in the per-tile finish: WR = 8: warp w -> row w,
+    // two columns per lane; WR = 16: half-warps -> rows, four columns per lane
+    constexpr int TPR = 256 / WR;                  // threads per row (32 or 16)
+    constexpr int CPT = kWC / TPR;                 // columns per thread (2 or 4)
+    const int fr = tid / TPR, fc = (tid % TPR) * CPT;
+    TA run = TA(0);                                // row fr: sum of y^2 over this CTA's tiles
+    for (int tile = rank; tile < ntile; tile += cs) {
+        const int a0 = tile * kWC;
+        const int b_end = min(D, a0 + kWC);
+        const int Kp = (b_end + 31) & ~31;
+        TA acc[WR][2];
 #pragma unroll
-    for (int r = 0; r < kWR; ++r) { acc[r][0] = TA(0); acc[r][1] = TA(0); }
-    for (int k0 = 0; k0 < Kp; k0 += KC) {
-        const int len = min(KC, Kp - k0);          // multiple of 32
-        const int lv = max(0, min(len, b_end - k0)); // rows holding data
-        if (k0 > 0) __syncthreads();
-        // L^-T rows k0 .. k0 + len (zero beyond b_end and beyond column D)
-        if (vecL) {
-            constexpr int per = 16 / sizeof(TA), vpr = kWC / per;
-            for (int q = tid; q < len * vpr; q += 256) {
-                const int bb = q / vpr, v = q % vpr;
-                TA* dst = Ls + bb * kWC + v * per;
-                if (bb < lv && a0 + v * per < D) cp_async16(dst, LinvT + (size_t)(k0 + bb) * D + a0 + v * per);
-                else for (int e = 0; e < per; ++e) dst[e] = TA(0);
+        for (int r = 0; r < WR; ++r) { acc[r][0] = TA(0); acc[r][1] = TA(0); }
+        for (int k0 = 0; k0 < Kp; k0 += KC) {
+            const int len = min(KC, Kp - k0);          // multiple of 32
+            const int lv = max(0, min(len, b_end - k0)); // rows holding data
+            __syncthreads();                           // previous chunk / tile finish done with Ls, Rs
+            // L^-T rows k0 .. k0 + len (zero beyond b_end and beyond column D)
+            if (vecL) {
+                constexpr int per = 16 / sizeof(TA), vpr = kWC / per;
+                for (int q = tid; q < len * vpr; q += 256) {
+                    const int bb = q / vpr, v = q % vpr;
+                    TA* dst = Ls + bb * kWC + v * per;
+                    if (bb < lv && a0 + v * per < D) cp_async16(dst, LinvT + (size_t)(k0 + bb) * D + a0 + v * per);
+                    else for (int e = 0; e < per; ++e) dst[e] = TA(0);
+                }
+            } else {
+                for (int q = tid; q < len * kWC; q += 256) {
+                    const int bb = q / kWC, aa = q % kWC;
+                    if (bb < lv && a0 + aa < D) cp_async_elt(Ls + bb * kWC + aa, LinvT + (size_t)(k0 + bb) * D + a0 + aa);
+                    else Ls[bb * kWC + aa] = TA(0);
+                }
             }
-        } else {
-            for (int q = tid; q < len * kWC; q += 256) {
-                const int bb = q / kWC, aa = q % kWC;
-                if (bb < lv && a0 + aa < D) cp_async_elt(Ls + bb * kWC + aa, LinvT + (size_t)(k0 + bb) * D + a0 + aa);
-                else Ls[bb * kWC + aa] = TA(0);
+            // R rows row0 .. row0 + WR, columns k0 .. k0 + len (zero beyond b_end / M)
+            if (vecR) {
+                constexpr int per = 16 / sizeof(TR);
+                const int vpr = len / per;
+                for (int q = tid; q < WR * vpr; q += 256) {
+                    const int rr = q / vpr, v = q % vpr;
+                    TR* dst = Rs + rr * KC + v * per;
+                    if (row0 + rr < M && v * per < lv) cp_async16(dst, resid + (size_t)(row0 + rr) * D + k0 + v * per);
+                    else for (int e = 0; e < per; ++e) dst[e] = TR(0);
+                }
+            } else {
+                for (int q = tid; q < WR * len; q += 256) {
+                    const int rr = q / len, cc = q % len;
+                    if (row0 + rr < M && cc < lv) cp_async_elt(Rs + rr * KC + cc, resid + (size_t)(row0 + rr) * D + k0 + cc);
+                    else Rs[rr * KC + cc] = TR(0);
+                }
             }
-        }
-        // R rows row0 .. row0 + 16, columns k0 .. k0 + len (zero beyond b_end / M)
-        if (vecR) {
-            constexpr int per = 16 / sizeof(TR);
-            const int vpr = len / per;
-            for (int q = tid; q < kWR * vpr; q += 256) {
-                const int rr = q / vpr, v = q % vpr;
-                TR* dst = Rs + rr * KC + v * per;
-                if (row0 + rr < M && v * per < lv) cp_async16(dst, resid + (size_t)(row0 + rr) * D + k0 + v * per);
-                else for (int e = 0; e < per; ++e) dst[e] = TR(0);
-            }
-        } else {
-            for (int q = tid; q < kWR * len; q += 256) {
-                const int rr = q / len, cc = q % len;
-                if (row0 + rr < M && cc < lv) cp_async_elt(Rs + rr * KC + cc, resid + (size_t)(row0 + rr) * D + k0 + cc);
-                else Rs[rr * KC + cc] = TR(0);
-            }
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        const int kw = len / kWarps;               // multiple of 4
-        const int kb = wid * kw;
-        for (int k = kb; k < kb + kw; k += 4) {
-            TA l0[4], l1[4];
+            cp_async_wait_all();
+            __syncthreads();
+            const int kw = len / kWarps;               // multiple of 4
+            const int kb = wid * kw;
+            for (int k = kb; k < kb + kw; k += 4) {
+                TA l0[4], l1[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) { l0[j] = Ls[(k + j) * kWC + lane]; l1[j] = Ls[(k + j) * kWC + lane + 32]; }
+                for (int j = 0; j < 4; ++j) { l0[j] = Ls[(k + j) * kWC + lane]; l1[j] = Ls[(k + j) * kWC + lane + 32]; }
 #pragma unroll
-            for (int r = 0; r < kWR; ++r) {
-                TR rv[4];
-                ld4(Rs + r * KC + k, rv);
+                for (int r = 0; r < WR; ++r) {
+                    TR rv[4];
+                    ld4(Rs + r * KC + k, rv);
+                    if constexpr (sizeof(TA) == 4) {
+                        float2 a2 = make_float2(acc[r][0], acc[r][1]);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    acc[r][0] += (TA)rv[j] * l0[j];
-                    acc[r][1] += (TA)rv[j] * l1[j];
+                        for (int j = 0; j < 4; ++j)
+                            a2 = __ffma2_rn(make_float2((float)rv[j], (float)rv[j]), make_float2(l0[j], l1[j]), a2);
+                        acc[r][0] = a2.x;
+                        acc[r][1] = a2.y;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            acc[r][0] = fma((TA)rv[j], l0[j], acc[r][0]);
+                            acc[r][1] = fma((TA)rv[j], l1[j], acc[r][1]);
+                        }
+                    }
                 }
             }
         }
-    }
-    __syncthreads();
+        __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kWR; ++r) {
-        red[(wid * kWR + r) * kWC + lane] = acc[r][0];
-        red[(wid * kWR + r) * kWC + lane + 32] = acc[r][1];
-    }
-    __syncthreads();
-    // thread t: row t / 16, columns 4 (t % 16) .. + 3
-    {
-        const int r = tid >> 4, cb = (tid & 15) * 4;
+        for (int r = 0; r < WR; ++r) {
+            red[(wid * WR + r) * kWC + lane] = acc[r][0];
+            red[(wid * WR + r) * kWC + lane + 32] = acc[r][1];
+        }
+        __syncthreads();
         TA sq = TA(0);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < CPT; ++e) {
             TA y = TA(0);
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) y += red[(w * kWR + r) * kWC + cb + e];
-            if (a0 + cb + e < D) sq += y * y;
+            for (int w = 0; w < kWarps; ++w) y += red[(w * WR + fr) * kWC + fc + e];
+            if (a0 + fc + e < D) sq += y * y;
         }
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o, 16);
-        if ((tid & 15) == 0 && row0 + r < M) partial[(size_t)(row0 + r) * ntile + blockIdx.x] = sq;
+        for (int o = TPR / 2; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o, TPR);
+        run += sq;
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = atomicAdd(&done[blockIdx.y], 1) == ntile - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (tid < kWR && row0 + tid < M) {
-        const int r = row0 + tid;
-        // issue the tile loads together, then add in tile order
-        TA v[16];
-#pragma unroll
-        for (int t = 0; t < 16; ++t) v[t] = (t < ntile) ? __ldcg(partial + (size_t)r * ntile + t) : TA(0);
+    // rank 0 collects the ranks' row sums in its shared memory
+    if (tid % TPR == 0) {
+        TA* dst = cluster.map_shared_rank(&s_rank_sum[0][0], 0);
+        dst[rank * WR + fr] = run;
+    }
+    cluster.sync();
+    if (rank == 0 && tid < WR && row0 + tid < M) {
         TA s2 = TA(0);
-#pragma unroll
-        for (int t = 0; t < 16; ++t) s2 += v[t];
-        for (int t = 16; t < ntile; ++t) s2 += __ldcg(partial + (size_t)r * ntile + t);
-        logL[r] = c0 - 0.5 * (double)s2;
+        for (int q = 0; q < cs; ++q) s2 += s_rank_sum[q][tid];
+        logL[row0 + tid] = c0 - 0.5 * (double)s2;
     }
-    if (tid == 0) done[blockIdx.y] = 0;
 }
 
 template <typename TR, typename TA>
-static size_t whiten_smem(int KC) {
-    return std::max((size_t)KC * kWC * sizeof(TA) + (size_t)kWR * KC * sizeof(TR),
-                    (size_t)kWarps * kWR * kWC * sizeof(TA));
+static size_t whiten_smem(int KC, int WR) {
+    return std::max((size_t)KC * kWC * sizeof(TA) + (size_t)WR * KC * sizeof(TR),
+                    (size_t)kWarps * WR * kWC * sizeof(TA));
 }
 
-template <typename TR, typename TA>
-int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL, void* partial, int* done,
-                const int* nrows, int grid_rows, cudaStream_t st) {
+template <typename TR, typename TA, int WR>
+static int launch_whiten(const TR* resid, int D, const TA* LinvT, double c0, double* logL, const int* nrows,
+                         int grid_rows, size_t smem_cap, cudaStream_t st) {
     const int ntile = (D + kWC - 1) / kWC;
-    // the whole (padded) reduction range in one chunk when it fits ~200 KB
+    const int cs = std::min(ntile, kWClusterMax);
+    // the whole (padded) reduction range in one chunk when it fits smem_cap
     const int Kp = (D + 31) & ~31;
-    const size_t per_k = (size_t)kWC * sizeof(TA) + (size_t)kWR * sizeof(TR);
-    int KC = (int)std::min<size_t>((size_t)Kp, ((200 * 1024) / per_k) & ~(size_t)31);
+    const size_t per_k = (size_t)kWC * sizeof(TA) + (size_t)WR * sizeof(TR);
+    int KC = (int)std::min<size_t>((size_t)Kp, (smem_cap / per_k) & ~(size_t)31);
     KC = std::max(KC, 32);
-    const size_t smem = whiten_smem<TR, TA>(KC);
+    const size_t smem = whiten_smem<TR, TA>(KC, WR);
     static bool attr = false;
     if (!attr) {
-        NS_CUDA_TRY(cudaFuncSetAttribute(k_whiten<TR, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 64));
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_whiten<TR, TA, WR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         227 * 1024 - 1024));
         attr = true;
     }
-    dim3 g(ntile, (grid_rows + kWR - 1) / kWR);
-    NS_CUDA_TRY(launch_pdl(k_whiten<TR, TA>, g, dim3(256), smem, st, resid, D, LinvT, (TA*)partial, ntile, KC, done,
-                           c0, logL, nrows));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, (grid_rows + WR - 1) / WR);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr2[2];
+    attr2[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr2[0].val.programmaticStreamSerializationAllowed = 1;
+    attr2[1].id = cudaLaunchAttributeClusterDimension;
+    attr2[1].val.clusterDim.x = cs;
+    attr2[1].val.clusterDim.y = 1;
+    attr2[1].val.clusterDim.z = 1;
+    cfg.attrs = attr2;
+    cfg.numAttrs = 2;
+    NS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_whiten<TR, TA, WR>, resid, D, LinvT, ntile, KC, c0, logL, nrows));
     return NS_OK;
 }
-template int launch_chi2<float, float>(const float*, int, const float*, double, double*, void*, int*, const int*,
-                                       int, cudaStream_t);
-template int launch_chi2<float, double>(const float*, int, const double*, double, double*, void*, int*, const int*,
-                                        int, cudaStream_t);
-template int launch_chi2<double, double>(const double*, int, const double*, double, double*, void*, int*, const int*,
-                                         int, cudaStream_t);
+
+template <typename TR, typename TA>
+int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL, const int* nrows, int grid_rows,
+                cudaStream_t st) {
+    // short data vectors: 8-row blocks of up to ~100 KB (two CTAs per SM);
+    // long ones: 16-row blocks (half the passes over L^-T) with the whole SM
+    if ((D + kWC - 1) / kWC <= kWClusterMax)
+        return launch_whiten<TR, TA, 8>(resid, D, LinvT, c0, logL, nrows, grid_rows, 100 * 1024, st);
+    return launch_whiten<TR, TA, 16>(resid, D, LinvT, c0, logL, nrows, grid_rows, 200 * 1024, st);
+}
+template int launch_chi2<float, float>(const float*, int, const float*, double, double*, const int*, int,
+                                       cudaStream_t);
+template int launch_chi2<float, double>(const float*, int, const double*, double, double*, const int*, int,
+                                        cudaStream_t);
+template int launch_chi2<double, double>(const double*, int, const double*, double, double*, const int*, int,
+                                         cudaStream_t);
 
 template <typename T>
 static size_t windows_smem(const ShearParams& sp) {
