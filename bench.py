@@ -145,14 +145,14 @@ def limber_flops_per_eval(cfg) -> float:
     return cfg.n_ell * (N - 1) * (32 + 10 + nb + 2 * npairs) + D * (3 + 2 * cfg.n_tmpl)
 
 
-# DRAM traffic of k_limber per evaluation from one ncu capture (25,032,704 bytes
+# DRAM traffic of k_limber per evaluation from one ncu capture (25,032,448 bytes
 # read and 0 written at 384 evaluations per launch, cold L2, the summary in
 # profiles/k_limber_bf16_shear39_B384.md).  It equals the kernel's algorithmic
 # input bytes, so it scales with the rows of a launch; it is reported only while
 # the kernel's sources are the ones the capture was taken on.
-LIMBER_TRAFFIC_BYTES_PER_EVAL = 25032704 / 384
+LIMBER_TRAFFIC_BYTES_PER_EVAL = 25032448 / 384
 LIMBER_TRAFFIC_SOURCES = ("paper_2509_13307_gb300/csrc/projection.cu", "paper_2509_13307_gb300/csrc/async_copy.cuh")
-LIMBER_TRAFFIC_SHA256 = "689ead86d13c3233b74ad673d5de86597fe307d5106a6f32bc760e9bd533c9fe"
+LIMBER_TRAFFIC_SHA256 = "ed49b15fbd51b1355a40582e4de978d03d441cca696e7d4bb4fbf0c8ff566fb1"
 
 
 def limber_traffic(avg_rows: float):
