@@ -6,13 +6,21 @@
 //   A: activations, row-major (K-major), bf16;  W: weights [N][K], bf16.
 //   epi 0: tanh, stored bf16 (next layer's A);  epi 1: mu + sigma * v, FP32.
 //
-// One CTA computes a 128 x BN tile.  Warp 0 (one lane) issues TMA loads of
-// 128 x 64 and BN x 64 bf16 boxes (128-byte swizzle) into a STAGES-deep ring
-// guarded by full/empty mbarriers; warp 1 (one lane) issues
+// One CTA computes a 128 x BN tile.  A ring of STAGES slots guarded by
+// full/empty mbarriers holds KPS k-blocks of 64 per slot; warp 0 (one lane)
+// loads a slot's A box (128 x 64 x KPS bf16, 128-byte swizzle) and B box
+// (BN x 64 x KPS); warp 1 (one lane) issues
 // tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = BN, K = 16) into a TMEM
 // accumulator and releases ring slots with tcgen05.commit; warp 2 owns the
 // TMEM allocation.  All four warps then drain TMEM with tcgen05.ld (warp w
 // reads lanes 32w..32w+31 = tile rows), apply the epilogue and store.
+// A thread's bulk copies complete one after another (a few hundred cycles
+// each on GB300, almost independent of their size), so the operand rate of a
+// CTA is set by its copy instructions per byte: with K a multiple of 128 a
+// slot holds two k-blocks, each operand's pair loaded by one copy through a
+// 3-D view of the row-major matrix ([K/64][rows][64], see
+// make_tensor_map_bf16), in two slots (the shared memory of four one-block
+// slots, so the CTA still fits beside the concurrent windows stage).
 // Every wait is bounded: on timeout the CTA records an error and leaves.
 #include <cudaTypedefs.h>
 
@@ -30,6 +38,20 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm,
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
         :: "r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar), "r"(x), "r"(y) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar), "r"(x), "r"(y), "r"(z) : "memory");
+}
+
+// k-blocks [KPS it, KPS (it + 1)) of the box rows starting at r0: a 2-D map
+// (x = k offset) for KPS = 1, the 3-D view (z = k-block) otherwise.
+template <int KPS>
+__device__ __forceinline__ void tma_load_kb(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int it, int r0) {
+    if constexpr (KPS == 1) tma_load_2d(dst, tm, bar, it * BK, r0);
+    else tma_load_3d(dst, tm, bar, 0, r0, it * KPS);
 }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
@@ -108,25 +130,28 @@ __device__ __forceinline__ float tanh_fast(float x) {
     return y;
 }
 
-template <int BN>
+template <int BN, int KPS>
 struct Cfg {
-    // narrow (hidden-layer) tiles keep 4 stages (80 KB) so that a GEMM CTA
-    // fits on an SM beside two Limber CTAs of the other chain group
-    static constexpr int STAGES = (BN >= 256) ? 4 : (BN >= 128 ? 6 : 4);
-    static constexpr int A_BYTES = BM * BK * 2;
-    static constexpr int B_BYTES = BN * BK * 2;
+    // one-block slots: 4 (6 for 128-wide tiles); two-block slots: the same
+    // shared memory (2 slots, 3 for 128-wide tiles)
+    static constexpr int STAGES = KPS == 1 ? ((BN >= 256) ? 4 : (BN >= 128 ? 6 : 4)) : (BN == 128 ? 3 : 2);
+    static constexpr int A_SUB = BM * BK * 2;          // one k-block of A
+    static constexpr int B_SUB = BN * BK * 2;          // one k-block of B
+    static constexpr int A_BYTES = KPS * A_SUB;
+    static constexpr int B_BYTES = KPS * B_SUB;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
     static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+    static_assert(STAGE_BYTES % 1024 == 0 && B_SUB % 1024 == 0, "slots and k-blocks keep the 1024-byte swizzle atom");
 };
 
-template <int BN, int EPI>
+template <int BN, int EPI, int KPS>
 __global__ void __launch_bounds__(128, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           const float* __restrict__ bias, const float* __restrict__ out_mu, float out_sigma,
           void* __restrict__ Cout, const int* __restrict__ nrows, int N, int K, const float* __restrict__ act_beta,
           int* __restrict__ err) {
-    using C = Cfg<BN>;
+    using C = Cfg<BN, KPS>;
     pdl_begin();
     const int M = *nrows;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -159,30 +184,33 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int nk = (K + BK - 1) / BK;
+    // slots of KPS k-blocks; KPS > 1 only when K is a multiple of 64 KPS
+    const int n_it = (K + BK * KPS - 1) / (BK * KPS);
 
     if (warp == 0 && lane == 0) {
-        // TMA producer
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % C::STAGES;
-            if (kb >= C::STAGES && !mbar_wait(empty_bar(s), ((kb / C::STAGES) & 1) ^ 1)) { s_fail = 1; break; }
-            const uint32_t sa = base + s * C::STAGE_BYTES;
+        // TMA producer: the A and B boxes of a slot
+        for (int it = 0; it < n_it; ++it) {
+            const int s = it % C::STAGES;
+            if (it >= C::STAGES && !mbar_wait(empty_bar(s), ((it / C::STAGES) & 1) ^ 1)) { s_fail = 1; break; }
             mbar_expect_tx(full_bar(s), C::STAGE_BYTES);
-            tma_load_2d(sa, &tmA, full_bar(s), kb * BK, m0);
-            tma_load_2d(sa + C::A_BYTES, &tmB, full_bar(s), kb * BK, n0);
+            tma_load_kb<KPS>(base + s * C::STAGE_BYTES, &tmA, full_bar(s), it, m0);
+            tma_load_kb<KPS>(base + s * C::STAGE_BYTES + C::A_BYTES, &tmB, full_bar(s), it, n0);
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         constexpr uint32_t idesc = instr_desc<BN>();
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % C::STAGES;
-            if (!mbar_wait(full_bar(s), (kb / C::STAGES) & 1)) { s_fail = 1; break; }
+        for (int it = 0; it < n_it; ++it) {
+            const int s = it % C::STAGES;
+            if (!mbar_wait(full_bar(s), (it / C::STAGES) & 1)) { s_fail = 1; break; }
             fence_after();
             const uint32_t sa = base + s * C::STAGE_BYTES;
-            const uint64_t da = smem_desc(sa), db = smem_desc(sa + C::A_BYTES);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-                mma_bf16(tmem, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0);
+            for (int j = 0; j < KPS; ++j) {
+                const uint64_t da = smem_desc(sa + j * C::A_SUB), db = smem_desc(sa + C::A_BYTES + j * C::B_SUB);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    mma_bf16(tmem, da + 2 * kk, db + 2 * kk, idesc, (it | j | kk) != 0);
+            }
             mma_commit(empty_bar(s));
         }
         mma_commit(accf);
@@ -574,23 +602,33 @@ static int launch_split_bn(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo, c
     return NS_OK;
 }
 
+template <int BN, int KPS>
+static int launch_bn_kps(const CUtensorMap* tmA, const CUtensorMap* tmB, const float* bias, const float* mu,
+                         float sigma, void* Cout, const int* nrows, int grid_rows, int N, int K, int epi,
+                         const float* beta, int* err, cudaStream_t st) {
+    using C = Cfg<BN, KPS>;
+    static bool attr = false;
+    if (!attr) {
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<BN, 0, KPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<BN, 1, KPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<BN, 2, KPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+        attr = true;
+    }
+    dim3 grid((N + BN - 1) / BN, (grid_rows + BM - 1) / BM);
+    auto kern = (epi == TC_EPI_TANH) ? k_gemm_tc<BN, 0, KPS>
+              : (epi == TC_EPI_OUT) ? k_gemm_tc<BN, 1, KPS> : k_gemm_tc<BN, 2, KPS>;
+    NS_CUDA_TRY(launch_pdl(kern, grid, dim3(128), (size_t)C::SMEM, st, *tmA, *tmB, bias, mu, sigma, Cout, nrows, N,
+                           K, beta, err));
+    return NS_OK;
+}
+
 template <int BN>
 static int launch_bn(const CUtensorMap* tmA, const CUtensorMap* tmB, const float* bias, const float* mu,
                      float sigma, void* Cout, const int* nrows, int grid_rows, int N, int K, int epi,
                      const float* beta, int* err, cudaStream_t st) {
-    using C = Cfg<BN>;
-    static bool attr = false;
-    if (!attr) {
-        NS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<BN, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-        NS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<BN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-        NS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<BN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-        attr = true;
-    }
-    dim3 grid((N + BN - 1) / BN, (grid_rows + BM - 1) / BM);
-    auto kern = (epi == TC_EPI_TANH) ? k_gemm_tc<BN, 0> : (epi == TC_EPI_OUT) ? k_gemm_tc<BN, 1> : k_gemm_tc<BN, 2>;
-    NS_CUDA_TRY(launch_pdl(kern, grid, dim3(128), (size_t)C::SMEM, st, *tmA, *tmB, bias, mu, sigma, Cout, nrows, N,
-                           K, beta, err));
-    return NS_OK;
+    if (gemm_tc_kps(K) == 2)
+        return launch_bn_kps<BN, 2>(tmA, tmB, bias, mu, sigma, Cout, nrows, grid_rows, N, K, epi, beta, err, st);
+    return launch_bn_kps<BN, 1>(tmA, tmB, bias, mu, sigma, Cout, nrows, grid_rows, N, K, epi, beta, err, st);
 }
 
 }  // namespace tc
@@ -662,18 +700,36 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-// 2-D bf16 tensor map over rows x K (row-major), box = box_rows x 64, 128-byte swizzle.
-int make_tensor_map_bf16(CUtensorMap* tm, const void* base, int rows, int K, int box_rows) {
+int gemm_tc_kps(int K) { return (K % (2 * tc::BK) == 0) ? 2 : 1; }
+
+// bf16 tensor map over a row-major rows x K matrix, 128-byte swizzle.
+// kps = 1: 2-D map, box = box_rows x 64.  kps > 1 (K a multiple of 64 kps):
+// the 3-D view [K/64][rows][64] (strides: a row K * 2 bytes, a k-block 128
+// bytes), box = kps k-blocks of box_rows x 64, landing in shared memory as kps
+// consecutive box_rows x 64 tiles.
+int make_tensor_map_bf16(CUtensorMap* tm, const void* base, int rows, int K, int box_rows, int kps) {
     auto enc = get_encode();
     if (!enc) return NS_ECUDA;
     if ((reinterpret_cast<uintptr_t>(base) & 15) || (K * 2) % 16) return NS_EINVAL;
-    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-    cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r;
+    if (kps == 1) {
+        cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+        cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+        cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+        cuuint32_t estr[2] = {1, 1};
+        r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        if (kps < 1 || K % (tc::BK * kps)) return NS_EINVAL;
+        cuuint64_t dims[3] = {(cuuint64_t)tc::BK, (cuuint64_t)rows, (cuuint64_t)(K / tc::BK)};
+        cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)tc::BK * 2};
+        cuuint32_t box[3] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows, (cuuint32_t)kps};
+        cuuint32_t estr[3] = {1, 1, 1};
+        r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
     return r == CUDA_SUCCESS ? NS_OK : NS_EINVAL;
 }
 

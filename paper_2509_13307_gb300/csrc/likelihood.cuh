@@ -192,7 +192,12 @@ int launch_gemm_tc(const CUtensorMap* tmA, const CUtensorMap* tmB, int tile_n,
                    const float* bias, const float* out_mu, float out_sigma,
                    void* C, const int* d_nrows, int grid_rows, int N, int K, int epi,
                    const float* act_beta, int* d_err, cudaStream_t st);
-int make_tensor_map_bf16(CUtensorMap* tm, const void* base, int rows, int K, int box_rows);
+// k-blocks of 64 per ring slot of launch_gemm_tc for a reduction length K; its
+// tmA and tmB must be made with kps = gemm_tc_kps(K).
+int gemm_tc_kps(int K);
+// bf16 tensor map over a row-major rows x K matrix: kps = 1 a 2-D map with
+// box_rows x 64 boxes; kps > 1 a 3-D view whose box is kps such tiles.
+int make_tensor_map_bf16(CUtensorMap* tm, const void* base, int rows, int K, int box_rows, int kps = 1);
 // Split-BF16 tcgen05 GEMM (adjoint): C = epi((A_hi + A_lo) W^T + ...) with A
 // given as a bf16 (hi, lo) pair whose sum is the FP32 operand; tmAhi / tmAlo box
 // 128 rows, tmB boxes tile_n (64, 128, 256) rows of W (N x K).  Epilogues:

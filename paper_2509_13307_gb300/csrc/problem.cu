@@ -128,7 +128,8 @@ int workspace_create(const ns_problem* p, int cap, Workspace* ws) {
             ws->tmA.resize(p->n_layers);
             int cur = 0;
             for (int l = 1; l + 1 < p->n_layers; ++l) {
-                NS_TRY(make_tensor_map_bf16(&ws->tmA[l], ws->act[cur], rows_pad, p->dims[l], 128));
+                NS_TRY(make_tensor_map_bf16(&ws->tmA[l], ws->act[cur], rows_pad, p->dims[l], 128,
+                                            gemm_tc_kps(p->dims[l])));
                 cur ^= 1;
             }
         }
@@ -160,7 +161,8 @@ int workspace_create(const ns_problem* p, int cap, Workspace* ws) {
         ws->tmA.resize(p->n_layers);
         int cur = 0;
         for (int l = 1; l < p->n_layers; ++l) {
-            NS_TRY(make_tensor_map_bf16(&ws->tmA[l], ws->act[cur], rows_pad, p->dims[l], 128));
+            NS_TRY(make_tensor_map_bf16(&ws->tmA[l], ws->act[cur], rows_pad, p->dims[l], 128,
+                                        gemm_tc_kps(p->dims[l])));
             if (l == p->n_layers - 1)
                 NS_TRY(make_tensor_map_bf16(&ws->tmX_out, ws->act[cur], rows_pad, p->dims[l], kSwapRows));
             cur ^= 1;
@@ -357,13 +359,13 @@ static int autotune_hidden_tiles(ns_problem* p, int last_hidden) {
     for (int l = 1; l <= last_hidden; ++l) {
         const int K = p->dims[l], N = p->dims[l + 1];
         CUtensorMap tmA, tmB;
-        int s = make_tensor_map_bf16(&tmA, a, rows_pad, K, 128);
+        int s = make_tensor_map_bf16(&tmA, a, rows_pad, K, 128, gemm_tc_kps(K));
         if (s) return done(s);
         int best = p->tile_n[l];
         float best_ms = 1e30f;
         for (int tn : {16, 32, 64, 128}) {
             if (tn > N) continue;
-            if ((s = make_tensor_map_bf16(&tmB, p->d_W[l], N, K, tn))) return done(s);
+            if ((s = make_tensor_map_bf16(&tmB, p->d_W[l], N, K, tn, gemm_tc_kps(K)))) return done(s);
             auto run = [&]() {
                 return launch_gemm_tc(&tmA, &tmB, tn, (const float*)p->d_b[l], nullptr, 0.f, o, dn, rows, N, K,
                                       TC_EPI_TANH, nullptr, nullptr, st);
@@ -380,7 +382,7 @@ static int autotune_hidden_tiles(ns_problem* p, int last_hidden) {
         }
         p->tile_n[l] = best;
         p->tile_ms[l] = best_ms / 5.f;
-        if ((s = make_tensor_map_bf16(&p->tmB[l], p->d_W[l], N, K, best))) return done(s);
+        if ((s = make_tensor_map_bf16(&p->tmB[l], p->d_W[l], N, K, best, gemm_tc_kps(K)))) return done(s);
     }
     return done(NS_OK);
 }
@@ -613,7 +615,9 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
             int tn = last ? 128 : 32;
             if (N < tn) tn = (N >= 64) ? 64 : 32;
             p->tile_n[l] = tn;
-            int s = make_tensor_map_bf16(&p->tmB[l], p->d_W[l], N, p->dims[l], tn);
+            // the swapped output layer (tile 128) reads W through 2-D boxes
+            const int kps = (last && tn == 128) ? 1 : gemm_tc_kps(p->dims[l]);
+            int s = make_tensor_map_bf16(&p->tmB[l], p->d_W[l], N, p->dims[l], tn, kps);
             if (s) return fail(s);
         }
         int s = autotune_hidden_tiles(p, e.n_layers - 2);   // hidden layers 1 .. L-2
