@@ -118,7 +118,7 @@ __device__ inline float cvt_in(__nv_bfloat16 v) { return __bfloat162float(v); }
 // and keeps a unit's bias and K0 (<= KMAX) weights in registers over the CTA's
 // rows, so the weights are read once per CTA and the launch has
 // ceil(rows / kInRows) CTAs rather than one per (row, 256 units).
-constexpr int kInRows = 4;
+constexpr int kInRows = 2;
 template <typename T, typename TO, int KMAX>
 __global__ void __launch_bounds__(256)
 k_emu_input(const double* __restrict__ theta_full, int P, const int* __restrict__ inputs,
