@@ -132,12 +132,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def limber_method_flops_per_eval(cfg) -> float:
+    """The method's FLOPs of the Limber stage per evaluation (the roofline
+    numerator): per (ell, chi node) the 16-tap bicubic lookup of Eq. 4 (16
+    FMA) and one FMA per bin pair of the Limber sum (Eq. 3-4), 2 FLOP per FMA:
+    2 n_ell N_chi (16 + n_pairs) = 1.271 MFLOP on the 39-d problem."""
+    return 2.0 * cfg.n_ell * cfg.n_chi * (16 + cfg.n_pairs)
+
+
 def limber_flops_per_eval(cfg) -> float:
-    """Algorithmic FLOPs of the Limber stage (k_limber) per evaluation, the
-    count stated in the design notes: per (ell, chi-node) a 16-tap bicubic
-    lookup (32) + bracket and Catmull-Rom weights (10) + nb window products +
-    2 n_pairs pair-sum FLOPs (one FMA each); per data element the bias
-    product and the template sum (3 + 2 n_tmpl)."""
+    """Every FLOP the Limber kernel (k_limber) executes per evaluation, a
+    larger count than the method's (reported beside it): per (ell, chi-node)
+    a 16-tap bicubic lookup (32) + bracket and Catmull-Rom weights (10) + nb
+    window products + 2 n_pairs pair-sum FLOPs (one FMA each); per data
+    element the bias product and the template sum (3 + 2 n_tmpl)."""
     N = cfg.n_chi
     nb = cfg.n_bins
     npairs = nb * (nb + 1) // 2
@@ -218,12 +226,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16")
-    ap.add_argument("--no-full-run", action="store_true", help="skip the time-to-converged-logZ run")
+    ap.add_argument("--no-full-run", action="store_true", help="skip the time-to-converged-logZ runs")
+    ap.add_argument("--no-fp32-run", action="store_true",
+                    help="skip the plain FP32 form's time-to-converged-logZ run (about two minutes)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-multi", action="store_true", help="skip the packed-runs measurement")
     ap.add_argument("--no-cmb", action="store_true", help="skip the CMB (D = 7521) measurement")
     ap.add_argument("--no-nuts", action="store_true", help="skip the NUTS measurement")
-    ap.add_argument("--nuts-warmup", type=int, default=10)
+    ap.add_argument("--nuts-warmup", type=int, default=10, help="NUTS warm-up iterations (bench line; "
+                    "--study nuts: use e.g. 500)")
     ap.add_argument("--nuts-samples", type=int, default=10)
     ap.add_argument("--profile", choices=["loglike", "round", "cmb", "grad"], default=None,
                     help="run a short fixed workload for a profiler and exit (no timing line): "
@@ -232,9 +243,29 @@ def main():
                          "'cmb' = 4 loglike_batch calls on the D = 7521 CMB problem, "
                          "'grad' = 4 loglike_grad_batch calls of --batch rows on the 39-d shear problem")
     ap.add_argument("--batch", type=int, default=500)
+    ap.add_argument("--hidden-tile", type=int, default=0,
+                    help="--profile: force the N-tile width (16/32/64/128) of the BF16 hidden layers (0: autotuned)")
+    ap.add_argument("--study", choices=["evidence", "oracle", "nuts"], default=None,
+                    help="one-off measurements printed as one JSON line (no timing line): 'evidence' = log Z and "
+                         "log B01 of the 39-d w0-wa vs 37-d LCDM runs over --seeds in each of --precisions, the "
+                         "interpolated-P(k) runs on the same data and the full - interpolated log L offset over "
+                         "the posterior; 'oracle' = the CPU oracle's evaluation rates (1 and all host threads) and "
+                         "full nested-sampling runs, with the 6-d CMB and 39-d shear times extrapolated from "
+                         "rates x the GPU runs' evaluation counts; 'nuts' = the HMC comparison: NUTS on the "
+                         "hand-written adjoint (64 chains, --nuts-warmup + --nuts-samples iterations) against the "
+                         "nested-sampling posterior of the same problem")
+    ap.add_argument("--seeds", default="3,4,5")
+    ap.add_argument("--precisions", default="bf16,fp32")
+    ap.add_argument("--oracle-limit", type=float, default=900.0, help="seconds allowed per full oracle run")
     args = ap.parse_args()
     if args.profile:
         return profile_workload(args)
+    if args.study == "evidence":
+        return evidence_study(args)
+    if args.study == "oracle":
+        return oracle_study(args)
+    if args.study == "nuts":
+        return nuts_study(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours(args)
@@ -254,7 +285,8 @@ def profile_workload(args):
         prob = Problem(inp, args.precision if args.precision != "bf16" else "fp32", max_batch=args.batch)
     else:
         inp = w.make_shear_inputs(w.shear39())
-        prob = Problem(inp, args.precision, max_batch=max(args.batch, 1000))   # grad: max_batch sizes its workspace
+        prob = Problem(inp, args.precision, max_batch=max(args.batch, 1000),   # grad: max_batch sizes its workspace
+                       hidden_tile=args.hidden_tile)
     if args.profile == "round":
         sc = w.shear39().sampler
         run = NestedRun.from_config(prob, sc)
@@ -275,6 +307,310 @@ def profile_workload(args):
                 prob.loglike(th)
         torch.cuda.synchronize()
     print(f"profile workload {args.profile} done", flush=True)
+    return 0
+
+
+def evidence_study(args):
+    """The benchmark spec's evidence check on the 39-d shear problem: nested
+    sampling to a converged log Z of the w0-wa (39-d) and LCDM (37-d, w0 = -1,
+    wa = 0 fixed) models on the same mock data, per seed and precision; log
+    B01 = ln Z_LCDM - ln Z_w0wa (Eq. 2) with error sqrt(s0^2 + s1^2); the same
+    with the emulator on 10 coarse z nodes interpolated to the 50-node table
+    (Catmull-Rom, and linear as in the paper's interpolated likelihood, App. B)
+    on the full problem's data; and the full - interpolated log L offset over
+    posterior samples of the full BF16 runs (FP64 likelihoods)."""
+    from dataclasses import replace
+    import numpy as np
+    import torch
+    from paper_2509_13307_gb300.build import build
+    build()
+    import workloads as w
+    from paper_2509_13307_gb300 import Problem, NestedRun
+    seeds = [int(x) for x in args.seeds.split(",") if x]
+    precs = [x for x in args.precisions.split(",") if x]
+    models = {"w0wa": w.shear39(), "lcdm": w.shear37_lcdm()}
+    interp = {"catmull_rom": {"w0wa": w.shear39_interp(), "lcdm": w.shear37_interp()},
+              "linear": {"w0wa": w.shear39_interp_linear(),
+                         "lcdm": replace(w.shear37_interp(), name="shear37_interp_linear", z_interp="linear")}}
+    inps = {m: w.make_shear_inputs(c) for m, c in models.items()}
+    base = Problem(inps["w0wa"], "fp64", max_batch=8)
+    data, cov = base.data, base.cov
+    base.close()
+    out = {"workload": WORKLOAD, "seeds": seeds, "runs": [], "bayes": {}}
+    posts = {}
+
+    def one(cfg, inp, prec, seed, tag):
+        sc = cfg.sampler
+        p = Problem(inp, prec, max_batch=sc.n_live, data=data, cov=cov)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        r = NestedRun(p, sc.n_live, sc.n_delete, sc.repeats, sc.tol, seed, sc.width, sc.step_cap, sc.ridge)
+        st = r.run(max_iters=5000)
+        ev = r.evidence()
+        dt = time.time() - t0
+        rec = dict(tag=tag, precision=prec, seed=seed, d=p.d, seconds=dt, iterations=st.iterations,
+                   evaluations=st.evaluations, converged=st.converged, status_bits=st.status_bits,
+                   nonfinite=st.nonfinite, logZ=ev["logZ"], logZ_err=ev["logZ_err"], H=ev["H"])
+        if prec == "bf16" and tag.startswith("full") and seed == seeds[0]:
+            posts[tag] = (r.posterior(), inp)
+        r.close()
+        p.close()
+        out["runs"].append(rec)
+        print(json.dumps(rec), file=sys.stderr, flush=True)
+        return rec
+
+    def bayes(recs0, recs1):
+        lb = [a["logZ"] - b["logZ"] for a, b in zip(recs0, recs1)]
+        eb = [math.hypot(a["logZ_err"], b["logZ_err"]) for a, b in zip(recs0, recs1)]
+        return dict(logB01_per_seed=lb, err_per_seed=eb, logB01_mean=float(np.mean(lb)),
+                    logB01_seed_sd=float(np.std(lb, ddof=1)) if len(lb) > 1 else None,
+                    logZ_lcdm=[a["logZ"] for a in recs0], logZ_w0wa=[b["logZ"] for b in recs1])
+
+    for prec in precs:
+        rl = [one(models["lcdm"], inps["lcdm"], prec, sd, "full_lcdm") for sd in seeds]
+        rw = [one(models["w0wa"], inps["w0wa"], prec, sd, "full_w0wa") for sd in seeds]
+        out["bayes"][f"full_{prec}"] = bayes(rl, rw)
+    for kind, cf in interp.items():
+        ii = {m: w.make_shear_inputs(c) for m, c in cf.items()}
+        rl = [one(cf["lcdm"], ii["lcdm"], "bf16", sd, f"interp_{kind}_lcdm") for sd in seeds]
+        rw = [one(cf["w0wa"], ii["w0wa"], "bf16", sd, f"interp_{kind}_w0wa") for sd in seeds]
+        out["bayes"][f"interp_{kind}_bf16"] = bayes(rl, rw)
+        # full - interpolated log L (FP64) over posterior samples of the full runs
+        for m in ("w0wa", "lcdm"):
+            key = f"full_{m}"
+            if key not in posts:
+                continue
+            (x, lg, logw), inp_full = posts[key]
+            rng = np.random.default_rng(11)
+            idx = rng.choice(len(logw), size=512, p=np.exp(logw))
+            cube = torch.tensor(x[idx], dtype=torch.float64, device="cuda")
+            pf = Problem(inp_full, "fp64", max_batch=512, data=data, cov=cov)
+            pi = Problem(ii[m], "fp64", max_batch=512, data=data, cov=cov)
+            th = pf.prior_transform(cube)
+            dl = (pf.loglike(th) - pi.loglike(th)).cpu().numpy()
+            out.setdefault("offset", {})[f"{kind}_{m}"] = dict(
+                mean=float(np.mean(dl)), sd=float(np.std(dl, ddof=1)), min=float(np.min(dl)), max=float(np.max(dl)),
+                samples=512, how="FP64 log L_full - log L_interp at 512 posterior draws of the full BF16 run")
+            pf.close()
+            pi.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def posterior_moments(theta, logw):
+    """Weighted mean and standard deviation of nested-sampling posterior
+    samples, and the Kish effective sample size of the weights."""
+    import numpy as np
+    w = np.exp(logw - np.max(logw))
+    w /= w.sum()
+    mean = w @ theta
+    sd = np.sqrt(np.maximum(w @ (theta - mean) ** 2, 0.0))
+    return mean, sd, 1.0 / np.sum(w * w)
+
+
+def nuts_study(args):
+    """The HMC comparison of the paper (Sec. 3.2, Table 2's NUTS rows) on the
+    39-d shear problem: NUTS (64 chains in lockstep on the hand-written
+    adjoint, dual averaging to a 0.8 acceptance target, diagonal mass matrix
+    from warm-up) started from nested-sampling posterior draws, and its
+    posterior means and standard deviations against the weighted dead points
+    of a converged nested-sampling run of the same problem and precision."""
+    import numpy as np
+    import torch
+    from paper_2509_13307_gb300.build import build
+    build()
+    import workloads as w
+    from paper_2509_13307_gb300 import Problem, NestedRun, nuts
+    cfg = w.shear39()
+    inp = w.make_shear_inputs(cfg)
+    sc = cfg.sampler
+    prob = Problem(inp, args.precision, max_batch=sc.n_live)
+    t0 = time.time()
+    run = NestedRun.from_config(prob, sc)
+    st = run.run(max_iters=5000)
+    ev = run.evidence()
+    t_ns = time.time() - t0
+    x, lg, logw = run.posterior()
+    run.close()
+    B = prob.max_batch
+    theta = np.concatenate([prob.prior_transform(torch.tensor(x[i:i + B], device="cuda")).cpu().numpy()
+                            for i in range(0, len(x), B)])
+    m_ns, s_ns, ess_ns = posterior_moments(theta, logw)
+    n_ch = 64
+    rng = np.random.default_rng(12)
+    pick = rng.choice(len(logw), size=n_ch, p=np.exp(logw))
+    xc = np.clip(x[pick], 1e-9, 1 - 1e-9)
+    z0 = np.log(xc) - np.log1p(-xc)
+    pn = Problem(inp, args.precision, max_batch=n_ch, data=prob.data, cov=prob.cov)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    out = nuts(pn, n_ch, args.nuts_warmup, args.nuts_samples, z0=z0, seed=5, init_step=0.02, max_depth=10)
+    t_nuts = time.time() - t0
+    th = out["theta"]                                   # chains x samples x d
+    m_hmc = th.reshape(-1, th.shape[-1]).mean(axis=0)
+    s_hmc = th.reshape(-1, th.shape[-1]).std(axis=0)
+    se_hmc = th.mean(axis=1).std(axis=0, ddof=1) / np.sqrt(n_ch)   # spread of chain means
+    se_ns = s_ns / np.sqrt(ess_ns)
+    zsc = (m_hmc - m_ns) / np.sqrt(se_hmc ** 2 + se_ns ** 2)
+    names = [inp["param_names"][i] for i, p in enumerate(inp["priors"]) if p[0] != "F"]
+    stn = out["stats"]
+    res = {"workload": WORKLOAD, "precision": args.precision,
+           "ns": {"seconds": t_ns, "evaluations": st.evaluations, "logZ": ev["logZ"], "logZ_err": ev["logZ_err"],
+                  "ess": ess_ns, "status_bits": st.status_bits},
+           "nuts": {"chains": n_ch, "warmup": args.nuts_warmup, "samples": args.nuts_samples, "seconds": t_nuts,
+                    "gradient_evals": stn["gradient_evals"], "grad_evals_per_s": stn["gradient_evals"] / t_nuts,
+                    "batched_calls": stn["batched_calls"], "mean_depth": stn["mean_depth"],
+                    "mean_accept": stn["mean_accept"], "divergences": stn["divergences"],
+                    "init": "64 draws from the nested-sampling posterior"},
+           "compare": {"param": names, "mean_ns": m_ns.tolist(), "sd_ns": s_ns.tolist(), "mean_nuts": m_hmc.tolist(),
+                       "sd_nuts": s_hmc.tolist(), "z_mean": zsc.tolist(), "max_abs_z": float(np.max(np.abs(zsc))),
+                       "sd_ratio_min": float(np.min(s_hmc / s_ns)), "sd_ratio_max": float(np.max(s_hmc / s_ns)),
+                       "how": "z = (mean_nuts - mean_ns) / sqrt(se_nuts^2 + se_ns^2); se_nuts from the spread of "
+                              "the 64 chain means, se_ns = sd / sqrt(Kish ESS of the NS weights)"}}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
+def _host_info():
+    info = {"nproc": os.cpu_count(), "machine": os.uname().machine}
+    try:
+        with open("/proc/cpuinfo") as fh:
+            txt = fh.read()
+        for key in ("model name", "CPU part", "Hardware"):
+            for line in txt.splitlines():
+                if line.startswith(key):
+                    info[key.replace(" ", "_")] = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20)
+        for line in r.stdout.splitlines():
+            if line.startswith("Model name"):
+                info["model_name"] = line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return info
+
+
+def _oracle_subprocess(code: str, threads: int, timeout: float):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = str(threads)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
+    if r.returncode != 0:
+        return {"error": r.stderr[-400:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+_ORACLE_RATE = r"""
+import sys, time, json
+sys.path.insert(0, %(root)r)
+import numpy as np
+import workloads as w
+kind = %(kind)r
+if kind == "cmb6":
+    from oracle.cmb import CMBOracle
+    o = CMBOracle(w.make_cmb_inputs(w.cmb6()))
+    d = 6
+else:
+    from oracle.shear import ShearOracle
+    cfg = getattr(w, kind)()
+    o = ShearOracle(w.make_shear_inputs(cfg))
+    d = cfg.d_free
+rng = np.random.default_rng(0)
+o.loglike_cube(rng.uniform(0.02, 0.98, d))
+n = 0; t0 = time.time()
+while time.time() - t0 < %(seconds)f or n < 2:
+    o.loglike_cube(rng.uniform(0.02, 0.98, d)); n += 1
+print(json.dumps({"n": n, "s": time.time() - t0}))
+"""
+
+_ORACLE_RUN = r"""
+import sys, time, json
+sys.path.insert(0, %(root)r)
+import numpy as np
+import workloads as w
+from oracle.ns import NestedSampler
+kind = %(kind)r
+if kind == "gauss5":
+    from oracle.gauss import GaussOracle
+    cfg = w.gauss_test(5)
+    f = GaussOracle(w.make_gauss_inputs(cfg)).loglike
+    d = 5
+else:
+    from oracle.shear import ShearOracle
+    cfg = getattr(w, kind)()
+    f = ShearOracle(w.make_shear_inputs(cfg)).loglike_cube
+    d = cfg.d_free
+ns = NestedSampler.from_config(f, d, cfg.sampler)
+t0 = time.time()
+ns.initialise()
+while not ns.converged() and time.time() - t0 < %(limit)f:
+    ns.iterate()
+dt = time.time() - t0
+ev = ns.evidence(n_replays=200) if ns.converged() else {}
+print(json.dumps({"seconds": dt, "converged": ns.converged(), "iterations": ns.it, "evaluations": ns.n_evals,
+                  "logZ": ev.get("logZ"), "logZ_err": ev.get("logZ_err")}))
+"""
+
+
+def oracle_study(args):
+    """The oracle as a baseline (FP64 NumPy on the host cores of the GPU machine):
+    evaluation rates at 1 and all threads for the 5-d toy, the 6-d CMB problem
+    and the 39-d shear problem; full nested-sampling runs of the 5-d Gaussian
+    test problem and the 5-d shear toy (bounded by --oracle-limit seconds);
+    for the 6-d CMB and 39-d shear problems, whose oracle runs would take
+    hours to days, the time to a converged log Z is extrapolated as the GPU
+    run's evaluation count / the oracle's rate, and labelled as such."""
+    nproc = os.cpu_count() or 1
+    out = {"host": _host_info(), "rates": {}, "runs": {}, "extrapolated": {}}
+    secs = {"shear5": 15.0, "cmb6": 20.0, "shear39": 15.0}
+    for kind, sec in secs.items():
+        for th in sorted({1, nproc}):
+            r = _oracle_subprocess(_ORACLE_RATE % dict(root=ROOT, kind=kind, seconds=sec), th, 1800)
+            if "n" in r:
+                r = {"evals_per_s": r["n"] / r["s"], "evals": r["n"], "seconds": r["s"]}
+            out["rates"][f"{kind}_threads{th}"] = r
+            print(json.dumps({kind: r, "threads": th}), file=sys.stderr, flush=True)
+    for kind in ("gauss5", "shear5"):
+        r = _oracle_subprocess(_ORACLE_RUN % dict(root=ROOT, kind=kind, limit=args.oracle_limit), 1,
+                               args.oracle_limit + 600)
+        r["threads"] = 1
+        out["runs"][kind] = r
+        print(json.dumps({kind: r}), file=sys.stderr, flush=True)
+    # GPU runs for the evaluation counts of the extrapolations (and the GPU's own times)
+    import torch
+    from paper_2509_13307_gb300.build import build
+    build()
+    import workloads as w
+    from paper_2509_13307_gb300 import Problem, NestedRun
+    gpu = {}
+    for kind, cfg, inp_fn, prec in (("gauss5", w.gauss_test(5), w.make_gauss_inputs, "fp64"),
+                                    ("shear5", w.shear5(), w.make_shear_inputs, "fp64"),
+                                    ("cmb6", w.cmb6(), w.make_cmb_inputs, "fp32"),
+                                    ("shear39", w.shear39(), w.make_shear_inputs, "bf16")):
+        sc = cfg.sampler
+        p = Problem(inp_fn(cfg), prec, max_batch=max(sc.n_live, 2 * sc.n_delete))
+        torch.cuda.synchronize()
+        t0 = time.time()
+        r = NestedRun.from_config(p, sc)
+        st = r.run(max_iters=100000)
+        ev = r.evidence()
+        gpu[kind] = dict(seconds=time.time() - t0, evaluations=st.evaluations, iterations=st.iterations,
+                         precision=prec, logZ=ev["logZ"], logZ_err=ev["logZ_err"])
+        r.close()
+        p.close()
+    out["gpu_runs"] = gpu
+    for kind in ("shear5", "cmb6", "shear39"):
+        for th in sorted({1, nproc}):
+            rate = out["rates"].get(f"{kind}_threads{th}", {}).get("evals_per_s")
+            if rate:
+                out["extrapolated"][f"{kind}_threads{th}"] = dict(
+                    seconds=gpu[kind]["evaluations"] / rate, label="extrapolated: GPU run's evaluation count / "
+                    "oracle evaluations per second (not a measured oracle run)")
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -364,7 +700,8 @@ def ours(args):
         st1 = run.step(0)
         prof = run.profile_read() if profile else None
         out = dict(ms=ms, evals=st1.evaluations - st0.evaluations, rounds=st1.rounds - st0.rounds,
-                   iters=st1.iterations - st0.iterations, prof=prof, status=st1.status_bits)
+                   iters=st1.iterations - st0.iterations, prof=prof, status=st1.status_bits,
+                   nonfinite=st1.nonfinite)
         run.close()
         return out
 
@@ -390,7 +727,7 @@ def ours(args):
 
     # ---------------- roofline of the dominant kernel (Limber stage), timed live
     prof = res["prof"]
-    flops = limber_flops_per_eval(cfg)
+    flops = limber_method_flops_per_eval(cfg)
     peak = fp32_alu_peak_tflops(2070.0)
     roofline = None
     if prof and prof["launches"] > 0 and prof["ms"] > 0:
@@ -400,7 +737,11 @@ def ours(args):
                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
                                     "scaled from 384 evaluations)",
                     "kernel": "k_limber<float,5,fast> (A10-A12: P lookup, Limber sums, data vector)",
-                    "flop_per_eval": flops, "avg_launch_ms": prof["ms"] / prof["launches"],
+                    "flop_per_eval": flops,
+                    "flop_basis": "A10 + A11L method count 2 n_ell N_chi (16 + n_pairs); the kernel's full "
+                                  "instruction-level count incl. weights and indexing is kernel_flop_per_eval",
+                    "kernel_flop_per_eval": limber_flops_per_eval(cfg),
+                    "avg_launch_ms": prof["ms"] / prof["launches"],
                     "avg_rows_per_launch": prof["rows"] / prof["launches"],
                     "peak_basis": "FP32 ALU 152 SM x 128 lanes x 2 x 2070 MHz (no measured FP32 peak in MEASURED_PEAKS.json)"}
         if roofline["traffic"]:
@@ -501,8 +842,44 @@ def ours(args):
         ev = run.evidence()
         t1 = time.time()
         extra.update(time_to_logZ_s=t1 - t0, logZ=ev["logZ"], logZ_err=ev["logZ_err"], logZ_iters=st.iterations,
-                     logZ_evals=st.evaluations, logZ_converged=st.converged)
+                     logZ_evals=st.evaluations, logZ_converged=st.converged, logZ_status_bits=st.status_bits,
+                     logZ_nonfinite_evals=st.nonfinite)
         run.close()
+        # the nested LCDM model (w0 = -1, wa = 0 fixed, 37-d) on the same data:
+        # the Bayes factor B01 = Z_LCDM / Z_w0wa (Eq. 2)
+        try:
+            c37 = w.shear37_lcdm()
+            p37 = Problem(w.make_shear_inputs(c37), args.precision, max_batch=sc.n_live, data=prob.data,
+                          cov=prob.cov)
+            torch.cuda.synchronize()
+            t0 = time.time()
+            r37 = NestedRun(p37, sc.n_live, sc.n_delete, sc.repeats, sc.tol, seed, sc.width, sc.step_cap, sc.ridge)
+            s37 = r37.run(max_iters=2000)
+            e37 = r37.evidence()
+            extra["bayes"] = {"logZ_w0wa": ev["logZ"], "logZ_w0wa_err": ev["logZ_err"],
+                              "logZ_lcdm": e37["logZ"], "logZ_lcdm_err": e37["logZ_err"],
+                              "logB01": e37["logZ"] - ev["logZ"],
+                              "logB01_err": math.hypot(e37["logZ_err"], ev["logZ_err"]),
+                              "lcdm_time_to_logZ_s": time.time() - t0, "lcdm_evals": s37.evaluations,
+                              "lcdm_status_bits": s37.status_bits, "precision": args.precision,
+                              "models": "B01 = Z(LCDM, 37-d) / Z(w0-wa, 39-d), same mock data, seed %d" % seed}
+            r37.close()
+            p37.close()
+        except Exception as exc:
+            extra["bayes_error"] = repr(exc)[:200]
+        # the plain FP32 form's wall time to a converged log Z on the same problem
+        if not args.no_fp32_run and args.precision != "fp32":
+            p32 = Problem(inp, "fp32", max_batch=sc.n_live, data=prob.data, cov=prob.cov)
+            torch.cuda.synchronize()
+            t0 = time.time()
+            r32 = NestedRun(p32, sc.n_live, sc.n_delete, sc.repeats, sc.tol, seed, sc.width, sc.step_cap, sc.ridge)
+            s32 = r32.run(max_iters=2000)
+            e32 = r32.evidence()
+            extra.update(fp32_time_to_logZ_s=time.time() - t0, fp32_logZ=e32["logZ"], fp32_logZ_err=e32["logZ_err"],
+                         fp32_logZ_evals=s32.evaluations, fp32_logZ_status_bits=s32.status_bits,
+                         time_to_logZ_speedup_vs_fp32=(time.time() - t0) / extra["time_to_logZ_s"])
+            r32.close()
+            p32.close()
 
     # ---------------- NUTS on the adjoint (the HMC comparison of the 39-d
     # shear problem): 64 chains in lockstep, a short warm-up and sample
@@ -609,7 +986,7 @@ def ours(args):
                 "config": {"workload": WORKLOAD, "precision": args.precision,
                            "l2": "flushed between timed steps (256 MB write)",
                            "evals_per_step": res["evals"] / max(res["iters"], 1),
-                           "status_bits": res["status"]},
+                           "status_bits": res["status"], "nonfinite_evals": res["nonfinite"]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": gpu_launches}
         line.update(extra)

@@ -167,6 +167,9 @@ typedef struct {
     ns_gauss_desc gauss;
     int max_batch;                /* largest batch B any call will pass (>= 1) */
     ns_cmb_desc cmb;
+    int hidden_tile;              /* BF16: N-tile width of every tensor-core hidden layer, one of
+                                     16, 32, 64, 128 (at most the layer's width); 0 = chosen by the
+                                     tile autotuner at creation.  Results do not depend on it. */
 } ns_problem_desc;
 
 typedef struct ns_problem ns_problem;
@@ -189,6 +192,10 @@ typedef struct {
     int chain_groups;             /* 1 or 2 groups of chains whose likelihood rounds run on two
                                      streams and overlap on the GPU (results are identical);
                                      <= 0: 1 */
+    int n_shards;                 /* > 1: one nested-sampling run split over n_shards devices,
+                                     this run object evolving shard `shard` of the k chains
+                                     (ns_shard_*); 0 or 1: an ordinary run */
+    int shard;                    /* shard index in [0, n_shards) */
 } ns_config;
 
 typedef struct {
@@ -200,6 +207,8 @@ typedef struct {
     double logZ;                  /* dead-point evidence so far */
     double logX;                  /* log enclosed prior mass */
     double lstar;                 /* last deletion threshold */
+    long long nonfinite;          /* likelihood evaluations that returned NaN / inf (each treated
+                                     as outside the constraint; sets NS_BIT_NONFINITE) */
 } ns_status;
 
 /* ---- entry points ------------------------------------------------------- */
@@ -217,17 +226,33 @@ const char* ns_strerror(int code);
 int ns_problem_create(const ns_problem_desc* desc, ns_problem** out);
 int ns_problem_free(ns_problem* p);
 
-/* Number of free (non-FIXED) parameters d. */
+/* Number of free (non-FIXED) parameters d: the dimension of the unit cube the
+ * sampler explores (Sec. 2.5: 39 for w0-wa, 37 for LCDM). */
 int ns_problem_dim(const ns_problem* p, int* d);
 
-/* Prior transform (Table 1): cube_dev (B x d) in (0,1) -> theta_dev (B x d)
- * physical free parameters.  B <= max_batch. */
+/* Prior transform of Table 1 (Sec. 2.5 priors; every prior is uniform in the
+ * unit cube, where the sampler works): cube_dev (B x d) in (0,1) -> theta_dev
+ * (B x d) physical free parameters, uniform a + (b - a) c, Gaussian
+ * a + b Phi^-1(c).  Phi^-1 is the sampler's: FP64 for FP64 problems, FP32 on
+ * min(c, 1 - c) for reduced-precision problems (finite on all of (0, 1)).
+ * B <= max_batch, else NS_EINVAL. */
 int ns_prior_transform(const ns_problem* p, const double* cube_dev, int B,
                        double* theta_dev, void* stream);
 
 /* Batched log-likelihood at physical free parameters theta_dev (B x d):
- * logL_dev[b] = log L(theta_b).  B <= max_batch; B = 0 is a no-op.
- * Non-finite results are returned as they are. */
+ * logL_dev[b] = log L(theta_b).
+ *   Shear kind: the Gaussian likelihood of App. A, log L = -1/2 (d - m)^T
+ *     C^-1 (d - m) - 1/2 ln det(2 pi C), with the data vector
+ *     m = (1 + m_i)(1 + m_j) C_ij(ell) + T b, C_ij(ell) the extended Limber
+ *     integral of Eq. 3-4 (k = (ell + 1/2) / chi) over the windows of Eq. 5
+ *     (lensing) and Eq. 6 (intrinsic alignment) on the a-uniform chi grid of
+ *     App. A, with P(k, z) from the emulator of Sec. 2.5 and the photo-z
+ *     shifts n_i(z - D_z,i).
+ *   CMB kind: Sec. 2.4 (cosmic-variance TT form) or a dense Gaussian.
+ *   Gaussian test kind: the closed form below.
+ * theta_dev and logL_dev are caller-owned device memory (row-major FP64).
+ * B <= max_batch (else NS_EINVAL); B = 0 is a no-op.  NS_EINVAL for a
+ * model-only problem.  Non-finite results are returned as they are. */
 int loglike_batch(const ns_problem* p, const double* theta_dev, int B,
                   double* logL_dev, void* stream);
 
@@ -257,9 +282,14 @@ int ns_problem_tiles(const ns_problem* p, int* tile_n, float* ms, int n);
  * same bits at every host synchronisation and stop with NS_ETIMEOUT. */
 int ns_problem_status(ns_problem* p, int* bits, int clear);
 
-/* Log-likelihood and its gradient d log L / d theta (B x d) by a hand-written
- * adjoint of the likelihood stages (shear kind; closed form for the Gaussian
- * test kind).  NS_ENOTSUP where not built (CMB kind). */
+/* Log-likelihood (as loglike_batch) and its gradient d log L / d theta
+ * (grad_dev, B x d, caller-owned device memory) by a hand-written reverse
+ * pass through the stages of App. A (chi^2, data vector, Limber Eq. 3-4,
+ * windows Eq. 5-6, distances and growth, the emulator of Sec. 2.5 and the
+ * Table 1 prior's physical parameters); the paper's pipeline is
+ * auto-differentiable (Sec. 2.2, Sec. 4.2) and its HMC comparison runs use
+ * these gradients (Sec. 3.2).  Shear kind; closed form for the Gaussian test
+ * kind; NS_ENOTSUP for the CMB kind.  B <= max_batch, else NS_EINVAL. */
 int loglike_grad_batch(const ns_problem* p, const double* theta_dev, int B,
                        double* logL_dev, double* grad_dev, void* stream);
 
@@ -304,18 +334,26 @@ typedef struct {
 int ns_nuts_run(const ns_problem* p, const ns_nuts_config* cfg, const double* z0, double* samples,
                 double* logp, double* step_size, ns_nuts_stats* stats, void* stream);
 
-/* Start a run: draws n live points uniformly in the cube (Philox counter
- * (INIT | chunk << 8, 0, point, 0)), evaluates them, zeroes the evidence
- * accumulators.  The run keeps the problem pointer: free the run first.
+/* Start a nested-sampling run (Sec. 2.1): draws n live points from the prior,
+ * i.e. uniformly in the unit cube (Philox counter (INIT | chunk << 8, 0,
+ * point, 0)), evaluates them, zeroes the evidence accumulators (Z = 0,
+ * X = 1).  *out is owned by the caller until ns_free.  The run keeps the problem pointer: free the run first.
  * Errors: NS_EINVAL (n_delete not in [1, n_live - 1], n_delete > max_batch,
  * n_live > 4096, d > 64). */
 int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, ns_run** out);
 
-/* Run up to n_iters NS iterations (fewer if the termination criterion is met)
- * and fill *st (may be NULL).  Synchronises the run's stream. */
+/* Run up to n_iters nested-sampling iterations (Sec. 2.1-2.2; fewer if the
+ * termination criterion is met) and fill *st (may be NULL).  An iteration
+ * deletes the k lowest live points (L* = the k-th lowest log L), books them
+ * into Z (Eq. 1) and X with n, n-1, ..., n-k+1 live points, and replaces them
+ * by k slice-sampling chains (Neal 2003, the NSS scheme the paper adopts) that
+ * evolve in parallel under the hard constraint log L > L*.  n_iters = 0 only
+ * fills *st.  Errors: NS_ETIMEOUT (a bounded device wait gave up, or the round
+ * bound was reached), NS_ECUDA.  Synchronises the run's stream. */
 int ns_step(ns_run* r, int n_iters, ns_status* st);
 
-/* Final evidence with the live points added (ascending log L with n, n-1, ...
+/* Final evidence (Eq. 1, the dead points weighted by the expected prior-volume
+ * shrinkage) with the live points added (ascending log L with n, n-1, ...
  * 1 live points) without changing the run: log Z, its error (standard
  * deviation over n_replays simulated shrinkage sequences, Philox counters
  * (ERR, replay, dead index, 0); n_replays <= 0 means 200), log X, the
@@ -323,14 +361,20 @@ int ns_step(ns_run* r, int n_iters, ns_status* st);
  * Any output pointer may be NULL.  Synchronises the run's stream. */
 int ns_evidence(const ns_run* r, int n_replays, double* logZ, double* logZ_err,
                 double* logX, double* H, long long* n_dead);
+/* (The simulated-shrinkage error assumes, as the paper's Sec. 4.2 notes, that
+ * each new point is drawn uniformly within the constraint; the slice chains
+ * approximate that draw.  Errors: NS_EINVAL for a NULL run, NS_ENOMEM,
+ * NS_ECUDA.) */
 
 /* Evidence of a dead-point sequence that the caller holds on the device, for
- * callers that cannot allocate device memory when they need it (work recorded
- * into a CUDA graph under a strict capture mode, where cudaMalloc is an error;
- * frameworks that own all device memory through their own pool).  It allocates
- * nothing: the per-replay values live in a library-owned array of 4096 doubles
- * that every GPU loading the library keeps until the process exits.  The paper
- * has no counterpart; this is an interface convenience.
+ * callers that cannot allocate device memory when they need the number: a host
+ * framework that reserves the device memory up front for its own caching pool
+ * (a library cudaMalloc then fails or fragments that pool), or a control loop
+ * that must not call cudaMalloc / cudaFree because they can synchronise the
+ * device.  It allocates nothing: the per-replay values live in a library-owned
+ * array of 4096 doubles that every GPU loading the library keeps until the
+ * process exits.  The paper has no counterpart; this is an interface
+ * convenience.
  *   logL_dev  (n) log L of the dead points in deletion order, the final live
  *             points appended in ascending order;
  *   nlive_dev (n) live-point count booked for each (n_live - j within a batch;
@@ -339,13 +383,47 @@ int ns_evidence(const ns_run* r, int n_replays, double* logZ, double* logZ_err,
  *             standard deviation (ddof 1) over n_replays Philox replays
  *             (counters (ERR, replay, index, 0) with key `seed`, so the same
  *             sequence and seed give ns_evidence's error), and the final ln X.
- * n_replays <= 0 means 200; 2 <= n_replays <= 4096 else NS_EINVAL.  The first
+ * n_replays <= 0 means 200; 2 <= n_replays <= 4096 else NS_EINVAL.  Every live
+ * count must be >= 1; a smaller one makes all three outputs NaN.  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current: make that first call before any stream capture.
- * All calls on a device share the array, so calls that overlap on the GPU race;
- * each call writes every slot it reads, so nothing needs clearing. */
+ * The address is kept for the process; calls after a cudaDeviceReset of that
+ * device are not supported.  All calls on a device share the array, so calls
+ * that overlap on the GPU race; each call writes every slot it reads, so
+ * nothing needs clearing. */
 int ns_evidence_noalloc(const double* logL_dev, const int* nlive_dev, long long n,
                         unsigned long long seed, int n_replays, double* out_dev, void* stream);
+
+/* One run split over several devices (the multi-device direction the paper
+ * leaves to future work, Sec. 4.1 and Sec. 5; the k chains of an iteration are
+ * independent, Sec. 2.2).  Every device holds an ns_run of the same problem and
+ * config (seed included) with n_shards = G and its own shard index s; the live
+ * set, deletion, evidence update, covariance factor and chain starts are
+ * computed redundantly and identically on every device, and shard s evolves
+ * the contiguous chains [floor(k s / G), floor(k (s + 1) / G)).  Per iteration:
+ *   ns_shard_evolve   deletion, evidence update, covariance, directions and
+ *                     starts, then the likelihood rounds of this shard's
+ *                     chains (synchronises the run's stream); does nothing
+ *                     once the run has converged (st->converged = 1);
+ *   ns_shard_export   this shard's final chain states into finals_dev
+ *                     (caller-owned device memory, rows = the shard's chain
+ *                     count, row = x[0..d), log L, evaluation count; FP64),
+ *                     asynchronously on the run's stream;
+ *   (the caller all-gathers the shards' rows in shard order, e.g. with NCCL;
+ *    the only exchange of the iteration: k (d + 2) doubles in total)
+ *   ns_shard_insert   all k rows in chain order (caller-owned device memory):
+ *                     the final points replace the deleted slots and the
+ *                     termination test is updated (synchronises).
+ * Each shard then holds exactly the single-device run's state (the chains draw
+ * from Philox counters keyed by chain index, and a likelihood value does not
+ * depend on the batch it is evaluated in), except that status bits and the
+ * non-finite count are the shard's own.  ns_step with n_iters > 0 returns
+ * NS_EINVAL on a shard; the ns_shard_* calls out of order return NS_EINVAL. */
+int ns_shard_evolve(ns_run* r, ns_status* st);
+int ns_shard_export(const ns_run* r, double* finals_dev);
+int ns_shard_insert(ns_run* r, const double* all_finals_dev, ns_status* st);
+/* The chain range [*chain_begin, *chain_end) this run evolves (0, k unless sharded). */
+int ns_shard_range(const ns_run* r, int* chain_begin, int* chain_end);
 
 /* Copy out the live set (x: n x d cube coordinates, logL: n); either may be NULL. */
 int ns_live_points(const ns_run* r, double* x, double* logL);

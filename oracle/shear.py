@@ -164,21 +164,25 @@ class ShearOracle:
         u &= np.uint32(0xFFFF0000)
         return u.view(np.float32).astype(np.float64)
 
-    def emulator(self, theta, bf16=False):
+    def emulator(self, theta, bf16=False, bf16_weights=False):
         """log10 P on the emulator's (z, k) grid, shape (n_z_emu, n_k).  With
         bf16=True the weights of layers >= 1 and every hidden activation are
         rounded to bfloat16 (arithmetic stays FP64): the model the tensor-core
-        path computes, up to its FP32 accumulation order."""
+        path computes, up to its FP32 accumulation order.  With
+        bf16_weights=True only those weights are rounded (activations exact):
+        the model whose gradient the split-bf16 adjoint computes, and a smooth
+        function of theta, so complex-step differentiation goes through it."""
         inp = self.inp
         x = (theta[inp["emu_inputs"]] - inp["emu_in_center"]) / inp["emu_in_scale"]
         Ws, bs = inp["emu_W"], inp["emu_b"]
+        rw = bf16 or bf16_weights
         h = x
         for l in range(len(Ws) - 1):
-            W = self.to_bf16(Ws[l]) if (bf16 and l >= 1) else Ws[l]
+            W = self.to_bf16(Ws[l]) if (rw and l >= 1) else Ws[l]
             h = np.tanh(W @ h + bs[l])
             if bf16:
                 h = self.to_bf16(h)
-        Wl = self.to_bf16(Ws[-1]) if bf16 else Ws[-1]
+        Wl = self.to_bf16(Ws[-1]) if rw else Ws[-1]
         y = Wl @ h + bs[-1]
         t = inp["emu_out_mu"] + inp["emu_out_sigma"] * y
         return t.reshape(self.n_z_emu, self.n_k)

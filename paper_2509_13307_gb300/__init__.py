@@ -6,11 +6,13 @@ include/gpuns.h); this package only marshals arguments.  Import is lazy: the
 library is loaded on first use and its absence is an error, never a fallback.
 """
 
-__all__ = ["Problem", "NestedRun", "MultiRun", "LogLike", "loglike_autograd", "nuts", "build"]
+__all__ = ["Problem", "NestedRun", "MultiRun", "ShardedRun", "shard_bounds", "LogLike", "loglike_autograd", "nuts",
+           "build"]
 
 
 def __getattr__(name):
-    if name in ("Problem", "NestedRun", "MultiRun", "LogLike", "loglike_autograd", "nuts"):
+    if name in ("Problem", "NestedRun", "MultiRun", "ShardedRun", "shard_bounds", "LogLike", "loglike_autograd",
+                "nuts"):
         from . import api
         return getattr(api, name)
     if name == "build":

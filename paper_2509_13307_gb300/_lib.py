@@ -22,7 +22,8 @@ EXPORTS = ["ns_strerror", "ns_problem_create", "ns_problem_free", "ns_problem_di
            "loglike_batch", "ns_model_batch", "ns_emulator_batch", "ns_problem_status", "ns_problem_tiles", "loglike_grad_batch", "ns_init", "ns_step", "ns_evidence",
            "ns_live_points", "ns_dead_points", "ns_last_iteration", "ns_profile_stage", "ns_profile_read",
            "ns_evidence_noalloc", "ns_multi_init", "ns_multi_step", "ns_multi_run",
-           "ns_multi_free", "ns_nuts_run", "ns_free"]
+           "ns_multi_free", "ns_nuts_run", "ns_shard_evolve", "ns_shard_export", "ns_shard_insert",
+           "ns_shard_range", "ns_free"]
 
 
 class Prior(C.Structure):
@@ -61,13 +62,14 @@ class ProblemDesc(C.Structure):
                 ("priors", C.POINTER(Prior)), ("n_data", C.c_int),
                 ("data", C.POINTER(C.c_double)), ("cov", C.POINTER(C.c_double)),
                 ("emu", EmulatorDesc), ("shear", ShearDesc), ("gauss", GaussDesc), ("max_batch", C.c_int),
-                ("cmb", CmbDesc)]
+                ("cmb", CmbDesc), ("hidden_tile", C.c_int)]
 
 
 class Config(C.Structure):
     _fields_ = [("n_live", C.c_int), ("n_delete", C.c_int), ("repeats", C.c_int), ("tol", C.c_double),
                 ("seed", C.c_ulonglong), ("width", C.c_double), ("step_cap", C.c_int), ("ridge", C.c_double),
-                ("rounds_per_sync", C.c_int), ("chain_groups", C.c_int)]
+                ("rounds_per_sync", C.c_int), ("chain_groups", C.c_int), ("n_shards", C.c_int),
+                ("shard", C.c_int)]
 
 
 class NutsConfig(C.Structure):
@@ -84,7 +86,7 @@ class NutsStats(C.Structure):
 class Status(C.Structure):
     _fields_ = [("iterations", C.c_longlong), ("evaluations", C.c_longlong), ("rounds", C.c_longlong),
                 ("converged", C.c_int), ("status_bits", C.c_int), ("logZ", C.c_double), ("logX", C.c_double),
-                ("lstar", C.c_double)]
+                ("lstar", C.c_double), ("nonfinite", C.c_longlong)]
 
 
 _lib = None
@@ -126,6 +128,10 @@ def load():
     lib.ns_multi_step.argtypes = [vp, C.c_int, C.POINTER(Status)]
     lib.ns_multi_run.argtypes = [vp, C.c_int, C.POINTER(vp)]
     lib.ns_multi_free.argtypes = [vp]
+    lib.ns_shard_evolve.argtypes = [vp, C.POINTER(Status)]
+    lib.ns_shard_export.argtypes = [vp, vp]
+    lib.ns_shard_insert.argtypes = [vp, vp, C.POINTER(Status)]
+    lib.ns_shard_range.argtypes = [vp, ip, ip]
     lib.ns_free.argtypes = [vp]
     for name in EXPORTS:
         getattr(lib, name).restype = C.c_char_p if name == "ns_strerror" else C.c_int

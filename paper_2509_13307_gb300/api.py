@@ -37,8 +37,9 @@ class Problem:
     """A likelihood problem resident on the current CUDA device."""
 
     def __init__(self, inp: dict, precision: str = "fp64", max_batch: int = 1024, data=None, cov=None,
-                 solve: str = "fold", form: str = "gauss"):
+                 solve: str = "fold", form: str = "gauss", hidden_tile: int = 0):
         self.lib = L.load()
+        self.hidden_tile = int(hidden_tile)
         self.inp = inp
         self.kind = inp["kind"]
         self.precision = precision
@@ -128,6 +129,7 @@ class Problem:
         keep.append(parr)
         desc.priors = parr
         desc.max_batch = max_batch
+        desc.hidden_tile = self.hidden_tile if precision.startswith("bf16") else 0
         if self.kind == "gauss":
             desc.gauss = L.GaussDesc(inp["mu"], inp["sigma"])
         else:
@@ -328,6 +330,7 @@ class RunStatus:
     logZ: float
     logX: float
     lstar: float
+    nonfinite: int = 0
 
 
 class NestedRun:
@@ -335,16 +338,47 @@ class NestedRun:
 
     def __init__(self, problem: Problem, n_live: int, n_delete: int, repeats: int | None = None,
                  tol: float = 1e-3, seed: int = 3, width: float = 1.0, step_cap: int = 100,
-                 ridge: float = 1e-12, rounds_per_sync: int = 0, chain_groups: int = 0, stream=None):
+                 ridge: float = 1e-12, rounds_per_sync: int = 0, chain_groups: int = 0, stream=None,
+                 n_shards: int = 1, shard: int = 0):
         self.lib = problem.lib
         self.problem = problem
         self.n_live, self.n_delete, self.d = n_live, n_delete, problem.d
         cfg = L.Config(n_live, n_delete, 0 if repeats is None else repeats, tol, seed, width, step_cap, ridge,
-                       rounds_per_sync, chain_groups)
+                       rounds_per_sync, chain_groups, n_shards, shard)
         self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         L.check(self.lib.ns_init(problem.handle, C.byref(cfg), _stream(self._stream_obj), C.byref(h)), "ns_init")
         self._h = h
+        self.n_shards, self.shard = max(1, n_shards), shard
+        b, e = C.c_int(), C.c_int()
+        L.check(self.lib.ns_shard_range(self._h, C.byref(b), C.byref(e)), "ns_shard_range")
+        self.chain_range = (b.value, e.value)
+
+    @staticmethod
+    def _status(st) -> "RunStatus":
+        return RunStatus(st.iterations, st.evaluations, st.rounds, bool(st.converged), st.status_bits,
+                         st.logZ, st.logX, st.lstar, st.nonfinite)
+
+    # ---- one run split over devices (ns_shard_*): see ShardedRun
+    def shard_evolve(self) -> "RunStatus":
+        st = L.Status()
+        L.check(self.lib.ns_shard_evolve(self._h, C.byref(st)), "ns_shard_evolve")
+        return self._status(st)
+
+    def shard_export(self) -> torch.Tensor:
+        """This shard's final chain states, (chains x (d + 2)) float64 on the device."""
+        b, e = self.chain_range
+        out = torch.empty((e - b, self.d + 2), dtype=torch.float64, device="cuda")
+        L.check(self.lib.ns_shard_export(self._h, C.c_void_p(out.data_ptr())), "ns_shard_export")
+        return out
+
+    def shard_insert(self, finals: torch.Tensor) -> "RunStatus":
+        finals = finals.contiguous()
+        if finals.shape != (self.n_delete, self.d + 2) or finals.dtype != torch.float64 or not finals.is_cuda:
+            raise ValueError("finals must be a (k, d + 2) float64 CUDA tensor")
+        st = L.Status()
+        L.check(self.lib.ns_shard_insert(self._h, C.c_void_p(finals.data_ptr()), C.byref(st)), "ns_shard_insert")
+        return self._status(st)
 
     @classmethod
     def from_config(cls, problem, sc, **kw):
@@ -354,7 +388,7 @@ class NestedRun:
         st = L.Status()
         L.check(self.lib.ns_step(self._h, n_iters, C.byref(st)), "ns_step")
         return RunStatus(st.iterations, st.evaluations, st.rounds, bool(st.converged), st.status_bits,
-                         st.logZ, st.logX, st.lstar)
+                         st.logZ, st.logX, st.lstar, st.nonfinite)
 
     def run(self, max_iters: int = 10 ** 9, chunk: int = 64) -> RunStatus:
         st = self.step(0)
@@ -387,6 +421,24 @@ class NestedRun:
                                         nl.ctypes.data_as(C.c_void_p), C.byref(cnt)), "ns_dead_points")
         m = cnt.value
         return x[:m], lg[:m], nl[:m]
+
+    def posterior(self):
+        """Posterior samples of the run: the dead points, then the live points in
+        ascending log L, as (cube x, log L, log w) with the normalised
+        importance weights of Eq. 1, w_i = L_i (X_{i-1} - X_i) / Z and the
+        expected shrinkage ln X_i = ln X_{i-1} - 1/n_i (host-side analysis of
+        the copied-out points)."""
+        xd, ld, nd = self.dead_points()
+        xl, ll = self.live_points()
+        o = np.argsort(ll, kind="stable")
+        x = np.vstack([xd, xl[o]])
+        lg = np.concatenate([ld, ll[o]])
+        nl = np.concatenate([nd, self.n_live - np.arange(self.n_live)]).astype(float)
+        lnX_prev = np.concatenate([[0.0], -np.cumsum(1.0 / nl)[:-1]])
+        logw = lg + lnX_prev + np.log(-np.expm1(-1.0 / nl))
+        m = np.max(logw)
+        logw = logw - (m + np.log(np.sum(np.exp(logw - m))))
+        return x, lg, logw
 
     def last_iteration(self):
         k = self.n_delete
@@ -421,6 +473,64 @@ class NestedRun:
             pass
 
 
+def shard_bounds(k: int, n_shards: int):
+    """Chain ranges of the shards of a run split over n_shards devices: shard s
+    evolves chains [floor(k s / G), floor(k (s + 1) / G)) (as ns_init sets them)."""
+    return [(k * s // n_shards, k * (s + 1) // n_shards) for s in range(n_shards)]
+
+
+class ShardedRun:
+    """One nested-sampling run split over the ranks of a torch.distributed
+    group, one device per rank (the k chains of an iteration are independent,
+    Sec. 2.2).  Every rank holds a shard run (NestedRun with n_shards = world
+    size, shard = rank; any object with the same shard_* methods works) of the
+    same problem and seed.  Per iteration the shards evolve their chains, then
+    one all-gather of every shard's final chain states (rows padded to the
+    largest shard, unpadded here in shard order) hands all k to every rank,
+    which inserts them; the deletion, covariance and evidence work is
+    redundant, so no other exchange is needed and every rank ends each
+    iteration with the single-device run's state."""
+
+    def __init__(self, shard_run, group=None):
+        import torch.distributed as dist
+        self.dist = dist
+        self.run = shard_run
+        self.group = group
+        self.world = dist.get_world_size(group)
+        self.rank = dist.get_rank(group)
+        self.k, self.d = shard_run.n_delete, shard_run.d
+        self.bounds = shard_bounds(self.k, self.world)
+        if tuple(shard_run.chain_range) != tuple(self.bounds[self.rank]):
+            raise ValueError(f"rank {self.rank} holds chains {shard_run.chain_range}, expected {self.bounds[self.rank]}")
+        self.rows = max(e - b for b, e in self.bounds)
+
+    def gather(self, local: torch.Tensor) -> torch.Tensor:
+        """All shards' rows (k x (d + 2)) in chain order from this rank's rows."""
+        w = self.d + 2
+        pad = torch.zeros((self.rows, w), dtype=local.dtype, device=local.device)
+        pad[:local.shape[0]] = local
+        parts = [torch.empty_like(pad) for _ in range(self.world)]
+        self.dist.all_gather(parts, pad, group=self.group)
+        return torch.cat([parts[s][:e - b] for s, (b, e) in enumerate(self.bounds)])
+
+    def step(self, n_iters: int = 1):
+        st = None
+        for _ in range(n_iters):
+            st = self.run.shard_evolve()
+            if st.converged:
+                break
+            st = self.run.shard_insert(self.gather(self.run.shard_export()))
+        return st
+
+    def run_until_converged(self, max_iters: int = 10 ** 9):
+        st = None
+        for _ in range(max_iters):
+            st = self.step(1)
+            if st.converged:
+                break
+        return st
+
+
 class MultiRun:
     """Several nested-sampling runs of one model packed into shared likelihood
     batches (ns_multi_*).  problems share the model; each has its own priors."""
@@ -431,7 +541,7 @@ class MultiRun:
         n = len(problems)
         arr = (C.c_void_p * n)(*[p.handle.value for p in problems])
         cfgs = (L.Config * n)(*[L.Config(sc.n_live, sc.n_delete, 0 if sc.repeats is None else sc.repeats, sc.tol,
-                                         sc.seed, sc.width, sc.step_cap, sc.ridge, 0, 1) for sc in samplers])
+                                         sc.seed, sc.width, sc.step_cap, sc.ridge, 0, 1, 0, 0) for sc in samplers])
         self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         L.check(self.lib.ns_multi_init(arr, n, cfgs, _stream(self._stream_obj), C.byref(h)), "ns_multi_init")
@@ -443,7 +553,7 @@ class MultiRun:
         st = (L.Status * self.n)()
         L.check(self.lib.ns_multi_step(self._h, n_iters, st), "ns_multi_step")
         return [RunStatus(s.iterations, s.evaluations, s.rounds, bool(s.converged), s.status_bits, s.logZ, s.logX,
-                          s.lstar) for s in st]
+                          s.lstar, s.nonfinite) for s in st]
 
     def run(self, max_iters: int = 10 ** 9, chunk: int = 64):
         sts = self.step(0)

@@ -72,6 +72,21 @@ __host__ __device__ inline Draw2 philox_uniforms(unsigned long long seed, uint32
 }
 
 // --------------------------------------------------------------------------
+// Phi^-1(c) of a Gaussian prior (Table 1).  With f32 (reduced-precision
+// problems) the quantile is taken in FP32 on the smaller tail probability
+// q = min(c, 1 - c) (1 - c is exact in FP64 for c >= 1/2) and mirrored, so a
+// coordinate within 2^-25 of 1 does not round to 1.0f, where the FP32
+// quantile is +inf; tails below 1e-37 (under FLT_MIN) use the FP64 quantile.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double gauss_quantile(double c, bool f32) {
+    if (!f32) return normcdfinv(c);
+    const double q = (c < 0.5) ? c : 1.0 - c;
+    if (q < 1e-37) return normcdfinv(c);
+    const double z = (double)normcdfinvf((float)q);
+    return (c < 0.5) ? z : -z;
+}
+
+// --------------------------------------------------------------------------
 // Catmull-Rom weights for taps (-1, 0, 1, 2) at fraction t.
 // --------------------------------------------------------------------------
 template <typename T>

@@ -47,7 +47,7 @@ __global__ void k_cube_to_theta(const double* __restrict__ cube, int d, int P,
 __global__ void k_cube_to_free(const double* __restrict__ cube, int d, int P,
                                const int* __restrict__ kind, const double* __restrict__ pa,
                                const double* __restrict__ pb, const int* __restrict__ free_of_full,
-                               double* __restrict__ theta, int B) {
+                               double* __restrict__ theta, int B, int f32) {
     const int row = blockIdx.x;
     if (row >= B) return;
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
@@ -55,7 +55,7 @@ __global__ void k_cube_to_free(const double* __restrict__ cube, int d, int P,
         if (f < 0) continue;
         const double c = cube[(size_t)row * d + f];
         theta[(size_t)row * d + f] = (kind[i] == NS_PRIOR_UNIFORM) ? pa[i] + (pb[i] - pa[i]) * c
-                                                                   : pa[i] + pb[i] * normcdfinv(c);
+                                                                   : pa[i] + pb[i] * gauss_quantile(c, f32 != 0);
     }
 }
 
@@ -592,7 +592,9 @@ int run_likelihood(const ns_problem* p, Workspace* ws, int grid_rows, double* lo
 // host helpers used by the C API in problem.cu
 namespace gpuns {
 int launch_cube_to_free(const ns_problem* p, const double* cube, int B, double* theta, cudaStream_t st) {
-    k_cube_to_free<<<B, 64, 0, st>>>(cube, p->d, p->P, p->d_pkind, p->d_pa, p->d_pb, p->d_free_of_full, theta, B);
+    // the sampler's prior transform: FP32 quantile for reduced-precision problems
+    k_cube_to_free<<<B, 64, 0, st>>>(cube, p->d, p->P, p->d_pkind, p->d_pa, p->d_pb, p->d_free_of_full, theta, B,
+                                     p->precision != NS_PREC_FP64 ? 1 : 0);
     NS_CUDA_TRY(cudaGetLastError());
     return NS_OK;
 }

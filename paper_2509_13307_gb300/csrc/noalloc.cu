@@ -2,15 +2,17 @@
 //
 // ns_evidence() allocates a small device buffer for the per-replay log Z values
 // of its simulated-shrinkage error estimate.  Some callers cannot allocate
-// device memory at the time they need the number: code that records its work
-// into a CUDA graph under a strict capture mode (where cudaMalloc is an error),
-// or a host framework that owns all device memory through its own pool and
-// forbids allocations by libraries it calls.  ns_evidence_noalloc() serves
-// them: the caller passes the sequence and an output buffer, and the per-replay
-// values go to the file-scope array g_replay_scratch below, which every GPU that
-// loads this library holds (kMaxNoallocReplays doubles) until the process exits.
+// device memory when they need the number: a host framework that reserves the
+// device memory up front for its own caching pool (a library cudaMalloc then
+// fails or fragments that pool, and the framework forbids it), or a control
+// loop that must not call cudaMalloc / cudaFree because they can synchronise
+// the device and stall its other streams.  ns_evidence_noalloc() serves them:
+// the caller passes the sequence and an output buffer, and the per-replay values
+// go to the file-scope array g_replay_scratch below, which every GPU that loads
+// this library holds (kMaxNoallocReplays doubles) until the process exits.
 #include <mutex>
 
+#include "evidence_seq.cuh"
 #include "likelihood.cuh"
 
 namespace gpuns {
@@ -20,87 +22,38 @@ constexpr int kMaxNoallocReplays = 4096;   // 32 KiB of device memory per GPU
 // Shared by every call on a device; each call overwrites the slots it uses.
 static __device__ __align__(256) double g_replay_scratch[kMaxNoallocReplays];
 
-__device__ inline double nl_lse2(double a, double b) {
-    if (a == -INFINITY) return b;
-    if (b == -INFINITY) return a;
-    const double m = fmax(a, b);
-    return m + log(exp(a - m) + exp(b - m));
-}
-
-// Block-wide log-sum-exp of sum_i exp(logL_i + ln X_{i-1} + ln(1 - t_i)) with
-// ln t_i = lnt(i); threads own contiguous chunks, offsets by a block scan.
-template <typename LnT>
-__device__ double sequence_logZ(const double* __restrict__ logL, long long N, LnT lnt, double* red,
-                                double* logX_out) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const long long chunk = (N + nt - 1) / nt;
-    const long long lo = min(N, (long long)tid * chunk), hi = min(N, lo + chunk);
-    double tot = 0.0;
-    for (long long i = lo; i < hi; ++i) tot += lnt(i);
-    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-    double inc = tot;
-    for (int o = 1; o < 32; o <<= 1) { const double y = __shfl_up_sync(0xffffffffu, inc, o); if (lane >= o) inc += y; }
-    __syncthreads();
-    if (lane == 31) red[wid] = inc;
-    __syncthreads();
-    if (wid == 0) {
-        const double v = (lane < nw) ? red[lane] : 0.0;
-        double vi = v;
-        for (int o = 1; o < 32; o <<= 1) { const double y = __shfl_up_sync(0xffffffffu, vi, o); if (lane >= o) vi += y; }
-        if (lane < nw) red[lane] = vi - v;
-        if (lane == nw - 1) red[32] = vi;      // total ln X
-    }
-    __syncthreads();
-    double logX = red[wid] + inc - tot;
-    if (logX_out && tid == 0) *logX_out = red[32];
-    __syncthreads();
-    double mx = -INFINITY, acc = 0.0;
-    for (long long i = lo; i < hi; ++i) {
-        const double lt = lnt(i);
-        const double term = logL[i] + logX + log(-expm1(lt));
-        if (term > mx) { acc = (mx == -INFINITY ? 0.0 : acc * exp(mx - term)) + 1.0; mx = term; }
-        else if (term > -INFINITY) acc += exp(term - mx);
-        logX += lt;
-    }
-    double gmx = warp_max(mx);
-    if (lane == 0) red[34 + wid] = gmx;
-    __syncthreads();
-    if (wid == 0) {
-        double v = (lane < nw) ? red[34 + lane] : -INFINITY;
-        v = warp_max(v);
-        if (lane == 0) red[33] = v;
-    }
-    __syncthreads();
-    gmx = red[33];
-    __syncthreads();
-    double part = (mx > -INFINITY && gmx > -INFINITY) ? acc * exp(mx - gmx) : 0.0;
-    part = block_sum(part, red);
-    return (gmx > -INFINITY) ? gmx + log(part) : -INFINITY;
-}
-
 // One block per replay s: ln t_i = ln(U_{s,i}) / n_i, U from Philox (ERR, s, i, 0).
 __global__ void __launch_bounds__(256)
 k_noalloc_replays(const double* __restrict__ logL, const int* __restrict__ nlive, long long N,
                   unsigned long long seed, double* __restrict__ scratch) {
     __shared__ double red[80];
     const int s = blockIdx.x;
+    auto Lof = [&](long long i) -> double { return logL[i]; };
     auto lnt = [&](long long i) -> double {
         const Draw2 u = philox_uniforms(seed, P_ERR, 0, (uint32_t)s, (uint32_t)i, 0);
         return log(u.a) / nlive[i];
     };
-    const double lz = sequence_logZ(logL, N, lnt, red, nullptr);
+    const double lz = sequence_logZ(Lof, N, lnt, red, nullptr);
     if (threadIdx.x == 0) scratch[s] = lz;
 }
 
 // out[0] = ln Z with the expected shrinkage ln t_i = -1/n_i, out[1] = standard
-// deviation (ddof 1) of the replays in scratch, out[2] = final ln X.
+// deviation (ddof 1) of the replays in scratch, out[2] = final ln X.  A live
+// count below 1 anywhere in the sequence makes all three outputs NaN.
 __global__ void __launch_bounds__(256)
 k_noalloc_finish(const double* __restrict__ logL, const int* __restrict__ nlive, long long N, int n_replays,
                  const double* __restrict__ scratch, double* __restrict__ out) {
     __shared__ double red[80];
     __shared__ double logX;
+    int bad = 0;
+    for (long long i = threadIdx.x; i < N; i += blockDim.x) bad |= (nlive[i] < 1);
+    if (__syncthreads_or(bad)) {
+        if (threadIdx.x < 3) out[threadIdx.x] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    auto Lof = [&](long long i) -> double { return logL[i]; };
     auto lnt = [&](long long i) -> double { return -1.0 / nlive[i]; };
-    const double lz = sequence_logZ(logL, N, lnt, red, &logX);
+    const double lz = sequence_logZ(Lof, N, lnt, red, &logX);
     double m = 0.0;
     for (int s = threadIdx.x; s < n_replays; s += blockDim.x) m += scratch[s];
     m = block_sum(m, red) / n_replays;
@@ -119,7 +72,9 @@ k_noalloc_finish(const double* __restrict__ logL, const int* __restrict__ nlive,
 using namespace gpuns;
 
 // Device address of g_replay_scratch for each device, looked up once per device
-// with that device current (the host-side symbol is only a stand-in).
+// with that device current (the host-side symbol is only a stand-in).  The
+// cached address belongs to the device's primary context: it is not refreshed
+// after a cudaDeviceReset, which this entry point does not support.
 static double* g_scratch_addr[64] = {nullptr};
 static std::mutex g_scratch_mu;
 

@@ -30,6 +30,7 @@
 #include <new>
 #include <vector>
 
+#include "evidence_seq.cuh"
 #include "likelihood.cuh"
 
 namespace gpuns {
@@ -41,6 +42,7 @@ struct Scalars {
     long long n_dead, iter, evals;
     int status, n_active, batch, converged;
     int batch2[2];        // round batch counters of chain group 0 (round i uses batch2[i & 1])
+    int nonfinite;        // likelihood evaluations that returned NaN / inf (counted as outside)
 };
 
 struct RunDev {
@@ -73,6 +75,7 @@ struct RunDev {
     int* batch_ctr;       // row counter of the round's batch (shared by packed runs)
     int* batch_next;      // the next round's counter, zeroed by this round's slice kernel (or null)
     int run_id;
+    int sh_c0, sh_c1;     // chains this run evolves: [sh_c0, sh_c1) of k (a shard of a run split over devices)
     int chain0;           // first chain of this group of rounds
     int grp_chains;       // chains of this group
     // prior transform fused into the proposal emission (Table 1)
@@ -204,7 +207,7 @@ __global__ void k_init_finish(RunDev r, const double* __restrict__ logL) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < r.n) {
         double v = logL[i];
-        if (!isfinite(v)) { v = -INFINITY; atomicOr(&r.sc->status, NS_BIT_NONFINITE); }
+        if (!isfinite(v)) { v = -INFINITY; atomicOr(&r.sc->status, NS_BIT_NONFINITE); atomicAdd(&r.sc->nonfinite, 1); }
         r.live_L[i] = v;
         for (int j = 0; j < r.d; ++j) r.live_x[(size_t)i * r.d + j] = r.prop[(size_t)i * r.d + j];
     }
@@ -355,7 +358,10 @@ __global__ void k_chains_start(RunDev r) {
         r.ch_row[c] = -1;
         r.ch_row2[c] = -1;
     }
-    if (c == 0) { r.sc->n_active = r.k; r.sc->batch = 0; r.sc->batch2[0] = 0; r.sc->batch2[1] = 0; }
+    if (c == 0) {
+        r.sc->n_active = r.sh_c1 - r.sh_c0;
+        r.sc->batch = 0; r.sc->batch2[0] = 0; r.sc->batch2[1] = 0;
+    }
 }
 
 // Slice directions for every (chain, move) of the iteration, one warp each:
@@ -367,8 +373,8 @@ __global__ void __launch_bounds__(256) k_directions(RunDev r) {
     __shared__ double zs[8][64];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long g = (long long)blockIdx.x * 8 + wib;
-    if (g >= (long long)r.k * r.R) return;
-    const int c = (int)(g / r.R), move = (int)(g % r.R);
+    if (g >= (long long)(r.sh_c1 - r.sh_c0) * r.R) return;
+    const int c = r.sh_c0 + (int)(g / r.R), move = (int)(g % r.R);
     const int d = r.d;
     const int it = (int)r.sc->iter;
     double* zsw = zs[wib];
@@ -389,7 +395,7 @@ __global__ void __launch_bounds__(256) k_directions(RunDev r) {
         if (2 * lane + 1 < d) zsw[2 * lane + 1] = z1 / nrm;
     }
     __syncwarp();
-    double* out = r.dirs + (size_t)g * d;
+    double* out = r.dirs + ((size_t)c * r.R + move) * d;
     if (lane < d) {
         double a0 = 0.0;
         for (int b = 0; b <= lane; ++b) a0 += r.chol[lane * d + b] * zsw[b];
@@ -420,7 +426,7 @@ __device__ __forceinline__ void emit_theta(const RunDev& r, int row, double y0, 
             } else {
                 const double c = (f < 32) ? c0 : c1;
                 if (r.pkind[i] == NS_PRIOR_UNIFORM) v = r.pa[i] + (r.pb[i] - r.pa[i]) * c;
-                else v = r.pa[i] + r.pb[i] * (r.prior_f32 ? (double)normcdfinvf((float)c) : normcdfinv(c));
+                else v = r.pa[i] + r.pb[i] * gauss_quantile(c, r.prior_f32 != 0);
             }
             r.theta_full[(size_t)row * r.P + i] = v;
         }
@@ -453,11 +459,11 @@ __device__ void advance_chain(const RunDev& r, int c, int lane) {
     int move = r.ch_move[c], step = r.ch_step[c], step2 = r.ch_step2[c];
     int row = r.ch_row[c], row2 = r.ch_row2[c], evals = r.ch_evals[c];
     double l = r.ch_l[c], rr = r.ch_r[c], t = r.ch_t[c], chL = r.ch_L[c];
-    int flags = 0;
+    int flags = 0, n_nonfinite = 0;
     auto inside_of = [&](int rw) {
         const double v = r.logL[rw];
         const bool fin = isfinite(v);
-        if (!fin) flags |= NS_BIT_NONFINITE;
+        if (!fin) { flags |= NS_BIT_NONFINITE; ++n_nonfinite; }
         return fin && (v > lstar);
     };
 
@@ -544,6 +550,7 @@ __device__ void advance_chain(const RunDev& r, int c, int lane) {
         r.ch_row[c] = row; r.ch_row2[c] = row2;
         r.ch_evals[c] = evals; r.ch_l[c] = l; r.ch_r[c] = rr; r.ch_t[c] = t; r.ch_L[c] = chL;
         if (flags) atomicOr(&r.sc->status, flags);
+        if (n_nonfinite) atomicAdd(&r.sc->nonfinite, n_nonfinite);
         if (phase == PH_DONE) atomicSub(&r.sc->n_active, 1);
     }
 }
@@ -572,6 +579,30 @@ __global__ void __launch_bounds__(32 * kSliceWarps) k_slice_advance_multi(const 
     while (r + 1 < n_runs && chain_off[r + 1] <= g) ++r;
     const RunDev rd = runs[r];
     advance_chain(rd, g - chain_off[r], threadIdx.x & 31);
+}
+
+// A shard's final chain states for the exchange between devices: row c - sh_c0
+// of out = (x[0..d), log L, evaluations) of chain c in [sh_c0, sh_c1).
+__global__ void k_shard_pack(RunDev r, double* __restrict__ out) {
+    const int w = r.d + 2;
+    const int nc = r.sh_c1 - r.sh_c0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nc * w; t += gridDim.x * blockDim.x) {
+        const int i = t / w, j = t % w, c = r.sh_c0 + i;
+        out[t] = (j < r.d) ? r.ch_x[(size_t)c * r.d + j] : (j == r.d) ? r.ch_L[c] : (double)r.ch_evals[c];
+    }
+}
+
+// Every chain's final state (k rows in chain order, as k_shard_pack writes
+// them) into the chain arrays, for k_insert.
+__global__ void k_shard_unpack(RunDev r, const double* __restrict__ in) {
+    const int w = r.d + 2;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < r.k * w; t += gridDim.x * blockDim.x) {
+        const int c = t / w, j = t % w;
+        const double v = in[t];
+        if (j < r.d) r.ch_x[(size_t)c * r.d + j] = v;
+        else if (j == r.d) r.ch_L[c] = v;
+        else r.ch_evals[c] = (int)v;
+    }
 }
 
 __global__ void k_insert(RunDev r) {
@@ -634,58 +665,16 @@ __global__ void __launch_bounds__(1024) k_final_evidence(RunDev r, double* out /
 // One block per replay: ln t_i = ln(U_{s,i}) / n_i; ln Z_s = LSE_i(L_i + ln X_{i-1} + ln(1 - t_i)).
 __global__ void __launch_bounds__(256) k_err_replays(RunDev r, long long n_dead, double* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* red = reinterpret_cast<double*>(smem_raw);     // 64
+    double* red = reinterpret_cast<double*>(smem_raw);     // 128 doubles
     const int s = blockIdx.x;
-    const long long N = n_dead + r.n;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const long long chunk = (N + nt - 1) / nt;
-    const long long lo = min(N, (long long)tid * chunk), hi = min(N, lo + chunk);
     auto Lof = [&](long long i) -> double { return (i < n_dead) ? r.dead_L[i] : r.live_L[r.order[i - n_dead]]; };
     auto nof = [&](long long i) -> int { return (i < n_dead) ? r.dead_n[i] : (int)(r.n - (i - n_dead)); };
     auto lnt = [&](long long i) -> double {
         const Draw2 u = philox_uniforms(r.seed, P_ERR, 0, (uint32_t)s, (uint32_t)i, 0);
         return log(u.a) / nof(i);
     };
-    double tot = 0.0;
-    for (long long i = lo; i < hi; ++i) tot += lnt(i);
-    // exclusive scan of per-thread totals
-    double* sc = red;   // 32 + 32
-    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-    double inc = tot;
-    for (int o = 1; o < 32; o <<= 1) { double y = __shfl_up_sync(0xffffffffu, inc, o); if (lane >= o) inc += y; }
-    if (lane == 31) sc[wid] = inc;
-    __syncthreads();
-    if (wid == 0) {
-        double v = (lane < nw) ? sc[lane] : 0.0, vi = v;
-        for (int o = 1; o < 32; o <<= 1) { double y = __shfl_up_sync(0xffffffffu, vi, o); if (lane >= o) vi += y; }
-        if (lane < nw) sc[lane] = vi - v;
-    }
-    __syncthreads();
-    double logX = sc[wid] + inc - tot;   // ln X before my first point
-    __syncthreads();
-    double mx = -INFINITY, acc = 0.0;    // running LSE
-    for (long long i = lo; i < hi; ++i) {
-        const double lt = lnt(i);
-        const double term = Lof(i) + logX + log(-expm1(lt));
-        if (term > mx) { acc = acc * exp(mx - term) + 1.0; mx = term; }
-        else if (term > -INFINITY) acc += exp(term - mx);
-        logX += lt;
-    }
-    // combine (mx, acc) across the block
-    double gmx = warp_max(mx);
-    if (lane == 0) red[32 + wid] = gmx;
-    __syncthreads();
-    if (wid == 0) {
-        double v = (lane < nw) ? red[32 + lane] : -INFINITY;
-        v = warp_max(v);
-        if (lane == 0) red[32] = v;
-    }
-    __syncthreads();
-    gmx = red[32];
-    __syncthreads();
-    double part = (mx > -INFINITY) ? acc * exp(mx - gmx) : 0.0;
-    part = block_sum(part, red);
-    if (tid == 0) out[s] = gmx + log(part);
+    const double lz = sequence_logZ(Lof, n_dead + r.n, lnt, red, nullptr);
+    if (threadIdx.x == 0) out[s] = lz;
 }
 
 }  // namespace gpuns
@@ -714,6 +703,8 @@ struct ns_run {
     // chain groups: group 0 uses rd / ws; group 1 (chains [k0, k)) its own
     // batch, proposals and likelihood workspace, with rounds on a second stream
     int n_groups = 1, k0 = 0;
+    int n_shards = 1;             // > 1: this run evolves one shard of the chains (ns_shard_*)
+    int shard_pending = 0;        // an iteration's chains evolved, waiting for ns_shard_insert
     int* grp1_ctr = nullptr;      // chain group 1's pair of round batch counters
     Workspace ws1;
     RunDev grd[2]{};
@@ -787,8 +778,8 @@ static int launch_round(ns_run* r, int g, int i, cudaStream_t st, const StagePro
 // graph, since the dead-list pointers in rd change when it grows).
 static void refresh_groups(ns_run* r) {
     r->grd[0] = r->rd;
-    r->grd[0].chain0 = 0;
-    r->grd[0].grp_chains = r->n_groups > 1 ? r->k0 : r->k;
+    r->grd[0].chain0 = r->rd.sh_c0;
+    r->grd[0].grp_chains = r->n_groups > 1 ? r->k0 : r->rd.sh_c1 - r->rd.sh_c0;
     if (r->n_groups > 1) {
         RunDev& g1 = r->grd[1];
         g1 = r->rd;
@@ -878,6 +869,8 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
     const int n = cfg->n_live, k = cfg->n_delete, d = p->d;
     if (n < 2 || n > 4096 || k < 1 || k >= n || d < 1 || d > 64) return NS_EINVAL;
     if (!(cfg->width > 0) || cfg->step_cap < 1 || !(cfg->tol > 0)) return NS_EINVAL;
+    const int G = cfg->n_shards > 1 ? cfg->n_shards : 1;
+    if (G > k || cfg->shard < 0 || cfg->shard >= G || (G > 1 && cfg->chain_groups == 2)) return NS_EINVAL;
     ns_run* r = new (std::nothrow) ns_run();
     if (!r) return NS_ENOMEM;
     auto fail = [&](int s) { run_release(r); return s; };
@@ -927,8 +920,12 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
     k_reset_chains<<<(k + 127) / 128, 128, 0, r->st>>>(rd);
     rd.batch_ctr = &rd.sc->batch;
     rd.run_id = 0;
-    rd.chain0 = 0;
-    rd.grp_chains = k;
+    // a shard evolves the contiguous chains [k s / G, k (s + 1) / G)
+    rd.sh_c0 = (int)((long long)k * (G > 1 ? cfg->shard : 0) / G);
+    rd.sh_c1 = (int)((long long)k * (G > 1 ? cfg->shard + 1 : 1) / G);
+    r->n_shards = G;
+    rd.chain0 = rd.sh_c0;
+    rd.grp_chains = rd.sh_c1 - rd.sh_c0;
     rd.P = p->P;
     rd.pkind = p->d_pkind;
     rd.pa = p->d_pa;
@@ -976,7 +973,10 @@ static int rounds_per_sync(const ns_run* r) {
     return (R + 1) & ~1;
 }
 
-static int one_iteration(ns_run* r) {
+// First part of an iteration: deletion and evidence update, live covariance
+// and its factor, directions and starts, then likelihood rounds until every
+// chain of this run (or of its shard) has made its R slice moves.
+static int iteration_evolve(ns_run* r) {
     RunDev& rd = r->rd;
     cudaStream_t st = r->st;
     NS_TRY(grow_dead(r, r->h_sc->n_dead + r->k));
@@ -986,7 +986,7 @@ static int one_iteration(ns_run* r) {
     k_live_mean<<<r->d, 256, 0, st>>>(rd);
     k_live_cov<<<r->d * (r->d + 1) / 2, 256, 0, st>>>(rd, r->cfg.ridge);
     k_cholesky<<<1, 128, 0, st>>>(rd);
-    k_directions<<<(unsigned)(((long long)r->k * r->R + 7) / 8), 256, 0, st>>>(rd);
+    k_directions<<<(unsigned)(((long long)(rd.sh_c1 - rd.sh_c0) * r->R + 7) / 8), 256, 0, st>>>(rd);
     k_chains_start<<<(r->k + 127) / 128, 128, 0, st>>>(rd);
     NS_CUDA_TRY(cudaGetLastError());
     const int R = rounds_per_sync(r);
@@ -1007,6 +1007,14 @@ static int one_iteration(ns_run* r) {
         if (r->h_sc->n_active == 0) break;
         if (done > max_rounds) { r->h_sc->status |= NS_BIT_TIMEOUT; return NS_ETIMEOUT; }
     }
+    return NS_OK;
+}
+
+// Second part: every chain's final point replaces its deleted slot, the
+// evaluation count and the termination test are updated.
+static int iteration_insert(ns_run* r) {
+    RunDev& rd = r->rd;
+    cudaStream_t st = r->st;
     k_insert<<<1, 1024, 0, st>>>(rd);
     NS_CUDA_TRY(cudaGetLastError());
     NS_TRY(sync_scalars(r));
@@ -1014,13 +1022,12 @@ static int one_iteration(ns_run* r) {
     return NS_OK;
 }
 
-extern "C" int ns_step(ns_run* r, int n_iters, ns_status* st) {
-    if (!r || n_iters < 0) return NS_EINVAL;
-    int s = NS_OK;
-    for (int i = 0; i < n_iters; ++i) {
-        if (r->h_sc->converged) break;
-        if ((s = one_iteration(r)) != NS_OK) break;
-    }
+static int one_iteration(ns_run* r) {
+    NS_TRY(iteration_evolve(r));
+    return iteration_insert(r);
+}
+
+static void fill_status(const ns_run* r, ns_status* st) {
     if (st) {
         st->iterations = r->h_sc->iter;
         st->evaluations = r->h_sc->evals;
@@ -1030,8 +1037,58 @@ extern "C" int ns_step(ns_run* r, int n_iters, ns_status* st) {
         st->logZ = r->h_sc->logZ;
         st->logX = r->h_sc->logX;
         st->lstar = r->h_sc->lstar;
+        st->nonfinite = r->h_sc->nonfinite;
     }
+}
+
+extern "C" int ns_step(ns_run* r, int n_iters, ns_status* st) {
+    if (!r || n_iters < 0) return NS_EINVAL;
+    if (r->n_shards > 1 && n_iters > 0) return NS_EINVAL;   // sharded runs advance by ns_shard_*
+    int s = NS_OK;
+    for (int i = 0; i < n_iters; ++i) {
+        if (r->h_sc->converged) break;
+        if ((s = one_iteration(r)) != NS_OK) break;
+    }
+    fill_status(r, st);
     return s;
+}
+
+extern "C" int ns_shard_evolve(ns_run* r, ns_status* st) {
+    if (!r || r->shard_pending) return NS_EINVAL;
+    int s = NS_OK;
+    if (!r->h_sc->converged) {
+        s = iteration_evolve(r);
+        if (s == NS_OK) r->shard_pending = 1;
+    }
+    fill_status(r, st);
+    return s;
+}
+
+extern "C" int ns_shard_export(const ns_run* r, double* finals_dev) {
+    if (!r || !finals_dev || !r->shard_pending) return NS_EINVAL;
+    const int rows = r->rd.sh_c1 - r->rd.sh_c0;
+    const int blocks = std::max(1, std::min(1024, (rows * (r->d + 2) + 255) / 256));
+    k_shard_pack<<<blocks, 256, 0, r->st>>>(r->rd, finals_dev);
+    NS_CUDA_TRY(cudaGetLastError());
+    return NS_OK;
+}
+
+extern "C" int ns_shard_insert(ns_run* r, const double* all_finals_dev, ns_status* st) {
+    if (!r || !all_finals_dev || !r->shard_pending) return NS_EINVAL;
+    const int blocks = std::max(1, std::min(1024, (r->k * (r->d + 2) + 255) / 256));
+    k_shard_unpack<<<blocks, 256, 0, r->st>>>(r->rd, all_finals_dev);
+    NS_CUDA_TRY(cudaGetLastError());
+    r->shard_pending = 0;
+    const int s = iteration_insert(r);
+    fill_status(r, st);
+    return s;
+}
+
+extern "C" int ns_shard_range(const ns_run* r, int* chain_begin, int* chain_end) {
+    if (!r) return NS_EINVAL;
+    if (chain_begin) *chain_begin = r->rd.sh_c0;
+    if (chain_end) *chain_end = r->rd.sh_c1;
+    return NS_OK;
 }
 
 extern "C" int ns_evidence(const ns_run* rc, int n_replays, double* logZ, double* logZ_err, double* logX,
@@ -1236,6 +1293,8 @@ extern "C" int ns_multi_init(const ns_problem* const* problems, int n_runs, cons
         ns_run* r = nullptr;
         ns_config ci = cfgs[i];
         ci.chain_groups = 1;      // packed runs share one batch instead
+        ci.n_shards = 0;          // and are not split across devices
+        ci.shard = 0;
         int s = ns_init(problems[i], &ci, stream, &r);
         if (s) return fail(s);
         m->runs.push_back(r);
@@ -1272,7 +1331,7 @@ static int multi_start_iteration(ns_multi* m, int i) {
     k_live_mean<<<r->d, 256, 0, m->st>>>(r->rd);
     k_live_cov<<<r->d * (r->d + 1) / 2, 256, 0, m->st>>>(r->rd, r->cfg.ridge);
     k_cholesky<<<1, 128, 0, m->st>>>(r->rd);
-    k_directions<<<(unsigned)(((long long)r->k * r->R + 7) / 8), 256, 0, m->st>>>(r->rd);
+    k_directions<<<(unsigned)(((long long)(r->rd.sh_c1 - r->rd.sh_c0) * r->R + 7) / 8), 256, 0, m->st>>>(r->rd);
     k_chains_start<<<(r->k + 127) / 128, 128, 0, m->st>>>(r->rd);
     NS_CUDA_TRY(cudaGetLastError());
     return NS_OK;
@@ -1353,6 +1412,7 @@ extern "C" int ns_multi_step(ns_multi* m, int n_iters, ns_status* st) {
             st[i].logZ = h->logZ;
             st[i].logX = h->logX;
             st[i].lstar = h->lstar;
+            st[i].nonfinite = h->nonfinite;
         }
     return NS_OK;
 }

@@ -390,6 +390,9 @@ static int autotune_hidden_tiles(ns_problem* p, int last_hidden) {
 static int validate_desc(const ns_problem_desc* d) {
     if (!d || !d->priors || d->n_params < 1 || d->n_params > 256 || d->max_batch < 1) return NS_EINVAL;
     if (d->precision < 0 || d->precision > NS_PREC_BF16_F64CHI2) return NS_EINVAL;
+    if (d->hidden_tile != 0 && d->hidden_tile != 16 && d->hidden_tile != 32 && d->hidden_tile != 64 &&
+        d->hidden_tile != 128)
+        return NS_EINVAL;
     int nfree = 0;
     for (int i = 0; i < d->n_params; ++i) {
         const ns_prior& q = d->priors[i];
@@ -620,7 +623,20 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
             int s = make_tensor_map_bf16(&p->tmB[l], p->d_W[l], N, p->dims[l], tn, kps);
             if (s) return fail(s);
         }
-        int s = autotune_hidden_tiles(p, e.n_layers - 2);   // hidden layers 1 .. L-2
+        int s = NS_OK;
+        if (desc->hidden_tile > 0) {
+            // a caller-chosen N-tile for every tensor-core hidden layer (no autotuning)
+            p->tile_ms.assign(e.n_layers, 0.0f);
+            for (int l = 1; l <= e.n_layers - 2 && !s; ++l) {
+                if (!tc_layer(l)) continue;
+                if (desc->hidden_tile > p->dims[l + 1]) return fail(NS_EINVAL);
+                p->tile_n[l] = desc->hidden_tile;
+                s = make_tensor_map_bf16(&p->tmB[l], p->d_W[l], p->dims[l + 1], p->dims[l], desc->hidden_tile,
+                                         gemm_tc_kps(p->dims[l]));
+            }
+        } else {
+            s = autotune_hidden_tiles(p, e.n_layers - 2);   // hidden layers 1 .. L-2
+        }
         if (s) return fail(s);
     }
 

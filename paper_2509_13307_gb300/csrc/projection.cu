@@ -67,6 +67,7 @@ template <> struct Math<float, false> {
     static __device__ __forceinline__ float ex(float x) { return expf(x); }
     static __device__ __forceinline__ float lg(float x) { return logf(x); }
     static __device__ __forceinline__ float p10(float v) { return exp2f(v * 3.32192809488736234787f); }
+    static __device__ __forceinline__ float e2(float v) { return exp2f(v); }
     static __device__ __forceinline__ float div(float a, float b) { return a / b; }
     static __device__ __forceinline__ float rsq(float x) { return 1.f / sqrtf(x); }
 };
@@ -78,6 +79,11 @@ template <> struct Math<float, true> {
     static __device__ __forceinline__ float p10(float v) {
         float y;
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v * 3.32192809488736234787f));
+        return y;
+    }
+    static __device__ __forceinline__ float e2(float v) {
+        float y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
         return y;
     }
 };
@@ -338,43 +344,57 @@ __host__ __device__ inline int limber_pitch(int n_k) {
 
 // FP32 Limber inner loop for the multipole pair (ell0, ell1) of a warp: the two
 // lookups and their pair sums run as packed f32x2 arithmetic (one FFMA2 per
-// two FMAs).  Nodes n0, n0 + 128, ...; acc[p] / acc[NP + p] receive the pair
+// two FMAs).  Nodes n0, n0 + stride, ...; acc[p] / acc[NP + p] receive the pair
 // sums of ell0 / ell1.  With a single multipole left, ell1 = ell0 and the
-// second half is discarded by the caller.
-template <int NB, bool FAST>
-__device__ __forceinline__ void limber_pair_f32(const float* __restrict__ U, int PK, int N, int n_k,
-                                                const int* __restrict__ zrp, const float* __restrict__ zwp,
+// second half is discarded by the caller.  The node constants come from shared
+// memory: zoff[n] = offset of the node's first z-tap row (+ the 3 ghost/pad
+// columns) in the padded table, zw[n] = its four doubled z-weights.  With a
+// compile-time row pitch PKC the four tap rows sit at immediate offsets.
+template <int NB, bool FAST, int PKC>
+__device__ __forceinline__ void limber_pair_f32(const float* __restrict__ U, int PKr, int N, int n_k,
+                                                const int* __restrict__ zoff, const float4* __restrict__ zw,
                                                 const float* __restrict__ lnchi, const float* __restrict__ V,
                                                 int Np, float lne0, float lne1, float lkmin, float lkmax,
                                                 float inv_dk, int n0, int stride, float* acc) {
     using M = Math<float, FAST>;
+    const int PK = PKC ? PKC : PKr;
     constexpr int NP = NB * (NB + 1) / 2;
     const float2 one = make_float2(1.f, 1.f), m1 = make_float2(-1.f, -1.f), two = make_float2(2.f, 2.f);
     const float2 three = make_float2(3.f, 3.f), m3 = make_float2(-3.f, -3.f), four = make_float2(4.f, 4.f);
     const float2 m5 = make_float2(-5.f, -5.f);
     const float gmax = 8388608.f + (float)(n_k - 2);
+    const float umax = (lkmax - lkmin) * inv_dk;
+    // table coordinate u = (ln(ell + 1/2) - ln chi - lnk_min) / dlnk of both
+    // multipoles as one FFMA2: u = a - ln chi / dlnk
+    const float2 ua = make_float2((lne0 - lkmin) * inv_dk, (lne1 - lkmin) * inv_dk);
+    const float2 minv = make_float2(-inv_dk, -inv_dk);
+    const float2 half = make_float2(8388607.5f, 8388607.5f), p23 = make_float2(8388608.f, 8388608.f);
     float2 a2[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) a2[p] = make_float2(0.f, 0.f);
     for (int n = n0; n < N; n += stride) {
-        const float* rz = U + zrp[n] * PK + 3;
-        const float4 wz = *reinterpret_cast<const float4*>(zwp + 4 * n);
+        const float* rz = U + zoff[n];
+        const float4 wz = zw[n];
         const float lc = lnchi[n];
         float2 vv[NB];
 #pragma unroll
         for (int i = 0; i < NB; ++i) { const float x = V[i * Np + n]; vv[i] = make_float2(x, x); }
-        const float u0 = (fminf(fmaxf(lne0 - lc, lkmin), lkmax) - lkmin) * inv_dk;
-        const float u1 = (fminf(fmaxf(lne1 - lc, lkmin), lkmax) - lkmin) * inv_dk;
+        // ln k clamped to the table (u to [0, n_k - 1])
+        float2 u = __ffma2_rn(make_float2(lc, lc), minv, ua);
+        u.x = fminf(fmaxf(u.x, 0.f), umax);
+        u.y = fminf(fmaxf(u.y, 0.f), umax);
         // cell index without conversion instructions: g = u + (2^23 - 1/2),
         // correctly rounded, is 2^23 + round(u - 1/2), an integer held in the
         // low mantissa bits (u >= 0, so g >= 2^23).  round(u - 1/2) = floor(u)
         // except at exact integers, where the cell below with t = 1 gives the
         // same interpolant.  The clamp to cell n_k - 2 is taken on g (exact).
-        const float g0 = fminf(__fadd_rn(u0, 8388607.5f), gmax);
-        const float g1 = fminf(__fadd_rn(u1, 8388607.5f), gmax);
-        const int ik0 = __float_as_int(g0) - 0x4B000000;
-        const int ik1 = __float_as_int(g1) - 0x4B000000;
-        const float2 t = make_float2(u0 - __fadd_rn(g0, -8388608.f), u1 - __fadd_rn(g1, -8388608.f));
+        float2 g = __fadd2_rn(u, half);
+        g.x = fminf(g.x, gmax);
+        g.y = fminf(g.y, gmax);
+        const int ik0 = __float_as_int(g.x) - 0x4B000000;
+        const int ik1 = __float_as_int(g.y) - 0x4B000000;
+        // t = u - (g - 2^23); 2^23 - g is exact (Sterbenz) and so is the sum
+        const float2 t = __fadd2_rn(u, __ffma2_rn(g, m1, p23));
         const float2 t2 = __fmul2_rn(t, t);
         // doubled Catmull-Rom weights (the z-taps are doubled too)
         const float2 k0 = __fmul2_rn(t, __ffma2_rn(t, __ffma2_rn(t, m1, two), m1));
@@ -395,7 +415,9 @@ __device__ __forceinline__ void limber_pair_f32(const float* __restrict__ U, int
             const float2 w = make_float2(wzr[r], wzr[r]);
             v = (r == 0) ? __fmul2_rn(w, sr) : __ffma2_rn(w, sr, v);
         }
-        const float2 P = make_float2(M::p10(0.25f * v.x), M::p10(0.25f * v.y));
+        // the z-weights carry the factor log2(10) / 4 (doubled k- and z-weights):
+        // P = 10^(log10 P) = 2^v
+        const float2 P = make_float2(M::e2(v.x), M::e2(v.y));
         float2 tv[NB];
 #pragma unroll
         for (int i = 0; i < NB; ++i) tv[i] = __fmul2_rn(vv[i], P);
@@ -409,7 +431,7 @@ __device__ __forceinline__ void limber_pair_f32(const float* __restrict__ U, int
     for (int p = 0; p < NP; ++p) { acc[p] = a2[p].x; acc[NP + p] = a2[p].y; }
 }
 
-template <typename T, int NB, bool FAST>
+template <typename T, int NB, bool FAST, int PKC>
 __global__ void __launch_bounds__(32 * kLimberWarps, sizeof(T) == 8 ? 1 : 2)
 k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* __restrict__ table,
          const T* __restrict__ win, T* __restrict__ resid, double* __restrict__ model_out,
@@ -423,11 +445,14 @@ k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* _
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;
     const int N = sp.N, n_k = sp.n_k, n_z = sp.n_z, n_ell = sp.n_ell;
-    const int PK = limber_pitch(n_k);
+    const int PK = PKC ? PKC : limber_pitch(n_k);
     const int Np = win_pitch(N);
     T* U = reinterpret_cast<T*>(smem_raw);          // padded table
     T* W = U + (n_z + 2) * PK;                      // ln chi, V_1..V_NB (pitch Np)
-    T* thr = W + (NB + 1) * Np;                     // the row's parameters in T (n_params)
+    // FP32: the nodes' z-weights (float4) and first-tap offsets, staged once per CTA
+    float4* ZW = reinterpret_cast<float4*>(W + (NB + 1) * Np);
+    int* ZO = reinterpret_cast<int*>(ZW + (sizeof(T) == 4 ? N : 0));
+    T* thr = reinterpret_cast<T*>(ZO + (sizeof(T) == 4 ? N : 0));   // the row's parameters in T (n_params)
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     const int n_lp = (n_ell + 1) / 2;               // multipole pairs, one warp each
@@ -437,6 +462,18 @@ k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* _
     const uint32_t win_bytes = (uint32_t)((NB + 1) * Np * sizeof(T));
     const bool bulk = (row_bytes % 16) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0 &&
                       (reinterpret_cast<uintptr_t>(wsrc) & 15) == 0;
+    auto stage_nodes = [&]() {
+        if constexpr (sizeof(T) == 4) {
+            const float4* zsrc = reinterpret_cast<const float4*>(sp.zw4f);
+            // z-weights scaled by log2(10) / 4 so the lookup yields log2 P directly
+            constexpr float c = 0.25f * 3.32192809488736234787f;
+            for (int n = tid; n < N; n += nt) {
+                const float4 q = zsrc[n];
+                ZW[n] = make_float4(c * q.x, c * q.y, c * q.z, c * q.w);
+                ZO[n] = sp.zrp[n] * PK + 3;
+            }
+        }
+    };
     // every output of the row is NaN when a bounded wait gives up
     auto fail_row = [&]() {
         if (tid == 0 && err) atomicOr(err, NS_BIT_TIMEOUT);
@@ -462,6 +499,7 @@ k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* _
                 bulk_g2s(smem_u32(U + (r + 1) * PK + 4), src + (size_t)r * n_k, row_bytes, bar);
         }
         for (int i = tid; i < sp.n_params; i += nt) thr[i] = (T)theta_full[(size_t)row * sp.n_params + i];
+        stage_nodes();
         // warp 0 polls the barrier while the others sleep at the CTA barrier;
         // afterwards every thread observes the completed phase (acquire).
         int fail = 0;
@@ -479,6 +517,7 @@ k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* _
             for (int k = lane; k < n_k; k += 32) U[(r + 1) * PK + 4 + k] = src[(size_t)r * n_k + k];
         for (int i = tid; i < (NB + 1) * Np; i += nt) W[i] = wsrc[i];
         for (int i = tid; i < sp.n_params; i += nt) thr[i] = (T)theta_full[(size_t)row * sp.n_params + i];
+        stage_nodes();
         __syncthreads();
     }
     for (int k = 4 + tid; k < 4 + n_k; k += nt) {
@@ -508,7 +547,7 @@ k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* _
 #pragma unroll
         for (int q = 0; q < 32; ++q) acc[q] = T(0);
         if constexpr (sizeof(T) == 4) {
-            limber_pair_f32<NB, FAST>(U, PK, N, n_k, zrp, reinterpret_cast<const float*>(zwp),
+            limber_pair_f32<NB, FAST, PKC>(U, PK, N, n_k, ZO, ZW,
                                       reinterpret_cast<const float*>(lnchi), reinterpret_cast<const float*>(V), Np,
                                       (float)lne0, (float)lne1, (float)lkmin, (float)lkmax, (float)inv_dk, 1 + lane,
                                       32, reinterpret_cast<float*>(acc));
@@ -800,8 +839,9 @@ static size_t windows_smem(const ShearParams& sp) {
 constexpr size_t kLimberSmemMax = 227 * 1024 - 64;
 template <typename T>
 static size_t limber_smem(const ShearParams& sp) {
+    const size_t nodes = sizeof(T) == 4 ? (size_t)sp.N * (sizeof(float4) + sizeof(int)) : 0;
     return ((size_t)(sp.n_z + 2) * limber_pitch(sp.n_k) + (size_t)(sp.nb + 1) * win_pitch(sp.N) + sp.n_params) *
-           sizeof(T);
+           sizeof(T) + nodes;
 }
 
 bool projection_fits(const ShearParams& sp, int elt) {
@@ -825,23 +865,38 @@ static int windows_nb(const ShearParams& sp, const double* theta_full, T* win, c
     return NS_OK;
 }
 
-template <typename T, int NB, bool FAST>
-static int limber_nb(const ShearParams& sp, const double* theta_full, const T* table, const T* win, T* resid,
-                     double* model_out, const int* nrows, int grid_rows, int* err, cudaStream_t st) {
+template <typename T, int NB, bool FAST, int PKC>
+static int limber_launch(const ShearParams& sp, const double* theta_full, const T* table, const T* win, T* resid,
+                         double* model_out, const int* nrows, int grid_rows, int* err, cudaStream_t st) {
     const size_t smem = limber_smem<T>(sp);
     if (smem > kLimberSmemMax) return NS_ENOTSUP;
     static bool attr_done = false;
     if (!attr_done) {
         cudaFuncAttributes fa;
-        NS_CUDA_TRY(cudaFuncGetAttributes(&fa, k_limber<T, NB, FAST>));
-        NS_CUDA_TRY(cudaFuncSetAttribute(k_limber<T, NB, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        NS_CUDA_TRY(cudaFuncGetAttributes(&fa, k_limber<T, NB, FAST, PKC>));
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_limber<T, NB, FAST, PKC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(227 * 1024 - fa.sharedSizeBytes)));
         attr_done = true;
     }
     const int warps = std::min(kLimberWarps, (sp.n_ell + 1) / 2);
-    NS_CUDA_TRY(launch_pdl(k_limber<T, NB, FAST>, dim3(grid_rows), dim3(32 * warps), smem, st, sp, theta_full, table,
-                           win, resid, model_out, nrows, err));
+    NS_CUDA_TRY(launch_pdl(k_limber<T, NB, FAST, PKC>, dim3(grid_rows), dim3(32 * warps), smem, st, sp, theta_full,
+                           table, win, resid, model_out, nrows, err));
     return NS_OK;
+}
+
+// The 39-d table (200 k nodes, padded row pitch 212) gets a compile-time pitch.
+constexpr int kPitch39 = 212;
+static_assert(kPitch39 % 4 == 0, "padded rows stay 16-byte aligned");
+
+template <typename T, int NB, bool FAST>
+static int limber_nb(const ShearParams& sp, const double* theta_full, const T* table, const T* win, T* resid,
+                     double* model_out, const int* nrows, int grid_rows, int* err, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4 && NB == 5) {
+        if (limber_pitch(sp.n_k) == kPitch39)
+            return limber_launch<T, NB, FAST, kPitch39>(sp, theta_full, table, win, resid, model_out, nrows,
+                                                        grid_rows, err, st);
+    }
+    return limber_launch<T, NB, FAST, 0>(sp, theta_full, table, win, resid, model_out, nrows, grid_rows, err, st);
 }
 
 template <typename T, bool FAST>

@@ -21,12 +21,12 @@ def oracle_for(name):
     return inp, ShearOracle(inp)
 
 
-def cuda_problem(name, precision, max_batch=64, own_mock=False):
+def cuda_problem(name, precision, max_batch=64, own_mock=False, hidden_tile=0):
     from paper_2509_13307_gb300 import Problem
     inp, orc = oracle_for(name)
     if own_mock:
-        return Problem(inp, precision, max_batch=max_batch)
-    return Problem(inp, precision, max_batch=max_batch, data=orc.data, cov=orc.cov)
+        return Problem(inp, precision, max_batch=max_batch, hidden_tile=hidden_tile)
+    return Problem(inp, precision, max_batch=max_batch, data=orc.data, cov=orc.cov, hidden_tile=hidden_tile)
 
 
 def random_cube(n, d, seed, lo=0.02, hi=0.98):

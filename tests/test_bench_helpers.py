@@ -21,6 +21,11 @@ def test_limber_flops_written_out():
     assert bench.limber_flops_per_eval(w.shear39()) == 20 * 1024 * 77 + 300 * 39
 
 
+def test_limber_method_flops_written_out():
+    # the method's count: 20 ell x 1025 nodes x (16 lookup taps + 15 bin pairs) FMA, 2 FLOP each
+    assert bench.limber_method_flops_per_eval(w.shear39()) == 2 * 20 * 1025 * (16 + 15) == 1271000
+
+
 def test_windows_flops_written_out():
     # 1024 intervals x 48 + 1025 nodes x 12 + 1025 x 5 bins x 25
     assert bench.windows_flops_per_eval(w.shear39()) == 1024 * 48 + 1025 * 12 + 1025 * 5 * 25

@@ -53,8 +53,26 @@ def test_adjoint_fp64_central_differences_of_gpu_loglike():
         assert abs(fd - g[i]) <= 1e-5 * max(abs(g[i]), 1.0), (i, fd, g[i])
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16", 2e-3)])
+def _grad_bf16_weights(orc, th):
+    """Complex-step gradient of the oracle whose emulator weights (layers >= 1)
+    are rounded to bf16, activations exact: the model the split-bf16 adjoint
+    differentiates."""
+    save = orc.emulator
+    orc.emulator = lambda t, _s=save: _s(t, bf16_weights=True)
+    try:
+        return orc.grad_complex_step(th)
+    finally:
+        orc.emulator = save
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16", 1e-4)])
 def test_adjoint_low_precision_error_is_bounded(prec, tol):
+    """FP32: against the FP64 oracle's complex-step gradient.  BF16: the
+    emulator weights are bf16 (the BF16 model), the activations and gradients
+    FP32-accurate split-bf16 pairs, so the gradient is checked against the
+    complex-step gradient of the oracle with bf16 weights, to the FP32
+    tolerance; its distance from the FP64 model's gradient (the bf16 weights'
+    effect) is printed."""
     inp, orc = oracle_for("shear39")
     p = cuda_problem("shear39", prec, max_batch=16)
     fid = np.asarray(inp["fiducial"])
@@ -62,8 +80,11 @@ def test_adjoint_low_precision_error_is_bounded(prec, tol):
     _, g = p.loglike_grad(_t(th))
     g = g.cpu().numpy()
     for b in range(len(th)):
-        ref = orc.grad_complex_step(th[b])
+        ref = orc.grad_complex_step(th[b]) if prec == "fp32" else _grad_bf16_weights(orc, th[b])
         err = np.max(np.abs(g[b] - ref)) / np.max(np.abs(ref))
+        if prec == "bf16":
+            r64 = orc.grad_complex_step(th[b])
+            print(f"bf16 gradient vs the FP64 model's: {np.max(np.abs(g[b] - r64)) / np.max(np.abs(r64)):.3e}")
         print(f"{prec} gradient max error / max |grad| = {err:.3e}")
         assert err < tol
 
@@ -84,8 +105,9 @@ def test_adjoint_bf16_batch_on_tensor_cores():
     """BF16 problems take the emulator forward and backward on the tensor
     cores (split-bf16 activations and gradients, exact bf16 weights).  At 300
     rows (three 128-row tiles and a ragged tail), random prior points: the
-    gradient of three sampled rows against the FP64 oracle's complex-step
-    gradient within the BF16 bound of the test above, every row finite."""
+    gradient of three sampled rows against the complex-step gradient of the
+    oracle with bf16 emulator weights, to the FP32 tolerance of the test above,
+    every row finite."""
     inp, orc = oracle_for("shear39")
     p = cuda_problem("shear39", "bf16", max_batch=300)
     th = free_theta(inp, random_cube(300, p.d, 24, 0.1, 0.9))
@@ -93,7 +115,7 @@ def test_adjoint_bf16_batch_on_tensor_cores():
     logL, g = logL.cpu().numpy(), g.cpu().numpy()
     assert np.all(np.isfinite(logL)) and np.all(np.isfinite(g))
     for b in (0, 129, 299):
-        ref = orc.grad_complex_step(th[b])
+        ref = _grad_bf16_weights(orc, th[b])
         err = np.max(np.abs(g[b] - ref)) / np.max(np.abs(ref))
         print(f"bf16 tensor-core adjoint row {b}: max error / max |grad| = {err:.3e}")
-        assert err < 2e-3
+        assert err < 1e-4

@@ -26,8 +26,7 @@ def _t(a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-def _problem_with_fixed(name, fixed, precision="fp64", max_batch=64):
-    from paper_2509_13307_gb300 import Problem
+def _inputs_with_fixed(name, fixed):
     inp, orc = oracle_for(name)
     names = inp["param_names"]
     pri = list(inp["priors"])
@@ -35,7 +34,12 @@ def _problem_with_fixed(name, fixed, precision="fp64", max_batch=64):
     for nm in fixed:
         i = names.index(nm)
         pri[i] = ("F", float(fid[i]), 0.0)
-    inp2 = dict(inp, priors=pri)
+    return dict(inp, priors=pri), orc
+
+
+def _problem_with_fixed(name, fixed, precision="fp64", max_batch=64):
+    from paper_2509_13307_gb300 import Problem
+    inp2, orc = _inputs_with_fixed(name, fixed)
     return Problem(inp2, precision, max_batch=max_batch, data=orc.data, cov=orc.cov)
 
 
@@ -61,6 +65,42 @@ def test_packed_runs_reproduce_single_runs():
             assert sts[i].logZ == s1.logZ and sts[i].evaluations == s1.evaluations
     for i, run in enumerate(singles):
         assert multi.evidence(i, 32) == run.evidence(32)
+    multi.close()
+
+
+def test_packed_runs_match_the_oracle():
+    """Packed runs against the oracle itself: a d = 19 run (w0, wa fixed) and a
+    d = 21 run share every likelihood batch; each reproduces, exactly, the
+    oracle's nested sampler on the same Philox streams (deleted slots, start
+    slots, evaluations per chain; L*, log Z to FP64 round-off)."""
+    from oracle.ns import NestedSampler
+    from oracle.shear import ShearOracle
+    from paper_2509_13307_gb300 import MultiRun
+    fixed_sets = [["w0", "wa"], []]
+    samplers = [w.SamplerConfig(n_live=36, n_delete=9, repeats=4, seed=41),
+                w.SamplerConfig(n_live=28, n_delete=7, repeats=3, seed=42)]
+    probs, onss = [], []
+    for f, sc in zip(fixed_sets, samplers):
+        inp2, orc = _inputs_with_fixed("shear_tiny", f)
+        probs.append(_problem_with_fixed("shear_tiny", f))
+        o2 = ShearOracle(inp2, data=orc.data, cov=orc.cov)
+        ons = NestedSampler.from_config(o2.loglike_cube, probs[-1].d, sc)
+        ons.initialise()
+        onss.append(ons)
+    assert [p.d for p in probs] == [19, 21]
+    multi = MultiRun(probs, samplers)
+    for it in range(3):
+        sts = multi.step(1)
+        for i, ons in enumerate(onss):
+            ons.iterate()
+            rec = ons.records[-1]
+            lstar, dele, starts, evals = multi.last_iteration(i)
+            assert lstar == pytest.approx(rec.lstar, rel=1e-12, abs=1e-12)
+            assert np.array_equal(dele, rec.deleted)
+            assert np.array_equal(starts, rec.starts)
+            assert np.array_equal(evals, rec.evals)
+            assert sts[i].logZ == pytest.approx(ons.acc.logZ, rel=1e-12, abs=1e-12)
+            assert sts[i].evaluations == ons.n_evals
     multi.close()
 
 

@@ -61,3 +61,37 @@ def test_nuts_on_shear_adjoint(precision):
     assert np.all(np.isfinite(out["logp"]))
     assert out["stats"]["gradient_evals"] > 8 * 30
     assert np.all(np.isfinite(out["theta"]))
+
+
+def test_nuts_posterior_agrees_with_nested_sampling():
+    """The two samplers of the paper's comparison (nested sampling and NUTS on
+    the hand-written adjoint, Sec. 3.2) sample the same posterior of the small
+    shear problem (FP64): posterior means agree within 5 combined standard
+    errors (NUTS: spread of the chain means; NS: sd / sqrt(Kish ESS of the
+    importance weights)) and standard deviations within 35 %."""
+    from paper_2509_13307_gb300 import NestedRun, nuts
+    prob = cuda_problem("shear_tiny", "fp64", max_batch=400)
+    run = NestedRun(prob, 400, 100, seed=21)
+    st = run.run()
+    assert st.converged
+    x, lg, logw = run.posterior()
+    run.close()
+    th = np.concatenate([prob.prior_transform(torch.tensor(x[i:i + 400], device="cuda")).cpu().numpy()
+                         for i in range(0, len(x), 400)])
+    wgt = np.exp(logw)
+    m_ns = wgt @ th
+    s_ns = np.sqrt(wgt @ (th - m_ns) ** 2)
+    ess = 1.0 / np.sum(wgt ** 2)
+    n_ch = 16
+    pick = np.random.default_rng(3).choice(len(wgt), size=n_ch, p=wgt)
+    xc = np.clip(x[pick], 1e-9, 1 - 1e-9)
+    out = nuts(prob, n_ch, 200, 250, z0=np.log(xc) - np.log1p(-xc), seed=13, init_step=0.05, max_depth=8)
+    t = out["theta"]
+    m_h = t.reshape(-1, t.shape[-1]).mean(axis=0)
+    s_h = t.reshape(-1, t.shape[-1]).std(axis=0)
+    se_h = t.mean(axis=1).std(axis=0, ddof=1) / np.sqrt(n_ch)
+    z = (m_h - m_ns) / np.sqrt(se_h ** 2 + (s_ns / np.sqrt(ess)) ** 2)
+    print(f"ESS(NS) {ess:.0f}, max |z| {np.max(np.abs(z)):.2f}, sd ratio {np.min(s_h / s_ns):.2f} .. "
+          f"{np.max(s_h / s_ns):.2f}, accept {out['stats']['mean_accept']:.2f}, depth {out['stats']['mean_depth']:.1f}")
+    assert np.all(np.abs(z) < 5.0), z
+    assert np.all(np.abs(s_h / s_ns - 1.0) < 0.35), s_h / s_ns

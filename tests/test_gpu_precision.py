@@ -12,8 +12,12 @@ FP32 log L: a model vector with relative error eps_m shifts chi^2 by
 2 y . L^-1 dm, so |d log L| <= eps_m sum_a |y_a| (|L^-1| |m|)_a with
 y = L^-1 (d - m).  The FP32 stages give eps_m ~ 1e-6 (1024-term FP32
 contractions in the emulator, 16-tap lookups, 1024-node Limber sums); the test
-uses eps_m = 2e-6 (measured errors reach 0.2 of that bound).  BF16 log L against the bf16-aware oracle obeys the same
-bound (its FP32 stages are the same)."""
+uses eps_m = 2e-6 (measured errors reach 0.2 of that bound).  BF16 log L is
+checked against the oracle fed the GPU's own BF16 emulator table (the
+emulator itself is checked against the bf16-aware oracle above): the stages
+after the emulator are FP32 and obey the same bound.  (The bf16 rounding flips
+of the emulator move log L far from the fiducial by more than this bound, so
+the two stages are checked separately.)"""
 
 import numpy as np
 import pytest
@@ -69,14 +73,15 @@ def test_loglike_reduced_precision_bound(name, prec):
     far = free_theta(inp, random_cube(3, p.d, 42))
     th = np.vstack([near, far])
     got = p.loglike(_t(th)).cpu().numpy()
+    tab = p.emulator(_t(th)).cpu().numpy() if prec == "bf16" else None
     for b in range(len(th)):
         full = _full(inp, th[b])
         if prec == "bf16":
-            # the oracle with the bf16-rounded emulator: the remaining error is the FP32 stages'
-            class _O:  # noqa: N801
-                pass
+            # the oracle's projection and chi^2 of the GPU's own emulator table
+            # (checked against the bf16-aware oracle emulator above): the
+            # remaining error is the FP32 stages'
             save = orc.emulator
-            orc.emulator = lambda t, _s=save: _s(t, bf16=True)
+            orc.emulator = lambda t, _tab=tab[b]: _tab.reshape(orc.n_z_emu, orc.n_k)
             try:
                 ref = orc.loglike_full(full)
                 bound = _fp32_bound(orc, full)

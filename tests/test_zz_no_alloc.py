@@ -1,8 +1,8 @@
 """ns_evidence_noalloc: the evidence of a caller-held dead-point sequence with
-no device allocation (for callers that record work into a CUDA graph under a
-strict capture mode, or that own all device memory through their own pool).
-It must reproduce ns_evidence on the same run, on two calls in a row (the
-second call reuses the library's static scratch array)."""
+no device allocation (for callers whose framework reserves the device memory
+for its own pool, or whose loop must not call cudaMalloc / cudaFree).  It must
+reproduce ns_evidence on the same run, on two calls in a row (the second call
+reuses the library's static scratch array)."""
 
 import ctypes as C
 
@@ -42,6 +42,12 @@ def test_noalloc_evidence_matches_ns_evidence():
         assert logZ == pytest.approx(ref["logZ"], rel=1e-11, abs=1e-11)
         assert err == pytest.approx(ref["logZ_err"], rel=1e-8)
         assert logX == pytest.approx(ref["logX"], rel=1e-12)
+    # a live count below 1 gives NaN outputs rather than a silent number
+    bad = dn.clone()
+    bad[5] = 0
+    rc = lib.ns_evidence_noalloc(C.c_void_p(dL.data_ptr()), C.c_void_p(bad.data_ptr()), len(seq_L),
+                                 cfg.sampler.seed, n_rep, C.c_void_p(out.data_ptr()), stream)
+    assert rc == 0 and np.all(np.isnan(out.cpu().numpy()))
     # sizes beyond the static array are rejected
     assert lib.ns_evidence_noalloc(C.c_void_p(dL.data_ptr()), C.c_void_p(dn.data_ptr()), len(seq_L),
                                    cfg.sampler.seed, 4097, C.c_void_p(out.data_ptr()), stream) == -1

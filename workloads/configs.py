@@ -91,6 +91,8 @@ class ShearConfig:
     c1rho: float = 5e-14 * 2.775e11   # C_1 rho_cr (dimensionless, h cancels)
     emu_out_sigma: float = 0.05   # emulator output scale in dex about the mean table
     emu_bias_sd: float = 0.1
+    emu_smooth_out: bool = False  # output layer a smooth function of (ln k, z) (Chebyshev bases), so
+                                  # the coarse-z emulator is the full one evaluated at fewer z nodes
     coarse_z: Optional[int] = None    # if set: emulator on this many z nodes, interpolated to n_z
     z_interp: str = "catmull_rom"     # coarse -> fine z: "catmull_rom" or "linear" (the paper's)
     seed_emulator: int = 0
@@ -192,7 +194,7 @@ def shear39(**sampler_kw) -> ShearConfig:
         nz_sigma=(0.15,) * 5, n_ell=20, n_k=200, n_z=50, z_max=5.02,
         n_chi=1025, a_min=1.0 / 6.02, emu_hidden=(1024,) * 4,
         emu_inputs=(0, 1, 2, 3, 4, 7, 8), n_tmpl=18, fixed={}, cov_kind="knox",
-        sampler=SamplerConfig(**kw))
+        emu_smooth_out=True, sampler=SamplerConfig(**kw))
 
 
 def shear37_lcdm(**sampler_kw) -> ShearConfig:

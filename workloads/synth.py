@@ -45,13 +45,50 @@ def _mlp_weights(rng: np.random.Generator, dims, bias_sd: float):
     return Ws, bs
 
 
+def _chebyshev(s: np.ndarray, n: int) -> np.ndarray:
+    """T_0 .. T_{n-1} at s in [-1, 1], shape (len(s), n)."""
+    return np.cos(np.arange(n)[None, :] * np.arccos(np.clip(s, -1.0, 1.0))[:, None])
+
+
+def _smooth_output_layer(rng: np.random.Generator, n_k: int, z_nodes: np.ndarray, z_max: float, fan_in: int,
+                         bias_sd: float, n_zb: int = 4, n_kb: int = 16):
+    """Output layer whose rows vary smoothly over the (ln k, z) table:
+    W[(jz, ik), :] = sum_{m < n_zb, q < n_kb} c_mq T_m(s_z) T_q(s_k) V[m, q, :],
+    s_z = 2 z / z_max - 1, s_k = 2 ik / (n_k - 1) - 1, V ~ N(0, 1/fan_in),
+    c_mq = 2^-m / (1 + q / 4), rescaled so the rows have variance 1/fan_in on
+    average; the bias likewise with scalar coefficients.  A real P(k, z) is
+    smooth in both variables (slow, growth-like variation in z); with this
+    layer the emulator on a coarser z grid is the same function evaluated at
+    fewer z nodes (the draws V do not depend on the z grid)."""
+    V = rng.standard_normal((n_zb, n_kb, fan_in)) / np.sqrt(fan_in)
+    vb = rng.standard_normal((n_zb, n_kb)) * bias_sd
+    c = (0.5 ** np.arange(n_zb))[:, None] / (1.0 + np.arange(n_kb)[None, :] / 4.0)
+    Tz = _chebyshev(2.0 * np.asarray(z_nodes) / z_max - 1.0, n_zb)
+    Tk = _chebyshev(2.0 * np.arange(n_k) / (n_k - 1) - 1.0, n_kb)
+    # normalisation over the fine reference grid (independent of z_nodes)
+    zr = np.linspace(0.0, z_max, 50)
+    Tzr = _chebyshev(2.0 * zr / z_max - 1.0, n_zb)
+    norm = np.sqrt(np.mean((Tzr ** 2) @ (c ** 2) @ (Tk ** 2).T))
+    coef = np.einsum("zm,kq,mq->zkmq", Tz, Tk, c / norm)          # (nz, nk, n_zb, n_kb)
+    W = np.einsum("zkmq,mqf->zkf", coef, V).reshape(len(z_nodes) * n_k, fan_in)
+    b = np.einsum("zkmq,mq->zk", coef, vb).reshape(-1)
+    return W, b
+
+
 def make_shear_inputs(cfg: ShearConfig) -> dict:
     """All inputs of a shear problem.  Emulator output ordering is z-major:
     output o = jz * n_k + ik, i.e. log10 P at (k_ik, z_jz)."""
     priors = cfg.priors()
     dims = cfg.emu_dims
     rng_e = np.random.default_rng(cfg.seed_emulator)
-    Ws, bs = _mlp_weights(rng_e, dims, cfg.emu_bias_sd)
+    if cfg.emu_smooth_out:
+        Ws, bs = _mlp_weights(rng_e, dims[:-1], cfg.emu_bias_sd)
+        Wo, bo = _smooth_output_layer(rng_e, cfg.n_k, np.linspace(0.0, cfg.z_max, cfg.n_z_emu), cfg.z_max,
+                                      dims[-2], cfg.emu_bias_sd)
+        Ws.append(Wo)
+        bs.append(bo)
+    else:
+        Ws, bs = _mlp_weights(rng_e, dims, cfg.emu_bias_sd)
 
     # Emulator input standardisation over the prior box of each input parameter.
     centers, scales = [], []
