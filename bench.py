@@ -153,14 +153,14 @@ def limber_flops_per_eval(cfg) -> float:
     return cfg.n_ell * (N - 1) * (32 + 10 + nb + 2 * npairs) + D * (3 + 2 * cfg.n_tmpl)
 
 
-# DRAM traffic of k_limber per evaluation from one ncu capture (25,032,448 bytes
-# read and 0 written at 384 evaluations per launch, cold L2, the summary in
-# profiles/k_limber_bf16_shear39_B384.md).  It equals the kernel's algorithmic
+# DRAM traffic of k_limber per evaluation from one ncu capture (29,974,784 bytes
+# read and 0 written at 460 evaluations per launch, cold L2, the summary in
+# profiles/k_limber_bf16_shear39_B460.md).  It equals the kernel's algorithmic
 # input bytes, so it scales with the rows of a launch; it is reported only while
 # the kernel's sources are the ones the capture was taken on.
-LIMBER_TRAFFIC_BYTES_PER_EVAL = 25032448 / 384
+LIMBER_TRAFFIC_BYTES_PER_EVAL = 29974784 / 460
 LIMBER_TRAFFIC_SOURCES = ("paper_2509_13307_gb300/csrc/projection.cu", "paper_2509_13307_gb300/csrc/async_copy.cuh")
-LIMBER_TRAFFIC_SHA256 = "ed49b15fbd51b1355a40582e4de978d03d441cca696e7d4bb4fbf0c8ff566fb1"
+LIMBER_TRAFFIC_SHA256 = "38accea52c7bb14d1db0ea25467640ef25c17d17303df9930f85470adcee44aa"
 
 
 def limber_traffic(avg_rows: float):
@@ -735,7 +735,7 @@ def ours(args):
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": limber_traffic(prof["rows"] / prof["launches"]),
                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                                    "scaled from 384 evaluations)",
+                                    "scaled from 460 evaluations)",
                     "kernel": "k_limber<float,5,fast> (A10-A12: P lookup, Limber sums, data vector)",
                     "flop_per_eval": flops,
                     "flop_basis": "A10 + A11L method count 2 n_ell N_chi (16 + n_pairs); the kernel's full "
