@@ -257,6 +257,9 @@ def main():
     ap.add_argument("--seeds", default="3,4,5")
     ap.add_argument("--precisions", default="bf16,fp32")
     ap.add_argument("--oracle-limit", type=float, default=900.0, help="seconds allowed per full oracle run")
+    ap.add_argument("--oracle-parts", default="rates,runs,gpu",
+                    help="--study oracle: any of rates (oracle evaluation rates), runs (full oracle runs), gpu (the "
+                         "GPU runs and the extrapolations; run alone, nothing else on the GPU)")
     args = ap.parse_args()
     if args.profile:
         return profile_workload(args)
@@ -565,8 +568,9 @@ def oracle_study(args):
     hours to days, the time to a converged log Z is extrapolated as the GPU
     run's evaluation count / the oracle's rate, and labelled as such."""
     nproc = os.cpu_count() or 1
+    parts = set(args.oracle_parts.split(","))
     out = {"host": _host_info(), "rates": {}, "runs": {}, "extrapolated": {}}
-    secs = {"shear5": 15.0, "cmb6": 20.0, "shear39": 15.0}
+    secs = {"shear5": 15.0, "cmb6": 20.0, "shear39": 15.0} if "rates" in parts else {}
     for kind, sec in secs.items():
         for th in sorted({1, nproc}):
             r = _oracle_subprocess(_ORACLE_RATE % dict(root=ROOT, kind=kind, seconds=sec), th, 1800)
@@ -574,12 +578,15 @@ def oracle_study(args):
                 r = {"evals_per_s": r["n"] / r["s"], "evals": r["n"], "seconds": r["s"]}
             out["rates"][f"{kind}_threads{th}"] = r
             print(json.dumps({kind: r, "threads": th}), file=sys.stderr, flush=True)
-    for kind in ("gauss5", "shear5"):
+    for kind in (("gauss5", "shear5") if "runs" in parts else ()):
         r = _oracle_subprocess(_ORACLE_RUN % dict(root=ROOT, kind=kind, limit=args.oracle_limit), 1,
                                args.oracle_limit + 600)
         r["threads"] = 1
         out["runs"][kind] = r
         print(json.dumps({kind: r}), file=sys.stderr, flush=True)
+    if "gpu" not in parts:
+        print(json.dumps(out), flush=True)
+        return 0
     # GPU runs for the evaluation counts of the extrapolations (and the GPU's own times)
     import torch
     from paper_2509_13307_gb300.build import build

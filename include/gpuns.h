@@ -167,9 +167,12 @@ typedef struct {
     ns_gauss_desc gauss;
     int max_batch;                /* largest batch B any call will pass (>= 1) */
     ns_cmb_desc cmb;
-    int hidden_tile;              /* BF16: N-tile width of every tensor-core hidden layer, one of
-                                     16, 32, 64, 128 (at most the layer's width); 0 = chosen by the
-                                     tile autotuner at creation.  Results do not depend on it. */
+    int hidden_tile;              /* BF16: 0 = the input and hidden layers as one clustered kernel
+                                     when the emulator allows it (tanh, every hidden width 512 or
+                                     1024, at most 4 hidden layers, at most 32 inputs, shear kind),
+                                     else per-layer GEMMs with autotuned N-tiles; 16, 32, 64 or 128
+                                     (at most the layer's width) = per-layer GEMMs with that N-tile
+                                     (results do not depend on the width). */
 } ns_problem_desc;
 
 typedef struct ns_problem ns_problem;
@@ -271,9 +274,10 @@ int ns_emulator_batch(const ns_problem* p, const double* theta_dev, int B,
                       double* out_dev, void* stream);
 
 /* BF16 problems: the N-tile width of every tensor-core layer (0 for layers on
- * CUDA cores) and, for the hidden layers, the time per launch [ms] the tile
- * autotuner measured at creation on min(max_batch, 512) rows; ms may be NULL.
- * n >= the number of emulator layers. */
+ * CUDA cores; 128 for the layers of the fused stack, whose CTAs own 128
+ * features of a 64-row tile) and, for autotuned hidden layers, the time per
+ * launch [ms] the tile autotuner measured at creation on min(max_batch, 384)
+ * rows (0 otherwise); ms may be NULL.  n >= the number of emulator layers. */
 int ns_problem_tiles(const ns_problem* p, int* tile_n, float* ms, int n);
 
 /* Device status bits of the problem's batch calls (NS_BIT_TIMEOUT: a bounded

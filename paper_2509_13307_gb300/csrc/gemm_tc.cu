@@ -85,6 +85,11 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // 32 consecutive FP32 columns of one TMEM lane per thread.
@@ -631,6 +636,315 @@ static int launch_bn(const CUtensorMap* tmA, const CUtensorMap* tmB, const float
     return launch_bn_kps<BN, 1>(tmA, tmB, bias, mu, sigma, Cout, nrows, grid_rows, N, K, epi, beta, err, st);
 }
 
+
+// ------------------------------------------------------------------ fused emulator stack
+// The input layer and every hidden layer of a BF16 emulator whose hidden
+// widths all equal H = 128 CS (CS <= 8), in one kernel.  A thread-block
+// cluster of CS CTAs takes a tile of FR = 64 rows; CTA q owns features
+// [128 q, 128 q + 128) of every layer.  The tile's activations (FR x H bf16)
+// stay in each CTA's shared memory as the MMA's B operand (K-major, 128-byte
+// swizzle, k-block after k-block); the CTA's weight slice (128 x H) streams
+// through a two-slot TMA ring (two k-blocks per copy) and
+// tcgen05.mma.cta_group::1 (M = 128 features, N = FR rows) accumulates
+// D^T = W_q A^T in TMEM.  The epilogue (tanh, bf16) writes the CTA's output
+// slice (FR x 128) to a staging tile in the same swizzled layout, and one
+// thread pushes it into every CTA's activation buffer with
+// cp.async.bulk.shared::cluster, completing on the receiver's A_ready barrier;
+// the last layer's slice goes to global memory by a TMA store instead.  A
+// slice may be pushed only when every CTA of the cluster has finished the
+// layer (its MMAs read the buffer being overwritten): each CTA arrives on
+// every peer's `ready` barrier (release, cluster scope) after its epilogue,
+// and the pusher waits on its own (acquire).  The input layer (K0 <= 32
+// inputs, FP32 on CUDA cores, the arithmetic of k_emu_input) fills the first
+// staging tile.  Warps 0-3: input layer and epilogues (thread = feature = TMEM
+// lane); warp 4 lane 0: weight producer (all layers, ahead of the MMAs);
+// warp 5: TMEM owner and MMA issuer.  Every wait is bounded; after a timeout
+// the CTA records NS_BIT_TIMEOUT, skips its MMAs and keeps the protocol's
+// arrivals, and all threads of the cluster meet at a final cluster barrier
+// before TMEM is freed and the CTAs exit.
+constexpr int FR = 64;                   // rows per cluster tile
+constexpr int F_SLICE = 128;             // features per CTA
+constexpr int F_SLOT = 2 * F_SLICE * BK * 2;   // ring slot: two k-blocks of the weight slice (32 KB)
+constexpr int F_STAGING = FR * F_SLICE * 2;    // the CTA's output slice (16 KB)
+constexpr int F_KIN = 32;                // largest input count of the fused input layer
+constexpr int F_THREADS = 192;
+
+struct FusedMaps {
+    CUtensorMap w[kFusedMaxHidden + 1];  // [l] for hidden layers l = 1 .. n_h: box 128 rows x (2 x 64) k
+    CUtensorMap out;                     // the last layer's activations: box FR rows x (2 x 64) k
+};
+struct FusedArgs {
+    const double* theta;                 // rows x P
+    int P, K0, n_h;
+    const int* inputs;
+    const double* center;
+    const double* inv_scale;
+    const float* W0;                     // H x K0
+    const float* b0;
+    const float* bh[kFusedMaxHidden + 1];// hidden biases, [l] for l = 1 .. n_h
+    const int* nrows;
+    int* err;
+};
+
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" :: "r"(cluster_bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+// bounded wait with cluster-scope acquire (peers' arrivals)
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_wait_cluster(bar, parity)) return true;
+        if ((i & 255u) == 0) {
+            __nanosleep(64);
+            if (globaltimer() - t0 > kWaitNs) return false;
+        }
+    }
+}
+// shared::cta -> shared::cluster bulk copy (a peer's buffer), completing on the peer's barrier
+__device__ __forceinline__ void bulk_s2cluster(uint32_t dst_cluster, uint32_t src, uint32_t bytes,
+                                               uint32_t bar_cluster) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(dst_cluster), "r"(src), "r"(bytes), "r"(bar_cluster) : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, uint32_t src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];"
+                 :: "l"(reinterpret_cast<uint64_t>(tm)), "r"(src), "r"(x), "r"(y), "r"(z) : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void named_sync_epi() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// byte offset of element (row r, k) of a k-block tile of FR rows x 64 k, 128-byte swizzle
+__device__ __forceinline__ uint32_t swz_off(int r, int k) {
+    return (uint32_t)(r * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + ((k & 7) << 1));
+}
+
+template <int CS>
+__global__ void __launch_bounds__(F_THREADS, 1)
+k_emu_fused(const __grid_constant__ FusedMaps maps, const FusedArgs args) {
+    constexpr int H = F_SLICE * CS;
+    constexpr int A_BYTES = FR * H * 2;              // the tile's activations, H / 64 k-blocks of FR x 64
+    constexpr int NKB2 = H / (2 * BK);               // ring slots per layer
+    pdl_begin();
+    const int M = *args.nrows;
+    const int r0 = blockIdx.y * FR;
+    if (r0 >= M) return;                             // the whole cluster (same row tile) leaves together
+    const uint32_t q = cluster_ctarank();
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - raw);
+    const uint32_t sA = base;                        // A_BYTES
+    const uint32_t sRing = base + A_BYTES;           // 2 x F_SLOT
+    const uint32_t sS = sRing + 2 * F_SLOT;          // F_STAGING
+    uint8_t* gS = gbase + (A_BYTES + 2 * F_SLOT);
+    const uint32_t bar0 = sS + F_STAGING;
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 16u + 8u * s; };
+    const uint32_t accf = bar0 + 32u, a_ready = bar0 + 40u, ready = bar0 + 48u;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + (A_BYTES + 2 * F_SLOT + F_STAGING) + 64);
+    __shared__ float xin[FR][F_KIN];
+    __shared__ int s_fail;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        s_fail = 0;
+        for (int s = 0; s < 2; ++s) { mbar_init(full_bar(s), 1); mbar_init(empty_bar(s), 1); }
+        mbar_init(accf, 1);
+        mbar_init(a_ready, 1);
+        mbar_init(ready, CS);                        // one arrival from every CTA of the cluster per layer
+        mbar_init_fence();
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tmem_slot)), "r"(64) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    // every CTA's barriers are initialised before any peer arrives on them
+    cluster_sync_all();
+    const uint32_t tmem = *tmem_slot;
+    const int n_h = args.n_h;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // weight producer: slots of two k-blocks of the CTA's 128-feature slice, all layers in order
+            int g = 0;
+            for (int l = 1; l <= n_h; ++l)
+                for (int kb2 = 0; kb2 < NKB2; ++kb2, ++g) {
+                    const int s = g & 1;
+                    if (g >= 2 && !mbar_wait(empty_bar(s), ((g >> 1) & 1) ^ 1)) { s_fail = 1; break; }
+                    mbar_expect_tx(full_bar(s), F_SLOT);
+                    tma_load_3d(sRing + s * F_SLOT, &maps.w[l], full_bar(s), 0, (int)q * F_SLICE, 2 * kb2);
+                }
+        }
+        __syncwarp();
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // MMA issuer: layer l waits for its activations (phase l - 1), then the ring
+            constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(FR >> 3) << 17) |
+                                       ((uint32_t)(F_SLICE >> 4) << 24);
+            int g = 0;
+            bool ok = true;
+            for (int l = 1; l <= n_h; ++l) {
+                ok = ok && mbar_wait(a_ready, (l - 1) & 1);
+                fence_after();
+                for (int kb2 = 0; kb2 < NKB2; ++kb2, ++g) {
+                    const int s = g & 1;
+                    ok = ok && mbar_wait(full_bar(s), (g >> 1) & 1);
+                    fence_after();
+                    if (ok) {
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const uint64_t dw = smem_desc(sRing + s * F_SLOT + j * (F_SLICE * BK * 2));
+                            const uint64_t da = smem_desc(sA + (2 * kb2 + j) * (FR * BK * 2));
+#pragma unroll
+                            for (int kk = 0; kk < BK / 16; ++kk)
+                                mma_bf16(tmem, dw + 2 * kk, da + 2 * kk, idesc, (kb2 | j | kk) != 0);
+                        }
+                    }
+                    mma_commit(empty_bar(s));        // frees the slot (or releases it unused after a failure)
+                }
+                mma_commit(accf);
+            }
+            if (!ok) s_fail = 1;
+        }
+        __syncwarp();
+    } else {
+        // warps 0-3: thread e owns feature 128 q + e (TMEM lane e)
+        const int e = tid;
+        auto write_slice = [&](int r, float v) {
+            *reinterpret_cast<__nv_bfloat16*>(gS + (e >> 6) * (FR * BK * 2) + swz_off(r, e & 63)) =
+                __float2bfloat16_rn(v);
+        };
+        // hand the staged slice of layer l to every CTA (or, after the last layer, to global memory)
+        auto boundary = [&](int l) {
+            fence_proxy_async_smem();
+            fence_before();
+            named_sync_epi();
+            if (tid == 0) {
+                if (l < n_h) mbar_expect_tx(a_ready, A_BYTES);   // the next layer's activations
+                for (uint32_t p = 0; p < (uint32_t)CS; ++p) mbar_arrive_remote(mapa_u32(ready, p));
+                if (!mbar_wait_cluster(ready, l & 1)) s_fail = 1;
+                if (l < n_h) {
+                    for (uint32_t p = 0; p < (uint32_t)CS; ++p)
+                        bulk_s2cluster(mapa_u32(sA + q * (2 * FR * BK * 2), p), sS, F_STAGING, mapa_u32(a_ready, p));
+                    bulk_commit();
+                    bulk_wait_read0();
+                } else {
+                    tma_store_3d(&maps.out, sS, 0, r0, 2 * (int)q);
+                    bulk_commit();
+                    bulk_wait0();
+                }
+            }
+            named_sync_epi();
+        };
+        // input layer: x = (theta[inputs] - center) * inv_scale (FP64, then FP32), h = tanh(W0 x + b0)
+        const int K0 = args.K0;
+        for (int i = tid; i < FR * K0; i += 128) {
+            const int r = i / K0, j = i - r * K0;
+            float xv = 0.f;
+            if (r0 + r < M) {
+                const double v = args.theta[(size_t)(r0 + r) * args.P + args.inputs[j]] - args.center[j];
+                xv = (float)(v * args.inv_scale[j]);
+            }
+            xin[r][j] = xv;
+        }
+        named_sync_epi();
+        {
+            const int n = (int)q * F_SLICE + e;
+            float w[F_KIN];
+#pragma unroll
+            for (int j = 0; j < F_KIN; ++j) w[j] = j < K0 ? args.W0[(size_t)n * K0 + j] : 0.f;
+            const float bn = args.b0[n];
+            for (int r = 0; r < FR; ++r) {
+                float acc = bn;
+#pragma unroll
+                for (int j = 0; j < F_KIN; ++j)
+                    if (j < K0) acc = fmaf(w[j], xin[r][j], acc);
+                write_slice(r, tanhf(acc));
+            }
+        }
+        boundary(0);
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int l = 1; l <= n_h; ++l) {
+            const bool ok = mbar_wait(accf, (l - 1) & 1);
+            fence_after();
+            if (!ok) s_fail = 1;
+            const float b = args.bh[l][(int)q * F_SLICE + e];
+#pragma unroll 1
+            for (int c = 0; c < FR / 32; ++c) {
+                float v[32];
+                tmem_ld32(lane_addr + c * 32, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) write_slice(c * 32 + j, tanh_fast(v[j] + b));
+            }
+            boundary(l);
+        }
+    }
+    // every thread of the cluster meets here: no CTA leaves while a peer may
+    // still push into its shared memory or arrive on its barriers
+    fence_before();
+    __syncwarp();
+    cluster_sync_all();
+    if (s_fail && tid == 0 && args.err) atomicOr(args.err, NS_BIT_TIMEOUT);
+    if (warp == 5) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(64) : "memory");
+    }
+}
+
+template <int CS>
+static int launch_fused_cs(const FusedMaps& maps, const FusedArgs& args, int grid_rows, cudaStream_t st) {
+    constexpr int H = F_SLICE * CS;
+    constexpr size_t SMEM = (size_t)FR * H * 2 + 2 * F_SLOT + F_STAGING + 1024 /*align*/ + 256 /*barriers*/;
+    static bool attr = false;
+    if (!attr) {
+        NS_CUDA_TRY(cudaFuncSetAttribute(k_emu_fused<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
+        attr = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CS, (grid_rows + FR - 1) / FR);
+    cfg.blockDim = dim3(F_THREADS);
+    cfg.dynamicSmemBytes = SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr2[2];
+    attr2[0].id = cudaLaunchAttributeClusterDimension;
+    attr2[0].val.clusterDim.x = CS;
+    attr2[0].val.clusterDim.y = 1;
+    attr2[0].val.clusterDim.z = 1;
+    attr2[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr2[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr2;
+    cfg.numAttrs = 2;
+    NS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_emu_fused<CS>, maps, args));
+    return NS_OK;
+}
+
 }  // namespace tc
 
 int launch_gemm_tc(const CUtensorMap* tmA, const CUtensorMap* tmB, int tile_n, const float* bias,
@@ -662,6 +976,33 @@ int launch_gemm_tc_out_swap(const CUtensorMap* tmW, const CUtensorMap* tmX, cons
     NS_CUDA_TRY(launch_pdl(tc::k_gemm_tc_swap<BR>, grid, dim3(128), (size_t)CS::SMEM, st, *tmW, *tmX, bias, out_mu,
                            out_sigma, C, d_nrows, N, K, d_err));
     return NS_OK;
+}
+
+int launch_emu_fused(const ns_problem* p, const Workspace* ws, int grid_rows, cudaStream_t st) {
+    if (grid_rows <= 0) return NS_OK;
+    const int n_h = p->n_layers - 2;
+    if (p->fused_cs < 1 || n_h < 1 || n_h > kFusedMaxHidden) return NS_EINVAL;
+    tc::FusedMaps maps;
+    for (int l = 1; l <= n_h; ++l) maps.w[l] = p->tmF[l];
+    maps.out = ws->tmF_out;
+    tc::FusedArgs a{};
+    a.theta = ws->theta_full;
+    a.P = p->P;
+    a.K0 = p->dims[0];
+    a.n_h = n_h;
+    a.inputs = p->d_inputs;
+    a.center = p->d_in_center;
+    a.inv_scale = p->d_in_inv_scale;
+    a.W0 = (const float*)p->d_W[0];
+    a.b0 = (const float*)p->d_b[0];
+    for (int l = 1; l <= n_h; ++l) a.bh[l] = (const float*)p->d_b[l];
+    a.nrows = ws->d_nrows;
+    a.err = ws->d_err;
+    switch (p->fused_cs) {
+        case 4: return tc::launch_fused_cs<4>(maps, a, grid_rows, st);
+        case 8: return tc::launch_fused_cs<8>(maps, a, grid_rows, st);
+        default: return NS_ENOTSUP;
+    }
 }
 
 int launch_gemm_split(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo, const CUtensorMap* tmB, int tile_n,

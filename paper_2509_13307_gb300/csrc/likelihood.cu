@@ -364,9 +364,19 @@ static int probe_end(const StageProbe* pr, int stage, cudaStream_t st) {
 static int run_emulator_bf16(const ns_problem* p, Workspace* ws, int grid_rows, cudaStream_t st,
                              const StageProbe* probe, const Head* hd) {
     const int L = p->n_layers;
-    NS_TRY((launch_emu_input<float, __nv_bfloat16>(p, ws, grid_rows, (__nv_bfloat16*)ws->act[0], true, st)));
-    int cur = 0;
-    for (int l = 1; l < L; ++l) {
+    int cur = 0, l1 = 1;
+    if (p->fused_cs) {
+        // input and hidden layers in one clustered kernel; its output is the
+        // buffer the per-layer path would leave the last hidden layer in
+        NS_TRY(probe_begin(probe, PROBE_EMU_HIDDEN, ws, st));
+        NS_TRY(launch_emu_fused(p, ws, grid_rows, st));
+        NS_TRY(probe_end(probe, PROBE_EMU_HIDDEN, st));
+        cur = (L - 2) & 1;
+        l1 = L - 1;
+    } else {
+        NS_TRY((launch_emu_input<float, __nv_bfloat16>(p, ws, grid_rows, (__nv_bfloat16*)ws->act[0], true, st)));
+    }
+    for (int l = l1; l < L; ++l) {
         const int K = p->dims[l], N = p->dims[l + 1];
         const bool last = (l == L - 1);
         const int stage = last ? PROBE_EMU_OUT : (l == 1 ? PROBE_EMU_HIDDEN : PROBE_NONE);

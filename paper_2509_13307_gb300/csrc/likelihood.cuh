@@ -59,6 +59,7 @@ struct Workspace {
     // tcgen05 tensor maps (BF16 precision): A operand of layer l >= 1 and its output
     std::vector<CUtensorMap> tmA;
     CUtensorMap tmX_out{};        // the last layer's activations in kSwapRows-row boxes
+    CUtensorMap tmF_out{};        // fused emulator stack: its output activations in 64-row boxes of two k-blocks
     std::vector<void*> owned;
     // second stream for the emulator-independent windows stage; fork/join events
     cudaStream_t side = nullptr;
@@ -84,6 +85,9 @@ struct ns_problem {
     std::vector<CUtensorMap> tmB;    // BF16: weight tensor maps for layers >= 1
     std::vector<int> tile_n;         // BF16: N tile per layer (hidden layers autotuned at creation)
     std::vector<float> tile_ms;      // BF16: measured time per launch of the chosen hidden tiles
+    int fused_cs = 0;                // BF16: > 0 when the input and hidden layers run as one clustered kernel
+                                     // (cluster of fused_cs CTAs, hidden width 128 fused_cs)
+    std::vector<CUtensorMap> tmF;    // its weight maps: boxes of 128 rows x two k-blocks
     int* d_inputs = nullptr;
     double* d_in_center = nullptr;
     double* d_in_scale = nullptr;
@@ -213,6 +217,12 @@ int launch_gemm_split(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo, const 
 // as its N, kSwapRows per CTA): tmW boxes 128 rows of W, tmX boxes kSwapRows
 // activation rows; FP32 out = mu + sigma (acc + b), row-major rows x N.
 constexpr int kSwapRows = 256;
+// Fused emulator stack (gemm_tc.cu): the input layer and every hidden layer of
+// a BF16 tanh emulator whose hidden widths all equal 128 p->fused_cs, one
+// thread-block cluster per 64-row tile; writes the last hidden layer's
+// activations through ws->tmF_out.
+constexpr int kFusedMaxHidden = 4;
+int launch_emu_fused(const ns_problem* p, const Workspace* ws, int grid_rows, cudaStream_t st);
 int launch_gemm_tc_out_swap(const CUtensorMap* tmW, const CUtensorMap* tmX, const float* bias, const float* out_mu,
                             float out_sigma, float* C, const int* d_nrows, int grid_rows, int N, int K, int* d_err,
                             cudaStream_t st);

@@ -165,6 +165,8 @@ int workspace_create(const ns_problem* p, int cap, Workspace* ws) {
                                         gemm_tc_kps(p->dims[l])));
             if (l == p->n_layers - 1)
                 NS_TRY(make_tensor_map_bf16(&ws->tmX_out, ws->act[cur], rows_pad, p->dims[l], kSwapRows));
+            if (p->fused_cs && l == p->n_layers - 2)
+                NS_TRY(make_tensor_map_bf16(&ws->tmF_out, ws->act[cur ^ 1], rows_pad, p->dims[l + 1], 64, 2));
             cur ^= 1;
         }
     }
@@ -624,7 +626,23 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
             if (s) return fail(s);
         }
         int s = NS_OK;
-        if (desc->hidden_tile > 0) {
+        // the fused input + hidden stack: tanh shear emulators whose hidden
+        // widths all equal 128 CS (CS = 4 or 8), at most kFusedMaxHidden hidden
+        // layers, at most 32 inputs, no forced per-layer tile
+        const int n_h = e.n_layers - 2;
+        bool fuse = !cmb && desc->hidden_tile == 0 && e.activation == NS_ACT_TANH && n_h >= 1 &&
+                    n_h <= kFusedMaxHidden && p->dims[0] <= 32 && p->dims[1] % 128 == 0 &&
+                    (p->dims[1] == 512 || p->dims[1] == 1024);
+        for (int l = 1; fuse && l <= n_h; ++l) fuse = p->dims[l] == p->dims[1] && p->dims[l + 1] == p->dims[1];
+        if (fuse) {
+            p->fused_cs = p->dims[1] / 128;
+            p->tmF.resize(e.n_layers);
+            p->tile_ms.assign(e.n_layers, 0.0f);
+            for (int l = 1; l <= n_h && !s; ++l) {
+                p->tile_n[l] = 128;
+                s = make_tensor_map_bf16(&p->tmF[l], p->d_W[l], p->dims[l + 1], p->dims[l], 128, 2);
+            }
+        } else if (desc->hidden_tile > 0) {
             // a caller-chosen N-tile for every tensor-core hidden layer (no autotuning)
             p->tile_ms.assign(e.n_layers, 0.0f);
             for (int l = 1; l <= e.n_layers - 2 && !s; ++l) {

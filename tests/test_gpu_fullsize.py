@@ -111,12 +111,40 @@ def test_hidden_tile_widths_are_bit_identical(B):
         assert np.array_equal(o[2], outs[0][2])
 
 
-def test_autotuned_problem_matches_forced_widths():
-    inp, _ = oracle_for("shear39")
-    th, emu, logL, _, _ = _outputs("shear39", 500, 32)
-    p = cuda_problem("shear39", "bf16", max_batch=500)
-    assert np.array_equal(p.loglike(_t(th)).cpu().numpy(), logL)
-    p.close()
+@pytest.mark.parametrize("B", [1, 65, 500, 1000])
+def test_fused_emulator_stack(B):
+    """The default BF16 39-d problem runs the input layer and the three hidden
+    layers as one clustered kernel (8 CTAs per 64-row tile, activations kept in
+    shared memory, features as the MMA's M).  Against the per-layer path (forced
+    16-wide tiles, rows as the MMA's M) and the bf16-aware oracle: both paths
+    accumulate each product in the same k order, so they differ only where the
+    tensor core's internal sums round differently and flip a bf16 activation
+    (measured and printed); every row stays within the emulator tolerance of
+    the oracle, including the ragged last tile, and log L follows."""
+    name = "shear39"
+    inp, orc = oracle_for(name)
+    pf = cuda_problem(name, "bf16", max_batch=max(B, 64))
+    tiles, _ = pf.tiles()
+    th = free_theta(inp, random_cube(B, pf.d, 91 + B))
+    thd = _t(th)
+    ef = pf.emulator(thd).cpu().numpy()
+    lf = pf.loglike(thd).cpu().numpy()
+    assert pf.device_status() == 0
+    pl = cuda_problem(name, "bf16", max_batch=max(B, 64), hidden_tile=16)
+    el = pl.emulator(thd).cpu().numpy()
+    ll = pl.loglike(thd).cpu().numpy()
+    same = np.mean(ef == el)
+    print(f"B={B}: fused vs per-layer emulator: {same:.4f} of values identical, max |d| {np.max(np.abs(ef - el)):.2e}")
+    assert np.max(np.abs(ef - el)) < 4e-4
+    assert np.all(np.isfinite(lf))
+    rows = sorted({0, B // 2, B - 1, min(B - 1, 63), min(B - 1, 64)})
+    for b in rows:
+        full = _full(inp, th[b])
+        assert np.max(np.abs(ef[b] - orc.emulator(full, bf16=True).reshape(-1))) < 2e-4, b
+        ref, bound = _ref_and_bound(name, full, ef[b])
+        assert abs(lf[b] - ref) <= bound, (b, abs(lf[b] - ref), bound)
+    pf.close()
+    pl.close()
 
 
 def test_invalid_hidden_tile_is_rejected():
