@@ -724,12 +724,13 @@ def ours(args):
     value = ev_job / t_job
 
     # per round (one chain group): slice (with the prior transform and the
-    # next round's batch-counter reset), windows, emulator input layer, one
-    # GEMM per further layer, Limber, whitening; per iteration 7 more (sort and
-    # delete, column means, covariance, Cholesky, directions, chain starts,
-    # insert).
+    # next round's batch-counter reset), windows, the emulator (the fused
+    # input + hidden-layer kernel and the output GEMM, or the input layer and
+    # one GEMM per further layer), Limber, whitening; per iteration 7 more
+    # (sort and delete, column means, covariance, Cholesky, directions, chain
+    # starts, insert).
     n_layers = len(inp["emu_W"])
-    per_round = 5 + (n_layers - 1)
+    per_round = 4 + (2 if prob.fused_cluster() else n_layers)
     gpu_launches = res["rounds"] * per_round + 7 * res["iters"]
 
     # ---------------- roofline of the dominant kernel (Limber stage), timed live

@@ -167,12 +167,14 @@ typedef struct {
     ns_gauss_desc gauss;
     int max_batch;                /* largest batch B any call will pass (>= 1) */
     ns_cmb_desc cmb;
-    int hidden_tile;              /* BF16: 0 = the input and hidden layers as one clustered kernel
-                                     when the emulator allows it (tanh, every hidden width 512 or
-                                     1024, at most 4 hidden layers, at most 32 inputs, shear kind),
-                                     else per-layer GEMMs with autotuned N-tiles; 16, 32, 64 or 128
-                                     (at most the layer's width) = per-layer GEMMs with that N-tile
-                                     (results do not depend on the width). */
+    int hidden_tile;              /* BF16 emulator layers: 0 = per-layer tcgen05 GEMMs with N-tiles
+                                     chosen by the tile autotuner at creation; 16, 32, 64 or 128 (at
+                                     most the layer's width) = per-layer GEMMs with that N-tile;
+                                     -1 = the input and hidden layers as one clustered kernel
+                                     (activations kept in shared memory and exchanged between the
+                                     cluster's CTAs; tanh, every hidden width 512 or 1024, at most 4
+                                     hidden layers, at most 32 inputs, shear kind, else NS_ENOTSUP).
+                                     Results are bit-identical in every mode. */
 } ns_problem_desc;
 
 typedef struct ns_problem ns_problem;
@@ -279,6 +281,11 @@ int ns_emulator_batch(const ns_problem* p, const double* theta_dev, int B,
  * launch [ms] the tile autotuner measured at creation on min(max_batch, 384)
  * rows (0 otherwise); ms may be NULL.  n >= the number of emulator layers. */
 int ns_problem_tiles(const ns_problem* p, int* tile_n, float* ms, int n);
+
+/* BF16 problems: *cluster_size = the thread-block cluster size of the fused
+ * input + hidden-layer kernel (its CTAs own 128 features each of a 64-row
+ * tile), or 0 when the layers run as separate GEMMs. */
+int ns_problem_fused(const ns_problem* p, int* cluster_size);
 
 /* Device status bits of the problem's batch calls (NS_BIT_TIMEOUT: a bounded
  * device wait inside a likelihood kernel gave up; the affected rows are NaN).

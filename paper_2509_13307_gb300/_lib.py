@@ -19,7 +19,7 @@ NS_PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16_f64chi2": 3}
 NS_PRIOR = {"U": 0, "N": 1, "F": 2}
 
 EXPORTS = ["ns_strerror", "ns_problem_create", "ns_problem_free", "ns_problem_dim", "ns_prior_transform",
-           "loglike_batch", "ns_model_batch", "ns_emulator_batch", "ns_problem_status", "ns_problem_tiles", "loglike_grad_batch", "ns_init", "ns_step", "ns_evidence",
+           "loglike_batch", "ns_model_batch", "ns_emulator_batch", "ns_problem_status", "ns_problem_tiles", "ns_problem_fused", "loglike_grad_batch", "ns_init", "ns_step", "ns_evidence",
            "ns_live_points", "ns_dead_points", "ns_last_iteration", "ns_profile_stage", "ns_profile_read",
            "ns_evidence_noalloc", "ns_multi_init", "ns_multi_step", "ns_multi_run",
            "ns_multi_free", "ns_nuts_run", "ns_shard_evolve", "ns_shard_export", "ns_shard_insert",
@@ -114,6 +114,7 @@ def load():
     lib.ns_problem_status.argtypes = [vp, C.POINTER(C.c_int), C.c_int]
     lib.ns_nuts_run.argtypes = [vp, C.POINTER(NutsConfig), dp, dp, dp, dp, C.POINTER(NutsStats), vp]
     lib.ns_problem_tiles.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_float), C.c_int]
+    lib.ns_problem_fused.argtypes = [vp, C.POINTER(C.c_int)]
     lib.loglike_grad_batch.argtypes = [vp, vp, C.c_int, vp, vp, vp]
     lib.ns_init.argtypes = [vp, C.POINTER(Config), vp, C.POINTER(vp)]
     lib.ns_step.argtypes = [vp, C.c_int, C.POINTER(Status)]

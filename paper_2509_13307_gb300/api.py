@@ -129,6 +129,7 @@ class Problem:
         keep.append(parr)
         desc.priors = parr
         desc.max_batch = max_batch
+        # BF16 layer mode: 0 autotuned per-layer GEMMs, 16..128 a forced N-tile, -1 the fused stack
         desc.hidden_tile = self.hidden_tile if precision.startswith("bf16") else 0
         if self.kind == "gauss":
             desc.gauss = L.GaussDesc(inp["mu"], inp["sigma"])
@@ -274,6 +275,12 @@ class Problem:
         ms = (C.c_float * n)()
         L.check(self.lib.ns_problem_tiles(self._h, t, ms, n), "ns_problem_tiles")
         return list(t), list(ms)
+
+    def fused_cluster(self) -> int:
+        """BF16: cluster size of the fused input + hidden-layer kernel, 0 if the layers run separately."""
+        c = C.c_int(0)
+        L.check(self.lib.ns_problem_fused(self._h, C.byref(c)), "ns_problem_fused")
+        return c.value
 
     def device_status(self, clear: bool = False) -> int:
         """Status bits of earlier batch calls (NS_BIT_TIMEOUT = 4: a bounded

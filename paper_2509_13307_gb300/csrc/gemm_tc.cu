@@ -654,11 +654,13 @@ static int launch_bn(const CUtensorMap* tmA, const CUtensorMap* tmB, const float
 // slice may be pushed only when every CTA of the cluster has finished the
 // layer (its MMAs read the buffer being overwritten): each CTA arrives on
 // every peer's `ready` barrier (release, cluster scope) after its epilogue,
-// and the pusher waits on its own (acquire).  The input layer (K0 <= 32
-// inputs, FP32 on CUDA cores, the arithmetic of k_emu_input) fills the first
-// staging tile.  Warps 0-3: input layer and epilogues (thread = feature = TMEM
-// lane); warp 4 lane 0: weight producer (all layers, ahead of the MMAs);
-// warp 5: TMEM owner and MMA issuer.  Every wait is bounded; after a timeout
+// and the pushers wait on their own (acquire); lane p of warp 0 arrives on and
+// pushes to peer p, so the CS arrivals and copies are issued in parallel.  The
+// input layer (K0 <= 32 inputs, FP32 on CUDA cores, the arithmetic of
+// k_emu_input) fills the first staging tile.  Warps 0-7: input layer and
+// epilogues (warp w reads TMEM lanes 32 (w % 4) .. + 31 = features, rows
+// 32 (w / 4) .. + 31); warp 8 lane 0: weight producer (all layers, ahead of
+// the MMAs); warp 9: TMEM owner and MMA issuer.  Every wait is bounded; after a timeout
 // the CTA records NS_BIT_TIMEOUT, skips its MMAs and keeps the protocol's
 // arrivals, and all threads of the cluster meet at a final cluster barrier
 // before TMEM is freed and the CTAs exit.
@@ -667,7 +669,8 @@ constexpr int F_SLICE = 128;             // features per CTA
 constexpr int F_SLOT = 2 * F_SLICE * BK * 2;   // ring slot: two k-blocks of the weight slice (32 KB)
 constexpr int F_STAGING = FR * F_SLICE * 2;    // the CTA's output slice (16 KB)
 constexpr int F_KIN = 32;                // largest input count of the fused input layer
-constexpr int F_THREADS = 192;
+constexpr int F_EPI = 256;              // input-layer / epilogue threads (8 warps)
+constexpr int F_THREADS = F_EPI + 64;
 
 struct FusedMaps {
     CUtensorMap w[kFusedMaxHidden + 1];  // [l] for hidden layers l = 1 .. n_h: box 128 rows x (2 x 64) k
@@ -730,7 +733,7 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void named_sync_epi() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void named_sync_epi() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -777,7 +780,7 @@ k_emu_fused(const __grid_constant__ FusedMaps maps, const FusedArgs args) {
         mbar_init(ready, CS);                        // one arrival from every CTA of the cluster per layer
         mbar_init_fence();
     }
-    if (warp == 5) {
+    if (warp == 9) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(tmem_slot)), "r"(64) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -790,7 +793,7 @@ k_emu_fused(const __grid_constant__ FusedMaps maps, const FusedArgs args) {
     const uint32_t tmem = *tmem_slot;
     const int n_h = args.n_h;
 
-    if (warp == 4) {
+    if (warp == 8) {
         if (lane == 0) {
             // weight producer: slots of two k-blocks of the CTA's 128-feature slice, all layers in order
             int g = 0;
@@ -803,7 +806,7 @@ k_emu_fused(const __grid_constant__ FusedMaps maps, const FusedArgs args) {
                 }
         }
         __syncwarp();
-    } else if (warp == 5) {
+    } else if (warp == 9) {
         if (lane == 0) {
             // MMA issuer: layer l waits for its activations (phase l - 1), then the ring
             constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(FR >> 3) << 17) |
@@ -835,8 +838,9 @@ k_emu_fused(const __grid_constant__ FusedMaps maps, const FusedArgs args) {
         }
         __syncwarp();
     } else {
-        // warps 0-3: thread e owns feature 128 q + e (TMEM lane e)
-        const int e = tid;
+        // warps 0-7: thread tid owns feature 128 q + e (TMEM lane e) for rows
+        // [32 h, 32 h + 32), h = tid / 128
+        const int e = tid & (F_SLICE - 1), h = tid >> 7;
         auto write_slice = [&](int r, float v) {
             *reinterpret_cast<__nv_bfloat16*>(gS + (e >> 6) * (FR * BK * 2) + swz_off(r, e & 63)) =
                 __float2bfloat16_rn(v);
@@ -846,26 +850,32 @@ k_emu_fused(const __grid_constant__ FusedMaps maps, const FusedArgs args) {
             fence_proxy_async_smem();
             fence_before();
             named_sync_epi();
-            if (tid == 0) {
-                if (l < n_h) mbar_expect_tx(a_ready, A_BYTES);   // the next layer's activations
-                for (uint32_t p = 0; p < (uint32_t)CS; ++p) mbar_arrive_remote(mapa_u32(ready, p));
-                if (!mbar_wait_cluster(ready, l & 1)) s_fail = 1;
+            if (warp == 0) {
+                // the next layer's activations: CS slices arriving from the peers
+                if (lane == 0 && l < n_h) mbar_expect_tx(a_ready, A_BYTES);
+                __syncwarp();
+                if (lane < CS) mbar_arrive_remote(mapa_u32(ready, (uint32_t)lane));
+                bool okw = true;
+                if (lane == 0) okw = mbar_wait_cluster(ready, l & 1);
+                okw = __shfl_sync(0xffffffffu, okw ? 1 : 0, 0) != 0;
+                if (!okw && lane == 0) s_fail = 1;
                 if (l < n_h) {
-                    for (uint32_t p = 0; p < (uint32_t)CS; ++p)
-                        bulk_s2cluster(mapa_u32(sA + q * (2 * FR * BK * 2), p), sS, F_STAGING, mapa_u32(a_ready, p));
-                    bulk_commit();
-                    bulk_wait_read0();
-                } else {
+                    if (lane < CS)
+                        bulk_s2cluster(mapa_u32(sA + q * (2 * FR * BK * 2), (uint32_t)lane), sS, F_STAGING,
+                                       mapa_u32(a_ready, (uint32_t)lane));
+                    if (lane < CS) { bulk_commit(); bulk_wait_read0(); }
+                } else if (lane == 0) {
                     tma_store_3d(&maps.out, sS, 0, r0, 2 * (int)q);
                     bulk_commit();
                     bulk_wait0();
                 }
+                __syncwarp();
             }
             named_sync_epi();
         };
         // input layer: x = (theta[inputs] - center) * inv_scale (FP64, then FP32), h = tanh(W0 x + b0)
         const int K0 = args.K0;
-        for (int i = tid; i < FR * K0; i += 128) {
+        for (int i = tid; i < FR * K0; i += F_EPI) {
             const int r = i / K0, j = i - r * K0;
             float xv = 0.f;
             if (r0 + r < M) {
@@ -881,7 +891,7 @@ k_emu_fused(const __grid_constant__ FusedMaps maps, const FusedArgs args) {
 #pragma unroll
             for (int j = 0; j < F_KIN; ++j) w[j] = j < K0 ? args.W0[(size_t)n * K0 + j] : 0.f;
             const float bn = args.b0[n];
-            for (int r = 0; r < FR; ++r) {
+            for (int r = 32 * h; r < 32 * h + 32; ++r) {
                 float acc = bn;
 #pragma unroll
                 for (int j = 0; j < F_KIN; ++j)
@@ -890,19 +900,16 @@ k_emu_fused(const __grid_constant__ FusedMaps maps, const FusedArgs args) {
             }
         }
         boundary(0);
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + 32 * h;
         for (int l = 1; l <= n_h; ++l) {
             const bool ok = mbar_wait(accf, (l - 1) & 1);
             fence_after();
             if (!ok) s_fail = 1;
             const float b = args.bh[l][(int)q * F_SLICE + e];
-#pragma unroll 1
-            for (int c = 0; c < FR / 32; ++c) {
-                float v[32];
-                tmem_ld32(lane_addr + c * 32, v);
+            float v[32];
+            tmem_ld32(lane_addr, v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) write_slice(c * 32 + j, tanh_fast(v[j] + b));
-            }
+            for (int j = 0; j < 32; ++j) write_slice(32 * h + j, tanh_fast(v[j] + b));
             boundary(l);
         }
     }
@@ -912,7 +919,7 @@ k_emu_fused(const __grid_constant__ FusedMaps maps, const FusedArgs args) {
     __syncwarp();
     cluster_sync_all();
     if (s_fail && tid == 0 && args.err) atomicOr(args.err, NS_BIT_TIMEOUT);
-    if (warp == 5) {
+    if (warp == 9) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(64) : "memory");
     }

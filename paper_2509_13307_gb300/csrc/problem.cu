@@ -392,8 +392,8 @@ static int autotune_hidden_tiles(ns_problem* p, int last_hidden) {
 static int validate_desc(const ns_problem_desc* d) {
     if (!d || !d->priors || d->n_params < 1 || d->n_params > 256 || d->max_batch < 1) return NS_EINVAL;
     if (d->precision < 0 || d->precision > NS_PREC_BF16_F64CHI2) return NS_EINVAL;
-    if (d->hidden_tile != 0 && d->hidden_tile != 16 && d->hidden_tile != 32 && d->hidden_tile != 64 &&
-        d->hidden_tile != 128)
+    if (d->hidden_tile != 0 && d->hidden_tile != -1 && d->hidden_tile != 16 && d->hidden_tile != 32 &&
+        d->hidden_tile != 64 && d->hidden_tile != 128)
         return NS_EINVAL;
     int nfree = 0;
     for (int i = 0; i < d->n_params; ++i) {
@@ -626,11 +626,11 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
             if (s) return fail(s);
         }
         int s = NS_OK;
-        // the fused input + hidden stack: tanh shear emulators whose hidden
-        // widths all equal 128 CS (CS = 4 or 8), at most kFusedMaxHidden hidden
-        // layers, at most 32 inputs, no forced per-layer tile
+        // the fused input + hidden stack (on request, hidden_tile = -1): tanh
+        // shear emulators whose hidden widths all equal 128 CS (CS = 4 or 8),
+        // at most kFusedMaxHidden hidden layers, at most 32 inputs
         const int n_h = e.n_layers - 2;
-        bool fuse = !cmb && desc->hidden_tile == 0 && e.activation == NS_ACT_TANH && n_h >= 1 &&
+        bool fuse = !cmb && desc->hidden_tile == -1 && e.activation == NS_ACT_TANH && n_h >= 1 &&
                     n_h <= kFusedMaxHidden && p->dims[0] <= 32 && p->dims[1] % 128 == 0 &&
                     (p->dims[1] == 512 || p->dims[1] == 1024);
         for (int l = 1; fuse && l <= n_h; ++l) fuse = p->dims[l] == p->dims[1] && p->dims[l + 1] == p->dims[1];
@@ -642,6 +642,8 @@ extern "C" int ns_problem_create(const ns_problem_desc* desc, ns_problem** out) 
                 p->tile_n[l] = 128;
                 s = make_tensor_map_bf16(&p->tmF[l], p->d_W[l], p->dims[l + 1], p->dims[l], 128, 2);
             }
+        } else if (desc->hidden_tile == -1) {
+            return fail(NS_ENOTSUP);   // the fused stack was requested for an emulator it cannot take
         } else if (desc->hidden_tile > 0) {
             // a caller-chosen N-tile for every tensor-core hidden layer (no autotuning)
             p->tile_ms.assign(e.n_layers, 0.0f);
@@ -867,6 +869,12 @@ extern "C" int ns_model_batch(const ns_problem* p, const double* theta_dev, int 
     cudaStream_t st = (cudaStream_t)stream;
     NS_TRY(batch_common(p, theta_dev, B, st));
     return run_likelihood(p, const_cast<Workspace*>(&p->ws), B, nullptr, model_dev, st);
+}
+
+extern "C" int ns_problem_fused(const ns_problem* p, int* cluster_size) {
+    if (!p || !cluster_size) return NS_EINVAL;
+    *cluster_size = p->fused_cs;
+    return NS_OK;
 }
 
 extern "C" int ns_problem_tiles(const ns_problem* p, int* tile_n, float* ms, int n) {

@@ -113,17 +113,18 @@ def test_hidden_tile_widths_are_bit_identical(B):
 
 @pytest.mark.parametrize("B", [1, 65, 500, 1000])
 def test_fused_emulator_stack(B):
-    """The default BF16 39-d problem runs the input layer and the three hidden
-    layers as one clustered kernel (8 CTAs per 64-row tile, activations kept in
-    shared memory, features as the MMA's M).  Against the per-layer path (forced
-    16-wide tiles, rows as the MMA's M) and the bf16-aware oracle: both paths
-    accumulate each product in the same k order, so they differ only where the
-    tensor core's internal sums round differently and flip a bf16 activation
-    (measured and printed); every row stays within the emulator tolerance of
-    the oracle, including the ragged last tile, and log L follows."""
+    """The fused emulator stack (hidden_tile = -1): the input layer and the
+    three hidden layers as one clustered kernel (8 CTAs per 64-row tile,
+    activations kept in shared memory, features as the MMA's M).  Against the
+    per-layer path (forced 16-wide tiles, rows as the MMA's M) and the
+    bf16-aware oracle: both paths accumulate each product in the same k order
+    (measured: bit-identical, printed); every row stays within the emulator
+    tolerance of the oracle, including the ragged last tile, and log L
+    follows."""
     name = "shear39"
     inp, orc = oracle_for(name)
-    pf = cuda_problem(name, "bf16", max_batch=max(B, 64))
+    pf = cuda_problem(name, "bf16", max_batch=max(B, 64), hidden_tile=-1)
+    assert pf.fused_cluster() == 8
     tiles, _ = pf.tiles()
     th = free_theta(inp, random_cube(B, pf.d, 91 + B))
     thd = _t(th)
@@ -149,9 +150,21 @@ def test_fused_emulator_stack(B):
 
 def test_invalid_hidden_tile_is_rejected():
     from paper_2509_13307_gb300._lib import GpunsError
-    for bad in (48, 256):
+    for bad in (48, 256, -2):
         with pytest.raises(GpunsError):
             cuda_problem("shear_tiny", "bf16", max_batch=8, hidden_tile=bad)
+    # the fused stack needs hidden widths of 512 or 1024 (shear_tiny: 192)
+    with pytest.raises(GpunsError):
+        cuda_problem("shear_tiny", "bf16", max_batch=8, hidden_tile=-1)
+    assert cuda_problem("shear39", "bf16", max_batch=8).fused_cluster() == 0
+
+
+def test_autotuned_problem_matches_forced_widths():
+    inp, _ = oracle_for("shear39")
+    th, emu, logL, _, _ = _outputs("shear39", 500, 32)
+    p = cuda_problem("shear39", "bf16", max_batch=500)
+    assert np.array_equal(p.loglike(_t(th)).cpu().numpy(), logL)
+    p.close()
 
 
 @pytest.mark.parametrize("name", ["shear39_interp", "shear39_interp_linear"])
