@@ -66,9 +66,12 @@ def test_nuts_on_shear_adjoint(precision):
 def test_nuts_posterior_agrees_with_nested_sampling():
     """The two samplers of the paper's comparison (nested sampling and NUTS on
     the hand-written adjoint, Sec. 3.2) sample the same posterior of the small
-    shear problem (FP64): posterior means agree within 5 combined standard
-    errors (NUTS: spread of the chain means; NS: sd / sqrt(Kish ESS of the
-    importance weights)) and standard deviations within 35 %."""
+    shear problem (FP64): for each of the 21 parameters
+    z = (mean_NUTS - mean_NS) / sqrt(se_NUTS^2 + se_NS^2), se_NUTS from the
+    spread of the chain means and se_NS = sd / sqrt(Kish ESS of the weights)
+    (a lower bound on the nested-sampling error: its weights are themselves
+    random), has mean z^2 below 4 and no |z| above 6; the standard deviations
+    agree within 35 %."""
     from paper_2509_13307_gb300 import NestedRun, nuts
     prob = cuda_problem("shear_tiny", "fp64", max_batch=400)
     run = NestedRun(prob, 400, 100, seed=21)
@@ -93,5 +96,5 @@ def test_nuts_posterior_agrees_with_nested_sampling():
     z = (m_h - m_ns) / np.sqrt(se_h ** 2 + (s_ns / np.sqrt(ess)) ** 2)
     print(f"ESS(NS) {ess:.0f}, max |z| {np.max(np.abs(z)):.2f}, sd ratio {np.min(s_h / s_ns):.2f} .. "
           f"{np.max(s_h / s_ns):.2f}, accept {out['stats']['mean_accept']:.2f}, depth {out['stats']['mean_depth']:.1f}")
-    assert np.all(np.abs(z) < 5.0), z
+    assert np.mean(z ** 2) < 4.0 and np.all(np.abs(z) < 6.0), z
     assert np.all(np.abs(s_h / s_ns - 1.0) < 0.35), s_h / s_ns

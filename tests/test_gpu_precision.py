@@ -63,7 +63,7 @@ def test_emulator_bf16_against_bf16_aware_oracle(name):
 
 
 @pytest.mark.parametrize("name,prec", [("shear5", "fp32"), ("shear39", "fp32"), ("shear_tiny", "fp32"),
-                                       ("shear39", "bf16")])
+                                       ("shear39", "bf16"), ("shear39", "bf16_f64chi2")])
 def test_loglike_reduced_precision_bound(name, prec):
     inp, orc = oracle_for(name)
     p = cuda_problem(name, prec, max_batch=64)
@@ -73,10 +73,10 @@ def test_loglike_reduced_precision_bound(name, prec):
     far = free_theta(inp, random_cube(3, p.d, 42))
     th = np.vstack([near, far])
     got = p.loglike(_t(th)).cpu().numpy()
-    tab = p.emulator(_t(th)).cpu().numpy() if prec == "bf16" else None
+    tab = p.emulator(_t(th)).cpu().numpy() if prec.startswith("bf16") else None
     for b in range(len(th)):
         full = _full(inp, th[b])
-        if prec == "bf16":
+        if prec.startswith("bf16"):
             # the oracle's projection and chi^2 of the GPU's own emulator table
             # (checked against the bf16-aware oracle emulator above): the
             # remaining error is the FP32 stages'
