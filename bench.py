@@ -153,14 +153,14 @@ def limber_flops_per_eval(cfg) -> float:
     return cfg.n_ell * (N - 1) * (32 + 10 + nb + 2 * npairs) + D * (3 + 2 * cfg.n_tmpl)
 
 
-# DRAM traffic of k_limber per evaluation from one ncu capture (29,974,784 bytes
+# DRAM traffic of k_limber per evaluation from one ncu capture (29,979,904 bytes
 # read and 0 written at 460 evaluations per launch, cold L2, the summary in
 # profiles/k_limber_bf16_shear39_B460.md).  It equals the kernel's algorithmic
 # input bytes, so it scales with the rows of a launch; it is reported only while
 # the kernel's sources are the ones the capture was taken on.
-LIMBER_TRAFFIC_BYTES_PER_EVAL = 29974784 / 460
+LIMBER_TRAFFIC_BYTES_PER_EVAL = 29979904 / 460
 LIMBER_TRAFFIC_SOURCES = ("paper_2509_13307_gb300/csrc/projection.cu", "paper_2509_13307_gb300/csrc/async_copy.cuh")
-LIMBER_TRAFFIC_SHA256 = "38accea52c7bb14d1db0ea25467640ef25c17d17303df9930f85470adcee44aa"
+LIMBER_TRAFFIC_SHA256 = "12b8acc2a71cace1c0342f5e7675de02f7509aa708d5ff559bcaf382f740e6b0"
 
 
 def limber_traffic(avg_rows: float):

@@ -372,6 +372,8 @@ __device__ __forceinline__ void limber_pair_f32(const float* __restrict__ U, int
     float2 a2[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) a2[p] = make_float2(0.f, 0.f);
+    // two nodes per trip: independent lookups interleave (same per-lane order)
+#pragma unroll 2
     for (int n = n0; n < N; n += stride) {
         const float* rz = U + zoff[n];
         const float4 wz = zw[n];
