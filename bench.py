@@ -560,7 +560,7 @@ print(json.dumps({"seconds": dt, "converged": ns.converged(), "iterations": ns.i
 
 
 def oracle_study(args):
-    """The oracle as a baseline (FP64 NumPy on the host cores of the GPU machine):
+    """The oracle as a baseline (FP64 NumPy on the host cores of the machine that runs the bench):
     evaluation rates at 1 and all threads for the 5-d toy, the 6-d CMB problem
     and the 39-d shear problem; full nested-sampling runs of the 5-d Gaussian
     test problem and the 5-d shear toy (bounded by --oracle-limit seconds);

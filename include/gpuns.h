@@ -45,7 +45,7 @@ extern "C" {
 #define NS_ETIMEOUT    (-4)   /* a bounded device wait gave up (kernel watchdog) */
 #define NS_ESLICE      (-5)   /* a slice step cap was reached (also a status bit) */
 #define NS_ENONFINITE  (-6)   /* a likelihood evaluated to NaN/inf (also a status bit) */
-#define NS_ENOTSUP     (-7)   /* combination not supported by this build */
+#define NS_ENOTSUP     (-7)   /* combination not supported by the library */
 
 /* ---- status bits accumulated by a run (ns_status.status_bits) ---------- */
 #define NS_BIT_SLICE_CAP  1   /* stepping-out or shrinkage hit its cap */
