@@ -408,25 +408,57 @@ __global__ void __launch_bounds__(256) k_directions(RunDev r) {
     }
 }
 
+// Prior-transform constants (Table 1) of the full parameters lane and
+// lane + 32, read once per chain: they are problem constants, so a kernel may
+// read them before its dependency wait.  Parameters from 64 on are read when
+// a row is written.
+struct PriorRegs {
+    int f0, f1, kind0, kind1;
+    double a0, a1, b0, b1;
+};
+__device__ __forceinline__ PriorRegs load_prior_regs(const RunDev& r, int lane) {
+    PriorRegs q;
+    const int i0 = lane, i1 = lane + 32;
+    q.f0 = (i0 < r.P) ? r.fof[i0] : -1;
+    q.kind0 = (i0 < r.P) ? r.pkind[i0] : 0;
+    q.a0 = (i0 < r.P) ? r.pa[i0] : 0.0;
+    q.b0 = (i0 < r.P) ? r.pb[i0] : 0.0;
+    q.f1 = (i1 < r.P) ? r.fof[i1] : -1;
+    q.kind1 = (i1 < r.P) ? r.pkind[i1] : 0;
+    q.a1 = (i1 < r.P) ? r.pa[i1] : 0.0;
+    q.b1 = (i1 < r.P) ? r.pb[i1] : 0.0;
+    return q;
+}
+
 // Physical parameters of proposal row `row` (Table 1 prior transform), written
-// by the chain's warp: lanes own full parameters lane and lane + 32 and fetch
-// their cube coordinate from the lane holding it (y0: dims < 32, y1: dims >= 32).
-__device__ __forceinline__ void emit_theta(const RunDev& r, int row, double y0, double y1, int lane) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int i = lane + 32 * h;
-        const int f = (i < r.P) ? r.fof[i] : -1;
+// by the chain's warp: lane l writes the full parameters l, l + 32, ... and
+// fetches each one's cube coordinate from the lane holding it (y0: dims < 32,
+// y1: dims >= 32).
+__device__ __forceinline__ void emit_theta(const RunDev& r, const PriorRegs& q, int row, double y0, double y1,
+                                           int lane) {
+    for (int i0 = 0; i0 < r.P; i0 += 32) {          // the same trip count in every lane
+        const int i = i0 + lane;
+        int f, kind;
+        double a, b;
+        if (i0 == 0) { f = q.f0; kind = q.kind0; a = q.a0; b = q.b0; }
+        else if (i0 == 32) { f = q.f1; kind = q.kind1; a = q.a1; b = q.b1; }
+        else {
+            f = (i < r.P) ? r.fof[i] : -1;
+            kind = (i < r.P) ? r.pkind[i] : 0;
+            a = (i < r.P) ? r.pa[i] : 0.0;
+            b = (i < r.P) ? r.pb[i] : 0.0;
+        }
         const int src = (f >= 0) ? (f & 31) : 0;
         const double c0 = __shfl_sync(0xffffffffu, y0, src);
         const double c1 = __shfl_sync(0xffffffffu, y1, src);
         if (i < r.P) {
             double v;
             if (f < 0) {
-                v = r.pa[i];
+                v = a;
             } else {
                 const double c = (f < 32) ? c0 : c1;
-                if (r.pkind[i] == NS_PRIOR_UNIFORM) v = r.pa[i] + (r.pb[i] - r.pa[i]) * c;
-                else v = r.pa[i] + r.pb[i] * gauss_quantile(c, r.prior_f32 != 0);
+                if (kind == NS_PRIOR_UNIFORM) v = a + (b - a) * c;
+                else v = a + b * gauss_quantile(c, r.prior_f32 != 0);
             }
             r.theta_full[(size_t)row * r.P + i] = v;
         }
@@ -443,7 +475,7 @@ __device__ __forceinline__ void emit_theta(const RunDev& r, int row, double y0, 
 // sampler's exactly.  Phase word: phase | done_ends << 8 (bit 0 left, bit 1
 // right); ch_row / ch_row2 hold the pending left (or shrinkage) / right rows,
 // ch_step / ch_step2 the left (or shrinkage) / right step counts.
-__device__ void advance_chain(const RunDev& r, int c, int lane) {
+__device__ void advance_chain(const RunDev& r, const PriorRegs& q, int c, int lane) {
     const int pw = r.ch_phase[c];
     int phase = pw & 0xff, ends = (pw >> 8) & 3;
     if (phase == PH_DONE) return;
@@ -493,7 +525,7 @@ __device__ void advance_chain(const RunDev& r, int c, int lane) {
         int rw = 0;
         if (lane == 0) rw = atomicAdd(r.batch_ctr, 1);
         rw = __shfl_sync(0xffffffffu, rw, 0);
-        emit_theta(r, rw, has0 ? y0 : 0.0, has1 ? y1 : 0.0, lane);
+        emit_theta(r, q, rw, has0 ? y0 : 0.0, has1 ? y1 : 0.0, lane);
         ++evals;
         return rw;
     };
@@ -560,12 +592,13 @@ __device__ void advance_chain(const RunDev& r, int c, int lane) {
 // the FP64 units of every SM instead of a few.
 constexpr int kSliceWarps = 1;
 __global__ void __launch_bounds__(32 * kSliceWarps) k_slice_advance(RunDev r) {
+    const PriorRegs q = load_prior_regs(r, threadIdx.x & 31);   // problem constants
     pdl_begin();
     // the previous round (the last reader of the other counter) has completed
     if (blockIdx.x == 0 && threadIdx.x == 0 && r.batch_next) *r.batch_next = 0;
     const int c = blockIdx.x * kSliceWarps + (threadIdx.x >> 5);
     if (c >= r.grp_chains) return;
-    advance_chain(r, r.chain0 + c, threadIdx.x & 31);
+    advance_chain(r, q, r.chain0 + c, threadIdx.x & 31);
 }
 
 // All chains of several packed runs: global warp g -> (run, chain) through the
@@ -578,7 +611,7 @@ __global__ void __launch_bounds__(32 * kSliceWarps) k_slice_advance_multi(const 
     int r = 0;
     while (r + 1 < n_runs && chain_off[r + 1] <= g) ++r;
     const RunDev rd = runs[r];
-    advance_chain(rd, g - chain_off[r], threadIdx.x & 31);
+    advance_chain(rd, load_prior_regs(rd, threadIdx.x & 31), g - chain_off[r], threadIdx.x & 31);
 }
 
 // A shard's final chain states for the exchange between devices: row c - sh_c0

@@ -53,6 +53,25 @@ def test_bookkeeping_gauss(k):
     _compare_iterations(ons, run, 4)
 
 
+def test_bookkeeping_more_than_64_parameters():
+    """70 full parameters: 67 fixed (the last three at full indices 64 - 66)
+    and 3 free at full indices 67 - 69.  The Gaussian likelihood sums over
+    every full parameter, so a proposal row whose parameters past 64 were not
+    written by the prior transform would leave the oracle's bookkeeping."""
+    from paper_2509_13307_gb300 import Problem, NestedRun
+    from oracle.priors import cube_to_theta
+    cfg = w.gauss_test(3, n_live=40, n_delete=4, seed=29)
+    inp = dict(w.make_gauss_inputs(cfg))
+    priors = [("F", 0.3 + 0.005 * i, 0.0) for i in range(67)] + [("U", 0.0, 1.0)] * 3
+    inp["priors"], inp["n_params"] = priors, len(priors)
+    orc = GaussOracle(inp)
+    ons = NestedSampler.from_config(lambda u: orc.loglike(cube_to_theta(priors, u)), 3, cfg.sampler)
+    ons.initialise()
+    prob = Problem(inp, "fp64", max_batch=40)
+    run = NestedRun.from_config(prob, cfg.sampler)
+    _compare_iterations(ons, run, 4)
+
+
 def test_bookkeeping_shear5_plain_ns():
     """The 5-parameter toy with k = 1 (plain nested sampling)."""
     from paper_2509_13307_gb300 import NestedRun
