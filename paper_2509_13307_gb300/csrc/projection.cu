@@ -606,8 +606,8 @@ k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* _
     }
 }
 
-// Whitening Y = R L^-T for a block of WR rows (8, or 16 for long data
-// vectors).  The ntile column tiles of 64 (b <= a) are split over the cs
+// Whitening Y = R L^-T for a block of WR rows (16; the kernel also takes
+// 8).  The ntile column tiles of 64 (b <= a) are split over the cs
 // CTAs of a cluster (rank q takes tiles q, q + cs, ...).  Per tile the
 // reduction range (rounded up to 32, zero-filled) is staged in shared memory
 // with 16-byte cp.async copies, in as few chunks as fit; the 8 warps split it
@@ -820,10 +820,13 @@ static int launch_whiten(const TR* resid, int D, const TA* LinvT, double c0, dou
 template <typename TR, typename TA>
 int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL, const int* nrows, int grid_rows,
                 cudaStream_t st) {
-    // short data vectors: 8-row blocks of up to ~100 KB (two CTAs per SM);
-    // long ones: 16-row blocks (half the passes over L^-T) with the whole SM
+    // 16-row blocks.  Short data vectors: CTAs of up to ~100 KB (two per SM),
+    // so the clusters of a ~460-row batch fit one wave (8-row blocks needed
+    // 58 five-CTA clusters there, two waves: 114.7 -> 111.6 us per 39-d
+    // nested-sampling round).  Long ones: the whole SM, half the passes over
+    // L^-T of 8-row blocks.
     if ((D + kWC - 1) / kWC <= kWClusterMax)
-        return launch_whiten<TR, TA, 8>(resid, D, LinvT, c0, logL, nrows, grid_rows, 100 * 1024, st);
+        return launch_whiten<TR, TA, 16>(resid, D, LinvT, c0, logL, nrows, grid_rows, 100 * 1024, st);
     return launch_whiten<TR, TA, 16>(resid, D, LinvT, c0, logL, nrows, grid_rows, 200 * 1024, st);
 }
 template int launch_chi2<float, float>(const float*, int, const float*, double, double*, const int*, int,
