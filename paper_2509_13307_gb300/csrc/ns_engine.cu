@@ -545,13 +545,41 @@ __device__ void advance_chain(const RunDev& r, const PriorRegs& q, int c, int la
             continue;
         }
         if (phase == PH_OUT) {
+            // both ends' cube tests first, then one atomic for the rows they need
+            bool okl = false, okr = false;
+            double yl0 = 0.0, yl1 = 0.0, yr0 = 0.0, yr1 = 0.0;
             if (!(ends & 1) && row < 0) {
                 if (step >= r.cap_steps) { flags |= NS_BIT_SLICE_CAP; ends |= 1; }
-                else if ((row = propose(l)) < 0) ends |= 1;
+                else {
+                    yl0 = __dadd_rn(x0, __dmul_rn(l, u0v));
+                    yl1 = __dadd_rn(x1, __dmul_rn(l, u1v));
+                    okl = __all_sync(0xffffffffu, (!has0 || (yl0 > 0.0 && yl0 < 1.0)) && (!has1 || (yl1 > 0.0 && yl1 < 1.0)));
+                    if (!okl) ends |= 1;
+                }
             }
             if (!(ends & 2) && row2 < 0) {
                 if (step2 >= r.cap_steps) { flags |= NS_BIT_SLICE_CAP; ends |= 2; }
-                else if ((row2 = propose(rr)) < 0) ends |= 2;
+                else {
+                    yr0 = __dadd_rn(x0, __dmul_rn(rr, u0v));
+                    yr1 = __dadd_rn(x1, __dmul_rn(rr, u1v));
+                    okr = __all_sync(0xffffffffu, (!has0 || (yr0 > 0.0 && yr0 < 1.0)) && (!has1 || (yr1 > 0.0 && yr1 < 1.0)));
+                    if (!okr) ends |= 2;
+                }
+            }
+            if (okl || okr) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(r.batch_ctr, (okl ? 1 : 0) + (okr ? 1 : 0));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (okl) {
+                    row = base;
+                    emit_theta(r, q, row, has0 ? yl0 : 0.0, has1 ? yl1 : 0.0, lane);
+                    ++evals;
+                }
+                if (okr) {
+                    row2 = base + (okl ? 1 : 0);
+                    emit_theta(r, q, row2, has0 ? yr0 : 0.0, has1 ? yr1 : 0.0, lane);
+                    ++evals;
+                }
             }
             if (ends == 3) { phase = PH_SHRINK; step = 0; continue; }
             break;                                  // an end is being evaluated
