@@ -126,6 +126,17 @@ k_emu_input(const double* __restrict__ theta_full, int P, const int* __restrict_
             const double* __restrict__ inv_scale, int K0,
             const T* __restrict__ W0, const T* __restrict__ b0, ActDev<T> act, int N,
             TO* __restrict__ out, const int* __restrict__ nrows) {
+    // the weights of a thread's first UP units are problem constants: in
+    // registers before the dependency wait
+    constexpr int UP = KMAX <= 8 ? 4 : 1;
+    T wp[UP][KMAX], bp[UP];
+#pragma unroll
+    for (int u = 0; u < UP; ++u) {
+        const int n = threadIdx.x + u * blockDim.x;
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) wp[u][j] = (n < N && j < K0) ? W0[(size_t)n * K0 + j] : T(0);
+        bp[u] = n < N ? b0[n] : T(0);
+    }
     pdl_begin();
     const int M = *nrows;
     const int r0 = blockIdx.x * kInRows;
@@ -140,11 +151,7 @@ k_emu_input(const double* __restrict__ theta_full, int P, const int* __restrict_
         x[r][j] = sizeof(T) == 8 ? (T)(v / scale[j]) : (T)(v * inv_scale[j]);
     }
     __syncthreads();
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        T w[KMAX];
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j) w[j] = j < K0 ? W0[(size_t)n * K0 + j] : T(0);
-        const T bn = b0[n];
+    auto unit = [&](int n, const T (&w)[KMAX], T bn) {
         for (int r = 0; r < nr; ++r) {
             T acc = bn;
 #pragma unroll
@@ -152,6 +159,17 @@ k_emu_input(const double* __restrict__ theta_full, int P, const int* __restrict_
                 if (j < K0) acc = fma(w[j], x[r][j], acc);
             out[(size_t)(r0 + r) * N + n] = cvt_out<TO, T>(act_apply<T>(act, n, acc));
         }
+    };
+#pragma unroll
+    for (int u = 0; u < UP; ++u) {
+        const int n = threadIdx.x + u * blockDim.x;
+        if (n < N) unit(n, wp[u], bp[u]);
+    }
+    for (int n = threadIdx.x + UP * blockDim.x; n < N; n += blockDim.x) {
+        T w[KMAX];
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) w[j] = j < K0 ? W0[(size_t)n * K0 + j] : T(0);
+        unit(n, w, b0[n]);
     }
 }
 

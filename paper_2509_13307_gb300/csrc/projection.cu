@@ -441,7 +441,10 @@ k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* _
     using M = Math<T, FAST>;
     constexpr int NP = NB * (NB + 1) / 2;
     static_assert(2 * NP <= 32, "two multipoles of pair sums must fit one warp transpose");
-    pdl_begin();
+    // Only the emulator table comes from the preceding kernel (programmatic
+    // dependency).  The row count and parameters (slice kernel) and the
+    // windows (side stream) reach this kernel through the likelihood's
+    // fork / join events, full dependencies: they are staged before the wait.
     const int row = blockIdx.x;
     if (row >= *nrows) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -491,17 +494,20 @@ k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* _
             mbar_init_fence();
         }
         __syncthreads();
-        if (wid == 0) {
-            // one arrival with the whole transaction count, then the copies,
-            // issued by the 32 lanes of warp 0 in parallel
-            if (lane == 0) mbar_expect_tx(bar, row_bytes * n_z + win_bytes);
-            __syncwarp();
-            if (lane == 0) bulk_g2s(smem_u32(W), wsrc, win_bytes, bar);
-            for (int r = lane; r < n_z; r += 32)
-                bulk_g2s(smem_u32(U + (r + 1) * PK + 4), src + (size_t)r * n_k, row_bytes, bar);
+        // one arrival with the whole transaction count and the windows copy;
+        // the table's row copies (lanes of warp 0 in parallel) after the wait
+        if (wid == 0 && lane == 0) {
+            mbar_expect_tx(bar, row_bytes * n_z + win_bytes);
+            bulk_g2s(smem_u32(W), wsrc, win_bytes, bar);
         }
         for (int i = tid; i < sp.n_params; i += nt) thr[i] = (T)theta_full[(size_t)row * sp.n_params + i];
         stage_nodes();
+        pdl_begin();
+        if (wid == 0) {
+            __syncwarp();
+            for (int r = lane; r < n_z; r += 32)
+                bulk_g2s(smem_u32(U + (r + 1) * PK + 4), src + (size_t)r * n_k, row_bytes, bar);
+        }
         // warp 0 polls the barrier while the others sleep at the CTA barrier;
         // afterwards every thread observes the completed phase (acquire).
         int fail = 0;
@@ -515,11 +521,12 @@ k_limber(const ShearParams sp, const double* __restrict__ theta_full, const T* _
             return;
         }
     } else {
-        for (int r = wid; r < n_z; r += nw)
-            for (int k = lane; k < n_k; k += 32) U[(r + 1) * PK + 4 + k] = src[(size_t)r * n_k + k];
         for (int i = tid; i < (NB + 1) * Np; i += nt) W[i] = wsrc[i];
         for (int i = tid; i < sp.n_params; i += nt) thr[i] = (T)theta_full[(size_t)row * sp.n_params + i];
         stage_nodes();
+        pdl_begin();
+        for (int r = wid; r < n_z; r += nw)
+            for (int k = lane; k < n_k; k += 32) U[(r + 1) * PK + 4 + k] = src[(size_t)r * n_k + k];
         __syncthreads();
     }
     for (int k = 4 + tid; k < 4 + n_k; k += nt) {
