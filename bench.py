@@ -162,7 +162,7 @@ LIMBER_TRAFFIC_BYTES_PER_EVAL = 29979904 / 460
 LIMBER_TRAFFIC_SOURCES = ("paper_2509_13307_gb300/csrc/projection.cu", "paper_2509_13307_gb300/csrc/async_copy.cuh")
 # the whitening kernel and its launcher share projection.cu; that section does not enter the digest
 LIMBER_DIGEST_SKIP = ("// Whitening Y = R L^-T", "template <typename T>\nstatic size_t windows_smem")
-LIMBER_TRAFFIC_SHA256 = "a8b34e31648e080815934a9029335d4b87e95ddc8ce8707f0b7db9997ec03b10"
+LIMBER_TRAFFIC_SHA256 = "52f6dbc59c1dce38ca2e5c08ab54174a9a1aec25b3ae3bace81f87e79b41af4f"
 
 
 def limber_source_digest() -> str:
