@@ -55,6 +55,7 @@ struct RunDev {
     int* deleted;
     int* starts;
     double* chol;
+    float* chol32;        // FP32 copy of chol (directions of reduced-precision problems)
     double* cov;
     double* mean;         // d column means of the live set
     double* dirs;         // k x R x d slice directions u = L_Sigma z / |z| of the iteration
@@ -336,6 +337,7 @@ __global__ void k_cholesky(RunDev r) {
     for (int t = threadIdx.x; t < d * d; t += blockDim.x) {
         const int i = t / d, j = t % d;
         r.chol[t] = (j <= i) ? A[t] : 0.0;
+        r.chol32[t] = (j <= i) ? (float)A[t] : 0.f;
     }
     if (threadIdx.x == 0 && bad) atomicOr(&r.sc->status, NS_BIT_NONFINITE);
 }
@@ -371,6 +373,7 @@ __global__ void k_chains_start(RunDev r) {
 // round (FP64 transcendentals run at a small fraction of the FP32 rate).
 __global__ void __launch_bounds__(256) k_directions(RunDev r) {
     __shared__ double zs[8][64];
+    __shared__ float zsf[8][64];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long g = (long long)blockIdx.x * 8 + wib;
     if (g >= (long long)(r.sh_c1 - r.sh_c0) * r.R) return;
@@ -379,6 +382,39 @@ __global__ void __launch_bounds__(256) k_directions(RunDev r) {
     const int it = (int)r.sc->iter;
     double* zsw = zs[wib];
     const int nch = (d + 1) / 2;
+    if (r.prior_f32) {
+        // reduced-precision problems: the same Philox draws, Box-Muller and
+        // the triangular product in FP32 (GB300's FP64 pipe is a small
+        // fraction of its FP32 rate); the direction is stored in FP64
+        float f0 = 0.f, f1 = 0.f;
+        if (lane < nch) {
+            const Draw2 q = philox_uniforms(r.seed, P_DIR, lane, (uint32_t)it, (uint32_t)c, (uint32_t)move);
+            const float rad = sqrtf(-2.f * logf((float)q.a));
+            float sn, cs;
+            sincospif(2.f * (float)q.b, &sn, &cs);
+            f0 = rad * cs;
+            f1 = (2 * lane + 1 < d) ? rad * sn : 0.f;
+        }
+        const float nrm = sqrtf(warp_sum(f0 * f0 + f1 * f1));
+        float* zf = zsf[wib];
+        if (lane < nch) {
+            zf[2 * lane] = f0 / nrm;
+            if (2 * lane + 1 < d) zf[2 * lane + 1] = f1 / nrm;
+        }
+        __syncwarp();
+        double* outf = r.dirs + ((size_t)c * r.R + move) * d;
+        if (lane < d) {
+            float a0 = 0.f;
+            for (int b = 0; b <= lane; ++b) a0 = fmaf(r.chol32[lane * d + b], zf[b], a0);
+            outf[lane] = (double)a0;
+        }
+        if (lane + 32 < d) {
+            float a1 = 0.f;
+            for (int b = 0; b <= lane + 32; ++b) a1 = fmaf(r.chol32[(lane + 32) * d + b], zf[b], a1);
+            outf[lane + 32] = (double)a1;
+        }
+        return;
+    }
     double z0 = 0.0, z1 = 0.0;
     if (lane < nch) {
         const Draw2 q = philox_uniforms(r.seed, P_DIR, lane, (uint32_t)it, (uint32_t)c, (uint32_t)move);
@@ -958,6 +994,7 @@ extern "C" int ns_init(const ns_problem* p, const ns_config* cfg, void* stream, 
     RA(deleted, sizeof(int) * k);
     RA(starts, sizeof(int) * k);
     RA(chol, sizeof(double) * d * d);
+    RA(chol32, sizeof(float) * d * d);
     RA(cov, sizeof(double) * d * d);
     RA(mean, sizeof(double) * d);
     RA(dirs, sizeof(double) * (size_t)k * r->R * d);
