@@ -46,6 +46,32 @@ def test_traffic_pin_follows_the_sources(monkeypatch):
     assert bench.limber_traffic(rows) is None
 
 
+def test_traffic_digest_skips_only_the_whitening_section(tmp_path, monkeypatch):
+    """The digest covers the Limber kernel's sources: an edit inside the
+    whitening section of projection.cu leaves it unchanged, an edit anywhere
+    else changes it."""
+    src = {f: open(os.path.join(ROOT, f), encoding="utf-8").read() for f in bench.LIMBER_TRAFFIC_SOURCES}
+    proj = bench.LIMBER_TRAFFIC_SOURCES[0]
+    a, b = bench.LIMBER_DIGEST_SKIP
+    assert a in src[proj] and b in src[proj] and src[proj].index(a) < src[proj].index(b)
+
+    def digest_with(text):
+        for f, t in src.items():
+            dst = tmp_path / f
+            dst.parent.mkdir(parents=True, exist_ok=True)
+            dst.write_text(text if f == proj else t, encoding="utf-8")
+        monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+        return bench.limber_source_digest()
+
+    base = digest_with(src[proj])
+    i = src[proj].index(a) + len(a)
+    inside = src[proj][:i] + " (edited)" + src[proj][i:]
+    j = src[proj].index("k_limber(")
+    outside = src[proj][:j] + "/* edited */ " + src[proj][j:]
+    assert digest_with(inside) == base
+    assert digest_with(outside) != base
+
+
 def test_measured_peaks_file_and_fallback(tmp_path, monkeypatch):
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 7000.5, "bf16_tflops_sustained": 1650.0}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
