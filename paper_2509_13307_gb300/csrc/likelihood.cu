@@ -582,7 +582,7 @@ int run_likelihood(const ns_problem* p, Workspace* ws, int grid_rows, double* lo
                                             model_out, ws->d_nrows, grid_rows, ws->d_err, st));
         if (model_out) return NS_OK;
         return launch_chi2<double, double>((const double*)ws->resid, sp.D, p->d_LinvT64, p->c0, logL_out,
-                                           ws->d_nrows, grid_rows, st);
+                                           ws->d_nrows, grid_rows, st, true);
     }
     // FP32 stages (FP32 / BF16 / BF16_F64CHI2)
     if (p->precision == NS_PREC_FP32) NS_TRY(run_emulator_simt<float>(p, ws, grid_rows, st, model_head(p, ws->table)));
@@ -608,10 +608,10 @@ int run_likelihood(const ns_problem* p, Workspace* ws, int grid_rows, double* lo
     NS_TRY(probe_begin(probe, PROBE_CHI2, ws, st));
     if (p->precision == NS_PREC_BF16_F64CHI2)
         NS_TRY(launch_chi2<float, double>((const float*)ws->resid, sp.D, p->d_LinvT64, p->c0, logL_out,
-                                          ws->d_nrows, grid_rows, st));
+                                          ws->d_nrows, grid_rows, st, true));
     else
         NS_TRY(launch_chi2<float, float>((const float*)ws->resid, sp.D, p->d_LinvT32, p->c0, logL_out,
-                                         ws->d_nrows, grid_rows, st));
+                                         ws->d_nrows, grid_rows, st, true));
     return probe_end(probe, PROBE_CHI2, st);
 }
 

@@ -170,10 +170,13 @@ int launch_limber(const ShearParams& sp, const double* theta_full, const T* tabl
                   double* model_out, const int* nrows, int grid_rows, int* err, cudaStream_t st);
 // Whether both projection stages fit the shared memory of one CTA (elt = 4 or 8).
 bool projection_fits(const ShearParams& sp, int elt);
-// Whitened chi^2 and log L = c0 - chi^2 / 2 (projection.cu).
+// Whitened chi^2 and log L = c0 - chi^2 / 2 (projection.cu).  rows_ready: the
+// row count is final before the preceding kernel completes (the shear
+// likelihood's fork / join events), so the kernel may read it, and request
+// the constant L^-T, before its dependency wait.
 template <typename TR, typename TA>
 int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL, const int* nrows, int grid_rows,
-                cudaStream_t st);
+                cudaStream_t st, bool rows_ready = false);
 
 // Adjoint of the shear projection (adjoint.cu).
 int adjoint_scratch_elems(const ShearParams& sp);

@@ -656,12 +656,19 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
 template <typename TR, typename TA, int WR>
 __global__ void __launch_bounds__(256)
 k_whiten(const TR* __restrict__ resid, int D, const TA* __restrict__ LinvT, int ntile, int KC, double c0,
-         double* __restrict__ logL, const int* __restrict__ nrows) {
+         double* __restrict__ logL, const int* __restrict__ nrows, int rows_ready) {
     static_assert(WR == 8 || WR == 16, "8 or 16 rows per block");
-    pdl_begin();
-    const int M = *nrows;
+    // rows_ready: the row count (slice kernel) reaches this kernel through
+    // the shear likelihood's fork / join events (full dependencies), so it is
+    // read, and the first tile's first chunk of the constant L^-T requested,
+    // before the dependency wait; the residuals (the preceding kernel's
+    // output) always after it.
     const int row0 = blockIdx.y * WR;
-    if (row0 >= M) return;                         // every CTA of the cluster has this row block
+    int M = 0;
+    if (rows_ready) {
+        M = *nrows;
+        if (row0 >= M) return;                     // every CTA of the cluster has this row block
+    }
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -677,6 +684,36 @@ k_whiten(const TR* __restrict__ resid, int D, const TA* __restrict__ LinvT, int 
     constexpr int TPR = 256 / WR;                  // threads per row (32 or 16)
     constexpr int CPT = kWC / TPR;                 // columns per thread (2 or 4)
     const int fr = tid / TPR, fc = (tid % TPR) * CPT;
+    // L^-T rows k0 .. k0 + len of the tile at column a0 (zero beyond b_end and beyond column D)
+    auto stage_L = [&](int a0, int b_end, int k0, int len) {
+        const int lv = max(0, min(len, b_end - k0));
+        if (vecL) {
+            constexpr int per = 16 / sizeof(TA), vpr = kWC / per;
+            for (int q = tid; q < len * vpr; q += 256) {
+                const int bb = q / vpr, v = q % vpr;
+                TA* dst = Ls + bb * kWC + v * per;
+                if (bb < lv && a0 + v * per < D) cp_async16(dst, LinvT + (size_t)(k0 + bb) * D + a0 + v * per);
+                else for (int e = 0; e < per; ++e) dst[e] = TA(0);
+            }
+        } else {
+            for (int q = tid; q < len * kWC; q += 256) {
+                const int bb = q / kWC, aa = q % kWC;
+                if (bb < lv && a0 + aa < D) cp_async_elt(Ls + bb * kWC + aa, LinvT + (size_t)(k0 + bb) * D + a0 + aa);
+                else Ls[bb * kWC + aa] = TA(0);
+            }
+        }
+    };
+    bool prefetched = false;
+    if (rows_ready && rank < ntile) {
+        const int a0 = rank * kWC, b_end = min(D, a0 + kWC);
+        stage_L(a0, b_end, 0, min(KC, (b_end + 31) & ~31));
+        prefetched = true;
+    }
+    pdl_begin();
+    if (!rows_ready) {
+        M = *nrows;
+        if (row0 >= M) return;                     // every CTA of the cluster has this row block
+    }
     TA run = TA(0);                                // row fr: sum of y^2 over this CTA's tiles
     for (int tile = rank; tile < ntile; tile += cs) {
         const int a0 = tile * kWC;
@@ -688,22 +725,10 @@ k_whiten(const TR* __restrict__ resid, int D, const TA* __restrict__ LinvT, int 
         for (int k0 = 0; k0 < Kp; k0 += KC) {
             const int len = min(KC, Kp - k0);          // multiple of 32
             const int lv = max(0, min(len, b_end - k0)); // rows holding data
-            __syncthreads();                           // previous chunk / tile finish done with Ls, Rs
-            // L^-T rows k0 .. k0 + len (zero beyond b_end and beyond column D)
-            if (vecL) {
-                constexpr int per = 16 / sizeof(TA), vpr = kWC / per;
-                for (int q = tid; q < len * vpr; q += 256) {
-                    const int bb = q / vpr, v = q % vpr;
-                    TA* dst = Ls + bb * kWC + v * per;
-                    if (bb < lv && a0 + v * per < D) cp_async16(dst, LinvT + (size_t)(k0 + bb) * D + a0 + v * per);
-                    else for (int e = 0; e < per; ++e) dst[e] = TA(0);
-                }
-            } else {
-                for (int q = tid; q < len * kWC; q += 256) {
-                    const int bb = q / kWC, aa = q % kWC;
-                    if (bb < lv && a0 + aa < D) cp_async_elt(Ls + bb * kWC + aa, LinvT + (size_t)(k0 + bb) * D + a0 + aa);
-                    else Ls[bb * kWC + aa] = TA(0);
-                }
+            if (prefetched) prefetched = false;        // this chunk's L^-T is already in flight
+            else {
+                __syncthreads();                       // previous chunk / tile finish done with Ls, Rs
+                stage_L(a0, b_end, k0, len);
             }
             // R rows row0 .. row0 + WR, columns k0 .. k0 + len (zero beyond b_end / M)
             if (vecR) {
@@ -791,7 +816,7 @@ static size_t whiten_smem(int KC, int WR) {
 
 template <typename TR, typename TA, int WR>
 static int launch_whiten(const TR* resid, int D, const TA* LinvT, double c0, double* logL, const int* nrows,
-                         int grid_rows, size_t smem_cap, cudaStream_t st) {
+                         int grid_rows, size_t smem_cap, cudaStream_t st, bool rows_ready) {
     const int ntile = (D + kWC - 1) / kWC;
     const int cs = std::min(ntile, kWClusterMax);
     // the whole (padded) reduction range in one chunk when it fits smem_cap
@@ -820,28 +845,29 @@ static int launch_whiten(const TR* resid, int D, const TA* LinvT, double c0, dou
     attr2[1].val.clusterDim.z = 1;
     cfg.attrs = attr2;
     cfg.numAttrs = 2;
-    NS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_whiten<TR, TA, WR>, resid, D, LinvT, ntile, KC, c0, logL, nrows));
+    NS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_whiten<TR, TA, WR>, resid, D, LinvT, ntile, KC, c0, logL, nrows,
+                                   rows_ready ? 1 : 0));
     return NS_OK;
 }
 
 template <typename TR, typename TA>
 int launch_chi2(const TR* resid, int D, const TA* LinvT, double c0, double* logL, const int* nrows, int grid_rows,
-                cudaStream_t st) {
+                cudaStream_t st, bool rows_ready) {
     // 16-row blocks.  Short data vectors: CTAs of up to ~100 KB (two per SM),
     // so the clusters of a ~460-row batch fit one wave (8-row blocks needed
     // 58 five-CTA clusters there, two waves: 114.7 -> 111.6 us per 39-d
     // nested-sampling round).  Long ones: the whole SM, half the passes over
     // L^-T of 8-row blocks.
     if ((D + kWC - 1) / kWC <= kWClusterMax)
-        return launch_whiten<TR, TA, 16>(resid, D, LinvT, c0, logL, nrows, grid_rows, 100 * 1024, st);
-    return launch_whiten<TR, TA, 16>(resid, D, LinvT, c0, logL, nrows, grid_rows, 200 * 1024, st);
+        return launch_whiten<TR, TA, 16>(resid, D, LinvT, c0, logL, nrows, grid_rows, 100 * 1024, st, rows_ready);
+    return launch_whiten<TR, TA, 16>(resid, D, LinvT, c0, logL, nrows, grid_rows, 200 * 1024, st, rows_ready);
 }
 template int launch_chi2<float, float>(const float*, int, const float*, double, double*, const int*, int,
-                                       cudaStream_t);
+                                       cudaStream_t, bool);
 template int launch_chi2<float, double>(const float*, int, const double*, double, double*, const int*, int,
-                                        cudaStream_t);
+                                        cudaStream_t, bool);
 template int launch_chi2<double, double>(const double*, int, const double*, double, double*, const int*, int,
-                                         cudaStream_t);
+                                         cudaStream_t, bool);
 
 template <typename T>
 static size_t windows_smem(const ShearParams& sp) {
